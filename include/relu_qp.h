@@ -1,0 +1,175 @@
+/*
+ * relu_qp.h -- C ABI of the GB300 (sm_103a) ReLU-QP solver.
+ *
+ * Problem (paper Sec. II-A, Eq. qp_def, with H->P, g->q, G->A, c,d->l,u):
+ *
+ *     minimise 1/2 x^T P x + q^T x   subject to   l <= A x <= u,
+ *
+ * P (n x n) symmetric positive definite, A (m x n), l_i in [-inf, +inf),
+ * u_i in (-inf, +inf], l <= u.  Rows with l_i == u_i are equality rows.
+ *
+ * Method (paper Sec. III, Algorithm 1): ADMM with a fixed penalty written as
+ * the weight-tied layer v+ = clamp(W_rho v + b_rho) on v = [x; z; lam]
+ * (Eq. gpu_update).  A bank of penalties rho_i is factored offline
+ * (relu_qp_setup); online, the layer runs until the residuals of Eqs. primal
+ * and dual meet the tolerance, checking every `check_interval` layers and
+ * switching to the bank entry closest to the estimate of Eq. rho_update
+ * (Sec. III-C).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are dense, row-major, contiguous.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership.  Output arrays are caller-owned and written in full.
+ *  - The handle owns all device memory it allocates; relu_qp_destroy frees it.
+ *  - All GPU work is issued on opts.stream and the call synchronises that
+ *    stream before returning (results are ready on return).
+ *  - Return value: RELU_QP_OK (0) or a negative RELU_QP_ERR_* code;
+ *    relu_qp_last_error(h) gives a one-line message.  Non-convergence is not
+ *    an error: it is reported as info->status == RELU_QP_MAX_ITER.
+ *  - No C++ exception crosses the ABI.  One handle must not be used from two
+ *    host threads at the same time.
+ */
+#ifndef RELU_QP_H
+#define RELU_QP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------- */
+#define RELU_QP_OK                0
+#define RELU_QP_ERR_INVALID      -1   /* bad sizes, NULL where required, l > u, NaN input */
+#define RELU_QP_ERR_NOT_PD       -2   /* Cholesky pivot <= 0: P + sigma I + A^T rho A not PD */
+#define RELU_QP_ERR_OOM          -3   /* device allocation refused (or over the memory budget) */
+#define RELU_QP_ERR_CUDA         -4   /* a CUDA runtime call failed */
+#define RELU_QP_ERR_TIMEOUT      -5   /* a device-side wait gave up at its deadline */
+#define RELU_QP_ERR_UNSUPPORTED  -6   /* feature not available for this handle / device */
+
+/* ---- per-solve status (relu_qp_info.status) ------------------------------ */
+#define RELU_QP_SOLVED            0   /* both residuals met the tolerance at a check */
+#define RELU_QP_MAX_ITER          1   /* max_iter layers ran without meeting it */
+#define RELU_QP_NUMERICAL         2   /* a residual became NaN or Inf */
+
+typedef struct relu_qp_s* relu_qp_t;
+
+typedef struct relu_qp_opts {
+    int    check_interval;  /* layers between residual checks; paper default 25
+                               (Sec. III-C "Convergence Checking"); 0 = never check
+                               (runs exactly max_iter layers at a fixed rho) */
+    int    adaptive_rho;    /* 1: apply Eq. rho_update + nearest bank entry at each
+                               unconverged check; 0: keep the starting rho */
+    double rho0;            /* starting penalty (paper default 0.1, Sec. III-C), mapped
+                               to the nearest bank entry */
+    double eq_scale;        /* penalty factor of equality rows (paper: 1000, Sec. II-B) */
+    int    keep_fp64;       /* 1: keep the FP64 layer matrices for relu_qp_get_layer */
+    int    max_batch;       /* capacity of batched solves (0: single-QP handle) */
+    int    batch_precision; /* RELU_QP_PREC_FP32 or RELU_QP_PREC_BF16X3 */
+    void*  stream;          /* cudaStream_t for all work; NULL = the legacy default stream */
+} relu_qp_opts;
+
+#define RELU_QP_PREC_FP32    0   /* batched layer product in FP32 on the CUDA cores */
+#define RELU_QP_PREC_BF16X3  1   /* batched layer product on tcgen05 tensor cores,
+                                    BF16 hi+lo split operands, FP32 accumulate */
+
+typedef struct relu_qp_info {
+    int    status;       /* RELU_QP_SOLVED / RELU_QP_MAX_ITER / RELU_QP_NUMERICAL */
+    int    iters;        /* layers executed */
+    int    rho_index;    /* bank index in use at return (feed back as a warm start) */
+    int    rho_switches; /* number of bank switches during the solve */
+    double r_prim;       /* ||A x - z||_inf at the last check (Eq. primal) */
+    double r_dual;       /* ||P x + q + A^T lam||_inf at the last check (Eq. dual) */
+    double solve_ms;     /* device time of the solve (CUDA events) */
+} relu_qp_info;
+
+/* Fill *opts with the defaults above (check 25, adaptive, rho0 0.1, eq 1000,
+ * no FP64 copy, single-QP, FP32, default stream). */
+void relu_qp_default_opts(relu_qp_opts* opts);
+
+/*
+ * relu_qp_setup -- offline stage of Algorithm 1 ("compute KKT inverse, W and b
+ * for each rho").  For every bank entry rho_r the library forms, in FP64 on
+ * the GPU, K_r = P + sigma I + A^T diag(rho_r) A, factors it with a blocked
+ * Cholesky, and solves K_r X = [sigma I - A^T rho_r A, A^T, -I] by blocked
+ * triangular solves; the layer matrices follow (Eq. gpu_update) and are
+ * stored in FP32 (and BF16 hi/lo when batched precision is BF16X3).
+ *
+ *   out       receives the handle (set to NULL on failure)
+ *   n, m      decision variables (n >= 1) and constraint rows (m >= 0)
+ *   P         n*n FP64, symmetric positive definite (only its values are read)
+ *   q         n FP64 linear cost (may be NULL: zeros; relu_qp_update can set it)
+ *   A         m*n FP64 (may be NULL when m == 0)
+ *   l, u      m FP64 bounds, +-INFINITY allowed, l <= u elementwise
+ *   sigma     > 0, the proximal weight of Eq. admm_al (typical 1e-6)
+ *   rho_bank  n_rho > 0 strictly positive penalties (paper: log-spaced list)
+ *   opts      NULL for defaults
+ * Errors: INVALID (sizes, l > u, NaN/Inf in P, q, A, sigma <= 0, rho <= 0),
+ * NOT_PD (a Cholesky pivot <= 0), OOM, CUDA.
+ */
+int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q,
+                  const double* A, const double* l, const double* u, double sigma,
+                  const double* rho_bank, int n_rho, const relu_qp_opts* opts);
+
+/*
+ * relu_qp_update -- online "update b, c~, d~" of Algorithm 1: replaces the
+ * linear cost and/or the bounds of the problem (NULL keeps the old array).
+ * b_r = [-D_r; -A D_r] q is recomputed for every bank entry.  Equality rows
+ * must keep the same pattern (l_i == u_i) they had at setup.
+ * Errors: INVALID (l > u, NaN, changed equality pattern), CUDA.
+ */
+int relu_qp_update(relu_qp_t h, const double* q, const double* l, const double* u);
+
+/*
+ * relu_qp_solve -- online stage of Algorithm 1 for the single QP held by h.
+ *   x_warm, lam_warm  n / m FP64 warm start (Sec. II-B "Warm Starting":
+ *                     z = A x_warm); NULL = cold start v = 0 (lam_warm NULL
+ *                     with x_warm given means lam = 0)
+ *   rho_index_warm    bank index to start from, or -1 for the entry nearest rho0
+ *   eps_abs, eps_rel  tolerances: converged when ||Ax-z|| <= eps_abs + eps_rel
+ *                     max(||Ax||,||z||) and ||Px+q+A^T lam|| <= eps_abs + eps_rel
+ *                     max(||Px||,||A^T lam||,||q||) (inf-norms, Eqs. primal, dual)
+ *   max_iter          >= 1 layers at most
+ *   x_out             n FP64 (required); z_out, lam_out m FP64 (may be NULL).
+ *                     lam_out is the standard ADMM multiplier lam' + rho (Ax - z).
+ *   info              may be NULL
+ * The whole loop runs in one cooperative kernel on the device; the host
+ * waits only for its end.  Errors: INVALID, CUDA, TIMEOUT.
+ */
+int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int rho_index_warm,
+                  double eps_abs, double eps_rel, int max_iter, double* x_out, double* z_out,
+                  double* lam_out, relu_qp_info* info);
+
+/*
+ * relu_qp_get_layer -- export the layer of bank entry rho_index for checking:
+ *   Wt   (n+m)*(n+m) FP64: rows [x; Ax] of the layer in the factored form
+ *        [x+; (A x)+] = Wt [x; 2 rho z - lam'] + Bop q.  With D the KKT inverse,
+ *        Wt = [D(sigma I - A^T rho A), D A^T; A D(sigma I - A^T rho A), A D A^T];
+ *        the paper's W (Eq. gpu_update) follows by splitting the second block
+ *        column into its z (times 2 rho) and lam (times -1) columns, adding
+ *        [A, -I, rho^{-1}] to the z row, and appending the row [rho A, -rho, I].
+ *   Bop  (n+m)*n FP64: [-D; -A D]
+ * FP64 values if the handle was set up with keep_fp64, else the FP32 copies
+ * widened.  Either pointer may be NULL.  Errors: INVALID, CUDA.
+ */
+int relu_qp_get_layer(relu_qp_t h, int rho_index, double* Wt, double* Bop);
+
+/* Change check_interval / adaptive_rho / rho0 of an existing handle
+ * (other fields of opts are ignored).  Errors: INVALID. */
+int relu_qp_set_opts(relu_qp_t h, const relu_qp_opts* opts);
+
+/* Sizes of a handle (any pointer may be NULL). */
+int relu_qp_dims(relu_qp_t h, int* n, int* m, int* n_rho);
+
+/* Free every device and host resource of h (NULL is a no-op). */
+void relu_qp_destroy(relu_qp_t h);
+
+/* One-line description of the last error on h (or of the last failed setup
+ * when h is NULL).  Valid until the next call on h. */
+const char* relu_qp_last_error(relu_qp_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELU_QP_H */

@@ -27,7 +27,7 @@ H -> P, g -> q, G -> A, c,d -> l,u, primal y -> x, dual lambda -> lam.
 * ``brute_force_qp``: enumerates every active set of a small QP; it is an
   independent solver used only to pin the oracle.
 
-Readings of points the paper leaves open (each listed in the design notes):
+Readings of points the paper leaves open:
   R1 the layer state after k layers is (x_k, z_k, lam'_k) where lam' is the
      multiplier *before* the lam-step of the next layer; the multiplier of
      standard ADMM is lam_std = lam' + rho (A x - z).

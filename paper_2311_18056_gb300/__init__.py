@@ -1,0 +1,203 @@
+"""GB300 (sm_103a) ReLU-QP solver: Python binding of ``librelu_qp.so``.
+
+This module only marshals arguments to the C ABI declared in
+``include/relu_qp.h``; every step of the solve runs in the library's CUDA
+kernels.  Importing it does not need a GPU; creating a solver does, and it
+fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["ReluQP", "ReluQPError", "lib", "library_path", "OK", "SOLVED", "MAX_ITER", "NUMERICAL",
+           "PREC_FP32", "PREC_BF16X3", "EXPORTED_SYMBOLS"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "librelu_qp.so")
+
+OK = 0
+SOLVED, MAX_ITER, NUMERICAL = 0, 1, 2
+PREC_FP32, PREC_BF16X3 = 0, 1
+ERRORS = {-1: "INVALID", -2: "NOT_PD", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "UNSUPPORTED"}
+
+_c_int, _c_double, _c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("check_interval", _c_int), ("adaptive_rho", _c_int), ("rho0", _c_double),
+                ("eq_scale", _c_double), ("keep_fp64", _c_int), ("max_batch", _c_int),
+                ("batch_precision", _c_int), ("stream", _c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", _c_int), ("iters", _c_int), ("rho_index", _c_int), ("rho_switches", _c_int),
+                ("r_prim", _c_double), ("r_dual", _c_double), ("solve_ms", _c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# name -> (restype, argtypes); the CPU test checks the library exports each one
+_SIGNATURES = {
+    "relu_qp_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "relu_qp_setup": (_c_int, [ctypes.POINTER(_c_void_p), _c_int, _c_int, _dp, _dp, _dp, _dp, _dp, _c_double,
+                               _dp, _c_int, ctypes.POINTER(Opts)]),
+    "relu_qp_update": (_c_int, [_c_void_p, _dp, _dp, _dp]),
+    "relu_qp_solve": (_c_int, [_c_void_p, _dp, _dp, _c_int, _c_double, _c_double, _c_int, _dp, _dp, _dp,
+                               ctypes.POINTER(Info)]),
+    "relu_qp_get_layer": (_c_int, [_c_void_p, _c_int, _dp, _dp]),
+    "relu_qp_set_opts": (_c_int, [_c_void_p, ctypes.POINTER(Opts)]),
+    "relu_qp_dims": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                              ctypes.POINTER(_c_int)]),
+    "relu_qp_destroy": (None, [_c_void_p]),
+    "relu_qp_last_error": (ctypes.c_char_p, [_c_void_p]),
+}
+EXPORTED_SYMBOLS = tuple(_SIGNATURES)
+
+_lib = None
+
+
+def lib():
+    """Load librelu_qp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(f"{library_path} is missing: build it with "
+                               "paper_2311_18056_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(library_path)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class ReluQPError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"relu_qp error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+        self.kind = ERRORS.get(code, "?")
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class ReluQP:
+    """One QP  min 1/2 x'Px + q'x  s.t.  l <= Ax <= u  with its bank of layers on the GPU."""
+
+    def __init__(self, P, A, l, u, q=None, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), *, check_interval=25,
+                 adaptive_rho=True, rho0=0.1, eq_scale=1e3, keep_fp64=False, max_batch=0,
+                 precision=PREC_FP32, stream=None):
+        L = lib()
+        P = _f64(P)
+        n = P.shape[0]
+        A = _f64(A) if A is not None else np.zeros((0, n))
+        m = A.shape[0] if A.ndim == 2 else 0
+        l = _f64(l, (m,)) if m else np.zeros(0)
+        u = _f64(u, (m,)) if m else np.zeros(0)
+        q = _f64(q, (n,))
+        bank = _f64(rho_bank)
+        o = Opts()
+        L.relu_qp_default_opts(ctypes.byref(o))
+        o.check_interval = int(check_interval)
+        o.adaptive_rho = int(bool(adaptive_rho))
+        o.rho0 = float(rho0)
+        o.eq_scale = float(eq_scale)
+        o.keep_fp64 = int(bool(keep_fp64))
+        o.max_batch = int(max_batch)
+        o.batch_precision = int(precision)
+        o.stream = _stream_handle(stream)
+        h = _c_void_p()
+        rc = L.relu_qp_setup(ctypes.byref(h), n, m, _ptr(P), _ptr(q), _ptr(A) if m else None,
+                             _ptr(l) if m else None, _ptr(u) if m else None, float(sigma), _ptr(bank),
+                             int(bank.size), ctypes.byref(o))
+        if rc != OK:
+            raise ReluQPError(rc, L.relu_qp_last_error(None).decode())
+        self._h = h
+        self.n, self.m, self.n_rho = n, m, int(bank.size)
+        self.rho_bank = tuple(float(r) for r in bank)
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc):
+        if rc != OK:
+            raise ReluQPError(rc, lib().relu_qp_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().relu_qp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- single QP ----------------------------------------------------------
+    def update(self, q=None, l=None, u=None):
+        q = _f64(q, (self.n,))
+        l = _f64(l, (self.m,))
+        u = _f64(u, (self.m,))
+        self._check(lib().relu_qp_update(self._h, _ptr(q), _ptr(l), _ptr(u)))
+
+    def solve(self, x_warm=None, lam_warm=None, rho_index=-1, eps_abs=1e-3, eps_rel=0.0, max_iter=4000):
+        x_warm = _f64(x_warm, (self.n,))
+        lam_warm = _f64(lam_warm, (self.m,))
+        x = np.empty(self.n)
+        z = np.empty(self.m)
+        lam = np.empty(self.m)
+        info = Info()
+        self._check(lib().relu_qp_solve(self._h, _ptr(x_warm), _ptr(lam_warm), int(rho_index), float(eps_abs),
+                                        float(eps_rel), int(max_iter), _ptr(x), _ptr(z) if self.m else None,
+                                        _ptr(lam) if self.m else None, ctypes.byref(info)))
+        out = info.as_dict()
+        out.update(x=x, z=z, lam=lam)
+        return out
+
+    def get_layer(self, rho_index):
+        R = self.n + self.m
+        Wt = np.empty((R, R))
+        Bop = np.empty((R, self.n))
+        self._check(lib().relu_qp_get_layer(self._h, int(rho_index), _ptr(Wt), _ptr(Bop)))
+        return Wt, Bop
+
+    def set_opts(self, check_interval=None, adaptive_rho=None, rho0=None):
+        o = Opts()
+        lib().relu_qp_default_opts(ctypes.byref(o))
+        o.check_interval = 25 if check_interval is None else int(check_interval)
+        o.adaptive_rho = 1 if adaptive_rho is None else int(bool(adaptive_rho))
+        o.rho0 = 0.1 if rho0 is None else float(rho0)
+        self._check(lib().relu_qp_set_opts(self._h, ctypes.byref(o)))

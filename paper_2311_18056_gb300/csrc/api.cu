@@ -1,0 +1,356 @@
+// C ABI entry points of librelu_qp.so (declared in include/relu_qp.h).
+#include "common.h"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace {
+thread_local std::string g_setup_error;
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// l <= u, no NaN, l != +inf, u != -inf.
+bool bounds_ok(const double* l, const double* u, int m) {
+    for (int i = 0; i < m; ++i) {
+        if (std::isnan(l[i]) || std::isnan(u[i])) return false;
+        if (l[i] > u[i]) return false;
+        if (l[i] == INFINITY || u[i] == -INFINITY) return false;
+    }
+    return true;
+}
+
+std::vector<float> to_f32(const double* p, size_t n) {
+    std::vector<float> v(n);
+    for (size_t i = 0; i < n; ++i) v[i] = (float)p[i];
+    return v;
+}
+
+int upload_problem(relu_qp_t h) {
+    const int n = h->n, m = h->m;
+    std::vector<float> q = to_f32(h->h_q.data(), n);
+    RQ_CUDA(h, cudaMemcpyAsync(h->q32, q.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+    if (m > 0) {
+        std::vector<float> l = to_f32(h->h_l.data(), m), u = to_f32(h->h_u.data(), m);
+        RQ_CUDA(h, cudaMemcpyAsync(h->l32, l.data(), sizeof(float) * m, cudaMemcpyHostToDevice, h->stream));
+        RQ_CUDA(h, cudaMemcpyAsync(h->u32, u.data(), sizeof(float) * m, cudaMemcpyHostToDevice, h->stream));
+        RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    double qn = 0.0;
+    for (int i = 0; i < n; ++i) qn = std::fmax(qn, std::fabs(h->h_q[i]));
+    h->qnorm = qn;
+    RQ_TRY(rq::compute_bias(h));
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RELU_QP_OK;
+}
+
+int setup_impl(relu_qp_t h, const double* P, const double* q, const double* A, const double* l,
+               const double* u, const double* rho_bank) {
+    const int n = h->n, m = h->m, R = h->R;
+    RQ_CUDA(h, cudaGetDevice(&h->device));
+    RQ_CUDA(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    RQ_CUDA(h, cudaEventCreate(&h->ev0));
+    RQ_CUDA(h, cudaEventCreate(&h->ev1));
+    h->h_q.assign(n, 0.0);
+    if (q) std::memcpy(h->h_q.data(), q, sizeof(double) * n);
+    h->h_l.assign(l, l + m);
+    h->h_u.assign(u, u + m);
+    h->eq.resize(m);
+    std::vector<double> row_scale(m);
+    std::vector<float> rs(m > 0 ? m : 1, 1.0f);
+    for (int i = 0; i < m; ++i) {
+        h->eq[i] = (l[i] == u[i]) ? 1 : 0;
+        row_scale[i] = h->eq[i] ? h->opts.eq_scale : 1.0;
+        rs[i] = (float)row_scale[i];
+    }
+    const int ldp = (int)rq::round_up(n, 4), ldt = (int)rq::round_up(m > 0 ? m : 1, 4);
+    for (int r = 0; r < h->nr; ++r) {
+        rq::BankEntry& be = h->be[r];
+        be.rho = rho_bank[r];
+        RQ_TRY(rq::alloc(h, &be.Wt, (size_t)R * h->ldw));
+        RQ_TRY(rq::alloc(h, &be.Bop, (size_t)R * n));
+        RQ_TRY(rq::alloc(h, &be.bias, (size_t)R));
+        if (h->opts.keep_fp64) {
+            RQ_TRY(rq::alloc(h, &be.Wt64, (size_t)R * R));
+            RQ_TRY(rq::alloc(h, &be.Bop64, (size_t)R * n));
+        }
+    }
+    RQ_TRY(rq::alloc(h, &h->P32, (size_t)n * ldp));
+    RQ_TRY(rq::alloc(h, &h->A32, (size_t)(m > 0 ? m : 1) * ldp));
+    RQ_TRY(rq::alloc(h, &h->At32, (size_t)n * ldt));
+    RQ_TRY(rq::alloc(h, &h->q32, (size_t)n));
+    RQ_TRY(rq::alloc(h, &h->l32, (size_t)(m > 0 ? m : 1)));
+    RQ_TRY(rq::alloc(h, &h->u32, (size_t)(m > 0 ? m : 1)));
+    RQ_TRY(rq::alloc(h, &h->rs32, (size_t)(m > 0 ? m : 1)));
+    RQ_CUDA(h, cudaMemcpy(h->rs32, rs.data(), sizeof(float) * rs.size(), cudaMemcpyHostToDevice));
+    rq::SingleWork& w = h->sw;
+    RQ_TRY(rq::alloc(h, &w.y, (size_t)h->ldw));
+    RQ_TRY(rq::alloc(h, &w.z, (size_t)ldt));
+    RQ_TRY(rq::alloc(h, &w.lam, (size_t)ldt));
+    RQ_TRY(rq::alloc(h, &w.Ay, (size_t)ldt));
+    RQ_TRY(rq::alloc(h, &w.s0, (size_t)h->ldw));
+    RQ_TRY(rq::alloc(h, &w.s1, (size_t)h->ldw));
+    RQ_TRY(rq::alloc(h, &w.Py, (size_t)ldp));
+    RQ_TRY(rq::alloc(h, &w.Axf, (size_t)ldt));
+    RQ_TRY(rq::alloc(h, &w.lstd, (size_t)ldt));
+    RQ_TRY(rq::alloc(h, &w.xin, (size_t)ldp));
+    RQ_TRY(rq::alloc(h, &w.lin, (size_t)ldt));
+    RQ_TRY(rq::alloc(h, &w.red, 3 * 8));
+    RQ_TRY(rq::alloc(h, &w.bar, 2));
+    RQ_TRY(rq::alloc(h, &w.out_i, 8));
+    RQ_TRY(rq::alloc(h, &w.out_f, 8));
+    // FP64 inputs for the offline stage (freed at the end of setup)
+    double *dP = nullptr, *dA = nullptr;
+    cudaError_t e1 = cudaMalloc(&dP, sizeof(double) * n * n);
+    cudaError_t e2 = cudaMalloc(&dA, sizeof(double) * (size_t)(m > 0 ? m : 1) * n);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaFree(dP);
+        cudaFree(dA);
+        cudaGetLastError();
+        return rq::fail(h, RELU_QP_ERR_OOM, "setup: FP64 input allocation failed");
+    }
+    int rc = RELU_QP_OK;
+    if (cudaMemcpy(dP, P, sizeof(double) * n * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (m > 0 && cudaMemcpy(dA, A, sizeof(double) * (size_t)m * n, cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = rq::fail(h, RELU_QP_ERR_CUDA, "setup: FP64 input upload failed");
+    if (rc == RELU_QP_OK) rc = rq::make_check_matrices(h, dP, dA);
+    if (rc == RELU_QP_OK) rc = rq::build_bank(h, dP, dA, row_scale);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(dP);
+    cudaFree(dA);
+    if (rc != RELU_QP_OK) return rc;
+    RQ_TRY(upload_problem(h));
+    RQ_TRY(rq::single_prepare(h));
+    return RELU_QP_OK;
+}
+
+int nearest_index(relu_qp_t h, double rho) {
+    int best = 0;
+    double bd = 1e300;
+    for (int k = 0; k < h->nr; ++k) {
+        const double d = std::fabs(std::log(rho) - std::log(h->bank[k]));
+        if (d < bd) {
+            bd = d;
+            best = k;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+namespace rq {
+
+int fail(relu_qp_t h, int code, const std::string& msg) {
+    if (h)
+        h->err = msg;
+    else
+        g_setup_error = msg;
+    return code;
+}
+
+int dev_alloc(relu_qp_t h, void** p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(h, RELU_QP_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                            " bytes): " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*p);
+    e = cudaMemset(*p, 0, bytes);
+    if (e != cudaSuccess) return fail(h, RELU_QP_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    return RELU_QP_OK;
+}
+
+}  // namespace rq
+
+extern "C" {
+
+void relu_qp_default_opts(relu_qp_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->check_interval = 25;
+    o->adaptive_rho = 1;
+    o->rho0 = 0.1;
+    o->eq_scale = 1e3;
+    o->keep_fp64 = 0;
+    o->max_batch = 0;
+    o->batch_precision = RELU_QP_PREC_FP32;
+    o->stream = nullptr;
+}
+
+int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q, const double* A,
+                  const double* l, const double* u, double sigma, const double* rho_bank, int n_rho,
+                  const relu_qp_opts* opts) {
+    if (out) *out = nullptr;
+    if (!out) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "out is NULL");
+    if (n < 1 || m < 0 || (long)n + m > 40000)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "need 1 <= n and 0 <= m with n + m <= 40000");
+    if (!P || (m > 0 && (!A || !l || !u)) || !rho_bank)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "P, A, l, u and rho_bank are required");
+    if (!(sigma > 0.0) || !std::isfinite(sigma))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "sigma must be finite and > 0");
+    if (n_rho < 1 || n_rho > RQ_MAX_RHO)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "n_rho must be in [1, 16]");
+    for (int r = 0; r < n_rho; ++r)
+        if (!(rho_bank[r] > 0.0) || !std::isfinite(rho_bank[r]))
+            return rq::fail(nullptr, RELU_QP_ERR_INVALID, "rho_bank entries must be finite and > 0");
+    if (!finite_all(P, (size_t)n * n) || (m > 0 && !finite_all(A, (size_t)m * n)) ||
+        (q && !finite_all(q, n)))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "P, q and A must be finite");
+    if (m > 0 && !bounds_ok(l, u, m))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "bounds need l <= u, no NaN, l != +inf, u != -inf");
+    relu_qp_opts o;
+    relu_qp_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.check_interval < 0 || !(o.rho0 > 0.0) || !(o.eq_scale > 0.0))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: check_interval >= 0, rho0 > 0, eq_scale > 0");
+    relu_qp_t h = new (std::nothrow) relu_qp_s;
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_OOM, "host allocation failed");
+    h->n = n;
+    h->m = m;
+    h->R = n + m;
+    h->ldw = (int)rq::round_up(h->R, 4);
+    h->nr = n_rho;
+    h->sigma = sigma;
+    h->opts = o;
+    h->stream = (cudaStream_t)o.stream;
+    h->bank.assign(rho_bank, rho_bank + n_rho);
+    static const double empty = 0.0;
+    const int rc = setup_impl(h, P, q, A, m > 0 ? l : &empty, m > 0 ? u : &empty, rho_bank);
+    if (rc != RELU_QP_OK) {
+        g_setup_error = h->err;
+        relu_qp_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return RELU_QP_OK;
+}
+
+int relu_qp_update(relu_qp_t h, const double* q, const double* l, const double* u) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    const int n = h->n, m = h->m;
+    if (q && !finite_all(q, n)) return rq::fail(h, RELU_QP_ERR_INVALID, "q must be finite");
+    std::vector<double> nl = h->h_l, nu = h->h_u;
+    if (l) nl.assign(l, l + m);
+    if (u) nu.assign(u, u + m);
+    if (m > 0 && !bounds_ok(nl.data(), nu.data(), m))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "bounds need l <= u, no NaN, l != +inf, u != -inf");
+    for (int i = 0; i < m; ++i)
+        if ((nl[i] == nu[i]) != (h->eq[i] != 0))
+            return rq::fail(h, RELU_QP_ERR_INVALID, "the equality-row pattern (l_i == u_i) changed since setup");
+    if (q) std::memcpy(h->h_q.data(), q, sizeof(double) * n);
+    h->h_l = nl;
+    h->h_u = nu;
+    return upload_problem(h);
+}
+
+int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int rho_index_warm,
+                  double eps_abs, double eps_rel, int max_iter, double* x_out, double* z_out,
+                  double* lam_out, relu_qp_info* info) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (!x_out || max_iter < 1 || !(eps_abs >= 0.0) || !(eps_rel >= 0.0) || rho_index_warm < -1 ||
+        rho_index_warm >= h->nr)
+        return rq::fail(h, RELU_QP_ERR_INVALID, "solve: x_out required, max_iter >= 1, eps >= 0, "
+                                                "rho_index_warm in [-1, n_rho)");
+    const int n = h->n, m = h->m;
+    if (x_warm && !finite_all(x_warm, n)) return rq::fail(h, RELU_QP_ERR_INVALID, "x_warm must be finite");
+    if (lam_warm && !finite_all(lam_warm, m)) return rq::fail(h, RELU_QP_ERR_INVALID, "lam_warm must be finite");
+    const int ri = rho_index_warm >= 0 ? rho_index_warm : nearest_index(h, h->opts.rho0);
+    const float* xin = nullptr;
+    const float* lin = nullptr;
+    if (x_warm) {
+        std::vector<float> xf = to_f32(x_warm, n);
+        RQ_CUDA(h, cudaMemcpyAsync(h->sw.xin, xf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+        xin = h->sw.xin;
+        if (lam_warm && m > 0) {
+            std::vector<float> lf = to_f32(lam_warm, m);
+            RQ_CUDA(h, cudaMemcpyAsync(h->sw.lin, lf.data(), sizeof(float) * m, cudaMemcpyHostToDevice,
+                                       h->stream));
+            lin = h->sw.lin;
+        }
+        RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    relu_qp_info inf{};
+    RQ_TRY(rq::single_solve(h, xin, lin, ri, eps_abs, eps_rel, max_iter, &inf));
+    std::vector<float> buf((size_t)(n > m ? n : m));
+    RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.y, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i) x_out[i] = buf[i];
+    if (z_out && m > 0) {
+        RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.z, sizeof(float) * m, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < m; ++i) z_out[i] = buf[i];
+    }
+    if (lam_out && m > 0) {
+        RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.lstd, sizeof(float) * m, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < m; ++i) lam_out[i] = buf[i];
+    }
+    if (info) *info = inf;
+    return RELU_QP_OK;
+}
+
+int relu_qp_get_layer(relu_qp_t h, int rho_index, double* Wt, double* Bop) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (rho_index < 0 || rho_index >= h->nr) return rq::fail(h, RELU_QP_ERR_INVALID, "rho_index out of range");
+    const int n = h->n, R = h->R;
+    const rq::BankEntry& be = h->be[rho_index];
+    if (Wt) {
+        if (be.Wt64) {
+            RQ_CUDA(h, cudaMemcpy(Wt, be.Wt64, sizeof(double) * R * R, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f((size_t)R * R);
+            RQ_CUDA(h, cudaMemcpy2D(f.data(), sizeof(float) * R, be.Wt, sizeof(float) * h->ldw, sizeof(float) * R,
+                                    R, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < f.size(); ++i) Wt[i] = f[i];
+        }
+    }
+    if (Bop) {
+        if (be.Bop64) {
+            RQ_CUDA(h, cudaMemcpy(Bop, be.Bop64, sizeof(double) * R * n, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f((size_t)R * n);
+            RQ_CUDA(h, cudaMemcpy(f.data(), be.Bop, sizeof(float) * R * n, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < f.size(); ++i) Bop[i] = f[i];
+        }
+    }
+    return RELU_QP_OK;
+}
+
+int relu_qp_set_opts(relu_qp_t h, const relu_qp_opts* opts) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (!opts || opts->check_interval < 0 || !(opts->rho0 > 0.0))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "opts: check_interval >= 0, rho0 > 0");
+    h->opts.check_interval = opts->check_interval;
+    h->opts.adaptive_rho = opts->adaptive_rho;
+    h->opts.rho0 = opts->rho0;
+    return RELU_QP_OK;
+}
+
+int relu_qp_dims(relu_qp_t h, int* n, int* m, int* n_rho) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (n) *n = h->n;
+    if (m) *m = h->m;
+    if (n_rho) *n_rho = h->nr;
+    return RELU_QP_OK;
+}
+
+void relu_qp_destroy(relu_qp_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+const char* relu_qp_last_error(relu_qp_t h) {
+    return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,121 @@
+// Internal declarations shared by the translation units of librelu_qp.so.
+// Nothing here is part of the public ABI (include/relu_qp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/relu_qp.h"
+
+#define RQ_MAX_RHO 16
+
+namespace rq {
+
+// ---------------------------------------------------------------------------
+// error plumbing: every CUDA call on the host goes through RQ_CUDA, which
+// records a message on the handle and returns RELU_QP_ERR_CUDA.
+// ---------------------------------------------------------------------------
+struct Status {
+    int code = RELU_QP_OK;
+    std::string msg;
+};
+
+#define RQ_CUDA(h, call)                                                              \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            cudaGetLastError();                                                       \
+            return ::rq::fail((h), e_ == cudaErrorMemoryAllocation ? RELU_QP_ERR_OOM  \
+                                                                  : RELU_QP_ERR_CUDA, \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));    \
+        }                                                                             \
+    } while (0)
+
+#define RQ_TRY(expr)                    \
+    do {                                \
+        int rc_ = (expr);               \
+        if (rc_ != RELU_QP_OK) return rc_; \
+    } while (0)
+
+// Device buffer owned by a handle.
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+// Per-bank-entry device data.
+struct BankEntry {
+    double rho = 0.0;
+    float* Wt = nullptr;      // R x ldw FP32, rows [x; Ax], cols [x; 2 rho z - lam'] (padded)
+    float* Bop = nullptr;     // R x n FP32: [-D; -A D]
+    float* bias = nullptr;    // R FP32 = Bop q (single-QP path)
+    double* Wt64 = nullptr;   // R x R FP64 (keep_fp64 only)
+    double* Bop64 = nullptr;  // R x n FP64 (keep_fp64 only)
+};
+
+// Workspace of the single-QP cooperative solve.
+struct SingleWork {
+    float *y = nullptr, *z = nullptr, *lam = nullptr, *Ay = nullptr;
+    float *s0 = nullptr, *s1 = nullptr;
+    float *Py = nullptr, *Axf = nullptr, *lstd = nullptr;
+    float* xin = nullptr;       // warm-start x (FP32)
+    float* lin = nullptr;       // warm-start lam (FP32)
+    unsigned* red = nullptr;    // 3 slots x 8 reduction words
+    unsigned* bar = nullptr;    // grid barrier [count, generation]
+    int* out_i = nullptr;       // status, iters, rho_index, switches, err
+    float* out_f = nullptr;     // r_prim, r_dual
+    int grid = 0;               // CTAs of the cooperative launch (autotuned)
+    int cached_rows = 0;        // rows of W each CTA keeps in shared memory
+    int rows_per_cta = 0;
+};
+
+}  // namespace rq
+
+struct relu_qp_s {
+    int n = 0, m = 0, R = 0, ldw = 0, nr = 0;
+    double sigma = 0.0;
+    relu_qp_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    std::vector<double> bank;
+    std::vector<double> h_q, h_l, h_u;      // current problem data (host FP64)
+    std::vector<unsigned char> eq;         // equality-row pattern fixed at setup
+    rq::BankEntry be[RQ_MAX_RHO];
+    float *P32 = nullptr, *A32 = nullptr, *At32 = nullptr;   // check matrices (FP32)
+    float *q32 = nullptr, *l32 = nullptr, *u32 = nullptr, *rs32 = nullptr;
+    double qnorm = 0.0;
+    rq::SingleWork sw;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+    std::vector<void*> allocs;               // every cudaMalloc of the handle
+};
+
+namespace rq {
+
+int fail(relu_qp_t h, int code, const std::string& msg);
+int dev_alloc(relu_qp_t h, void** p, size_t bytes);
+
+template <typename T>
+int alloc(relu_qp_t h, T** p, size_t count) {
+    return dev_alloc(h, reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+// FP64 setup (setup_fp64.cu): builds every bank entry of h from P, A (device FP64).
+int build_bank(relu_qp_t h, const double* dP, const double* dA, const std::vector<double>& rho_rows_scale);
+// FP32 copies of P, A, A^T from FP64 device arrays (setup_fp64.cu).
+int make_check_matrices(relu_qp_t h, const double* dP, const double* dA);
+// b_r = Bop_r q for every bank entry (single_solve.cu).
+int compute_bias(relu_qp_t h);
+// Cooperative single-QP solve (single_solve.cu).
+int single_solve(relu_qp_t h, const float* x_warm_dev, const float* lam_warm_dev, int rho_index,
+                 double eps_abs, double eps_rel, int max_iter, relu_qp_info* info);
+int single_prepare(relu_qp_t h);
+
+inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace rq
