@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""QP solves/s at eps_abs = 1e-3 for batched condensed-MPC QPs on GB300.
+
+Workload (one step): a batch of B = 1024 QPs of the condensed, LQR-
+preconditioned MPC problem with nx = 60, nu = 20, N = 40 (n = m = 800) that
+share P and A (one bank of layers, rho in {0.1, 1, 10}) and each have their
+own initial state x0 (hence q, l, u).  A step is the whole online path:
+x0 -> (q, l, u, b) update, Algorithm 1 to eps_abs = 1e-3 for every QP
+(layers, checks every 25 layers, penalty rule, regrouping) and the outputs.
+The offline stage (FP64 factorisation and layer bank) runs once before
+timing.  Inputs are synthetic and seeded (workloads/mpc.py).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QP solves/s at eps=1e-3 (batched BF16-split, one GB300)"
+UNIT = "QP solves/s"
+SIGMA = 1e-6
+BANK = (0.1, 1.0, 10.0)
+EPS = 1e-3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-extras", action="store_true", help="skip the FP32 comparison arms")
+    return ap.parse_args()
+
+
+def workload_config(B, x0_std, precision):
+    return {
+        "workload": (f"batched condensed MPC nx=60 nu=20 N=40 (n=m=800), {B} QPs per step sharing one layer "
+                     f"bank, own x0 ~ N(0, {x0_std:.3g}^2), eps_abs=1e-3, rho bank {list(BANK)}, sigma 1e-6"),
+        "batch": B, "n": 800, "m": 800, "precision": precision, "check_interval": 25,
+        "l2": "flushed (256 MiB write) before every timed step",
+    }
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample
+# ---------------------------------------------------------------------------
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_oracle(pq, X0, seconds):
+    from oracle import relu_qp_oracle as O
+    l0, u0 = pq.l0, pq.u0
+    weights = [O.relu_layer_weights(pq.P, pq.A, SIGMA, O.rho_vector(l0, u0, r)) for r in BANK]
+    done = 0
+    t0 = time.perf_counter()
+    iters = []
+    for x0 in X0:
+        q, l, u = pq.instance(x0)
+        r = O.solve(pq.P, q, pq.A, l, u, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS, weights=weights)
+        iters.append(r.iters)
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, iters
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "samples": len(rows),
+                "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d.get("bf16_tflops_sustained", 1700.0)), float(d.get("bf16_tflops", 1900.0)), "measured"
+    return 1700.0, 1900.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("batch_tc.cu", "batch.h"):
+        h.update(open(os.path.join(ROOT, "paper_2311_18056_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the refined tensor-core layer from the committed
+    ncu summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "tc_layer_refined_batched_n800.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; weak scaling, no data collective)
+# ---------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    """The oracle (FP64 NumPy, as it stands) on the host cores, same metric."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from workloads import mpc
+    pq, _, x0_std = mpc.workload("batched", 1)
+    per_step = 2
+    X0 = mpc.initial_states(pq.nx, per_step * (args.steps + args.warmup), 2, sub_id=7, std=x0_std)
+    from oracle import relu_qp_oracle as O
+    weights = [O.relu_layer_weights(pq.P, pq.A, SIGMA, O.rho_vector(pq.l0, pq.u0, r)) for r in BANK]
+    times = []
+    k = 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            q, l, u = pq.instance(X0[k])
+            k += 1
+            O.solve(pq.P, q, pq.A, l, u, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS, weights=weights)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * len(times) / total
+    cores = blas_threads()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(per_step, x0_std, "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} QPs per step of the batched workload (n=m=800), FP64 NumPy"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2311_18056_gb300 as rq
+    from paper_2311_18056_gb300 import build as _build
+    _build.build()
+    from workloads import mpc
+
+    pq, _, x0_std = mpc.workload("batched", 1)
+    B, K, W = args.batch, args.steps, args.warmup
+    prec = rq.PREC_BF16X3 if args.precision == "bf16x3" else rq.PREC_FP32
+    # per-step initial states: distinct seeded batches per rank and step
+    X0_host = [mpc.initial_states(pq.nx, B, 2, sub_id=1000 + 97 * rank + k, std=x0_std).astype(np.float32)
+               for k in range(W + K)]
+    X0_dev = [torch.from_numpy(x).to(dev) for x in X0_host]
+    q0, l0, u0 = pq.instance(X0_host[0][0].astype(np.float64))
+    solver = rq.ReluQP(pq.P, pq.A, l0, u0, q=q0, sigma=SIGMA, rho_bank=BANK, max_batch=B, precision=prec)
+    solver.set_parametric(pq.F, pq.E, pq.l0, pq.u0)
+    Xo = torch.empty((B, pq.n), dtype=torch.float32, device=dev)
+    Zo = torch.empty((B, pq.m), dtype=torch.float32, device=dev)
+    Lo = torch.empty((B, pq.m), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def step(X0):
+        solver.update_batch_x0(X0)
+        return solver.solve_batch(eps_abs=EPS, max_iter=4000, out=(Xo, Zo, Lo))
+
+    for k in range(W):
+        step(X0_dev[k])
+    torch.cuda.synchronize()
+    solver.profile(enable=1, reset=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    unsolved, iters = 0, []
+    for k in range(K):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        out = step(X0_dev[W + k])
+        ev[k][1].record()
+        unsolved += int(np.sum(out["status"] != rq.SOLVED))
+        iters.append(out["iters"])
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    prof = solver.profile(enable=0)
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    t_total = max_over_ranks(world, float(step_ms.sum()) / 1e3)
+    solves = sum_over_ranks(world, B * K)
+    value = solves / t_total
+
+    # ---- end to end through the C ABI with host (pinned) buffers ----
+    X0_pin = [torch.from_numpy(x).pin_memory() for x in X0_host[W:W + K]]
+    Xh = torch.empty((B, pq.n), dtype=torch.float32).pin_memory()
+    Zh = torch.empty((B, pq.m), dtype=torch.float32).pin_memory()
+    Lh = torch.empty((B, pq.m), dtype=torch.float32).pin_memory()
+    solver.update_batch_x0(X0_pin[0])
+    solver.solve_batch(eps_abs=EPS, out=(Xh, Zh, Lh))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(K):
+        solver.update_batch_x0(X0_pin[k])
+        solver.solve_batch(eps_abs=EPS, out=(Xh, Zh, Lh))
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": solves / t_e2e, "unit": UNIT, "h2d_bytes_per_step": B * pq.nx * 4,
+           "d2h_bytes_per_step": B * (pq.n + 2 * pq.m) * 4 + B * 40}
+
+    # ---- roofline of the dominant kernel (tensor-core refined layer) ----
+    peak_sus, peak_burst, peak_kind = measured_peaks()
+    roof = None
+    if prof["layer_timed"] > 0 and prof["layer_ms"] > 0:
+        flops_per_launch = prof["layer_flops"] / max(prof["layer_launches"], 1)
+        achieved = prof["layer_flops"] / (prof["layer_ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
+                "frac": achieved / peak_sus, "traffic": profiled_traffic(),
+                "kernel": "tc_gemm_kernel refined layer (3 BF16 products, FP32 accumulate in TMEM)",
+                "peak_kind": f"bf16 sustained, {peak_kind}",
+                "launches_timed": prof["layer_timed"], "avg_launch_us": 1e3 * prof["layer_ms"] / prof["layer_timed"],
+                "flops_per_launch": flops_per_launch}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if prec == rq.PREC_BF16X3 else "f32", "data": "synthetic",
+            "config": workload_config(B, x0_std, args.precision),
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "unsolved": unsolved, "mean_iters": float(np.mean(np.concatenate(iters))),
+            "e2e": e2e, "roofline": roof, "clocks": clk, "gpu_launches": int(prof["launches"])}
+
+    # ---- comparison arms on the same GPU (rank 0, N = 1): plain FP32 ----
+    if rank == 0 and world == 1 and not args.skip_extras:
+        extras = {}
+        s32 = rq.ReluQP(pq.P, pq.A, l0, u0, q=q0, sigma=SIGMA, rho_bank=BANK, max_batch=B, precision=rq.PREC_FP32)
+        s32.set_parametric(pq.F, pq.E, pq.l0, pq.u0)
+        s32.update_batch_x0(X0_dev[0])
+        s32.solve_batch(eps_abs=EPS, out=(Xo, Zo, Lo))
+        tt = []
+        for k in range(2):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s32.update_batch_x0(X0_dev[W + k])
+            s32.solve_batch(eps_abs=EPS, out=(Xo, Zo, Lo))
+            b.record()
+            torch.cuda.synchronize()
+            tt.append(a.elapsed_time(b))
+        s32.close()
+        extras["fp32_batched_solves_per_s"] = B / (np.mean(tt) / 1e3)
+        single = rq.ReluQP(pq.P, pq.A, l0, u0, q=q0, sigma=SIGMA, rho_bank=BANK)
+        Xs = X0_host[W][:48].astype(np.float64)
+        single.update(*pq.instance(Xs[0]))
+        single.solve(eps_abs=EPS)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat = []
+        for x0 in Xs:
+            single.update(*pq.instance(x0))
+            r = single.solve(eps_abs=EPS)
+            lat.append(r["solve_ms"])
+        t_single = time.perf_counter() - t0
+        single.close()
+        extras["fp32_single_solves_per_s"] = len(Xs) / t_single
+        extras["fp32_single_p50_ms"] = float(np.percentile(lat, 50))
+        extras["fp32_single_p99_ms"] = float(np.percentile(lat, 99))
+        extras["speedup_vs_fp32_single"] = value / extras["fp32_single_solves_per_s"]
+        extras["speedup_vs_fp32_batched"] = value / extras["fp32_batched_solves_per_s"]
+        line["comparison"] = extras
+    solver.close()
+
+    if rank == 0 and world == 1:
+        X0c = mpc.initial_states(pq.nx, 200, 2, sub_id=5000, std=x0_std)
+        done, dt, it = cpu_oracle(pq, X0c, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": done / dt, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": f"{done} QPs of the batched workload solved one by one by the FP64 "
+                                          f"NumPy oracle in {dt:.1f} s (mean {np.mean(it):.0f} layers)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

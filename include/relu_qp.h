@@ -154,6 +154,73 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
  */
 int relu_qp_get_layer(relu_qp_t h, int rho_index, double* Wt, double* Bop);
 
+/*
+ * ---- batched QPs --------------------------------------------------------
+ * A handle set up with opts.max_batch = Bmax > 0 also solves up to Bmax QPs
+ * at once that share P and A (hence every layer of the bank) but have their
+ * own q, l, u, warm start and penalty index.  Each layer is then one GEMM
+ * over the batch (tcgen05 tensor cores with BF16 hi+lo split operands and
+ * FP32 accumulation when opts.batch_precision = RELU_QP_PREC_BF16X3, FP32
+ * CUDA cores otherwise), checks run per QP, converged QPs leave the batch,
+ * and the rest are regrouped by bank entry after every check.
+ *
+ * Array arguments of the batched calls are row-major FP32 (B rows) and may
+ * be host memory (pageable or pinned) or device memory; the library copies
+ * through cudaMemcpyDefault.  Rows with l_i == u_i at setup must stay
+ * equality rows (and the others inequality rows) in every QP of a batch.
+ */
+
+/* Per-QP problem data: Q (B x n), L and U (B x m).  1 <= B <= max_batch.
+ * Recomputes b_r = [-D_r; -A D_r] q for every bank entry and QP.
+ * Errors: INVALID, UNSUPPORTED (max_batch = 0), CUDA. */
+int relu_qp_update_batch(relu_qp_t h, int B, const float* Q, const float* L, const float* U);
+
+/* Parametric form of the problem data for MPC (condensed form, paper Sec. IV):
+ * q = F x0, l = l0 - E x0, u = u0 - E x0 with F (n x nx), E (m x nx) FP64 and
+ * l0, u0 (m) FP64.  Precomputes [-D_r; -A D_r] F for every bank entry so that
+ * a batch update costs O((n + m) nx) per QP.  Errors: INVALID, UNSUPPORTED. */
+int relu_qp_set_parametric(relu_qp_t h, int nx, const double* F, const double* E, const double* l0,
+                           const double* u0);
+
+/* Per-QP initial states X0 (B x nx FP32) for the parametric form ("update b,
+ * c~, d~ with initial conditions", Algorithm 1).  Errors: INVALID, UNSUPPORTED. */
+int relu_qp_update_batch_x0(relu_qp_t h, int B, const float* X0);
+
+/*
+ * relu_qp_solve_batch -- Algorithm 1 for the first B QPs of the last batch update.
+ *   X_warm (B x n), Lam_warm (B x m), rho_warm (B, bank indices): warm start
+ *     (z = A x_warm); NULL = cold start (rho_warm needs X_warm)
+ *   eps_abs, eps_rel, max_iter: as relu_qp_solve, applied per QP
+ *   X_out (B x n, required), Z_out, Lam_out (B x m, may be NULL): the iterate
+ *     of each QP at its stop (Lam_out is the standard multiplier)
+ *   infos: B entries (may be NULL); solve_ms is the time of the whole batch
+ * Errors: INVALID, UNSUPPORTED, CUDA, TIMEOUT (a device wait passed its deadline).
+ */
+int relu_qp_solve_batch(relu_qp_t h, int B, const float* X_warm, const float* Lam_warm, const int* rho_warm,
+                        double eps_abs, double eps_rel, int max_iter, float* X_out, float* Z_out,
+                        float* Lam_out, relu_qp_info* infos);
+
+/*
+ * Kernel-level counters of a handle, for benchmarks.  `launches` counts every
+ * kernel the solve and update paths launched; `layer_*` cover the dominant
+ * kernel of a batched solve (the tensor-core refined layer in the BF16 form,
+ * the FP32 layer otherwise): its launches, the algorithmic FLOPs they did
+ * (2 x products x (n+m)^2 per active QP) and, while profiling is enabled,
+ * their device time from CUDA events recorded on the handle's stream around
+ * each launch (up to 8192 launches per solve are timed).
+ */
+typedef struct relu_qp_prof {
+    long long launches;
+    long long layer_launches;
+    long long layer_timed;
+    double layer_ms;
+    double layer_flops;
+} relu_qp_prof;
+
+/* Read the counters into *out (may be NULL), then reset them if `reset`, then
+ * turn event timing on (enable = 1) or off (0) or leave it (-1). */
+int relu_qp_profile(relu_qp_t h, int enable, int reset, relu_qp_prof* out);
+
 /* Change check_interval / adaptive_rho / rho0 of an existing handle
  * (other fields of opts are ignored).  Errors: INVALID. */
 int relu_qp_set_opts(relu_qp_t h, const relu_qp_opts* opts);

@@ -33,6 +33,11 @@ class Opts(ctypes.Structure):
                 ("batch_precision", _c_int), ("stream", _c_void_p)]
 
 
+class Prof(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("layer_launches", ctypes.c_longlong),
+                ("layer_timed", ctypes.c_longlong), ("layer_ms", _c_double), ("layer_flops", _c_double)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("status", _c_int), ("iters", _c_int), ("rho_index", _c_int), ("rho_switches", _c_int),
                 ("r_prim", _c_double), ("r_dual", _c_double), ("solve_ms", _c_double)]
@@ -53,6 +58,12 @@ _SIGNATURES = {
     "relu_qp_set_opts": (_c_int, [_c_void_p, ctypes.POINTER(Opts)]),
     "relu_qp_dims": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
                               ctypes.POINTER(_c_int)]),
+    "relu_qp_update_batch": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p]),
+    "relu_qp_set_parametric": (_c_int, [_c_void_p, _c_int, _dp, _dp, _dp, _dp]),
+    "relu_qp_update_batch_x0": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "relu_qp_solve_batch": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_int,
+                                     _c_void_p, _c_void_p, _c_void_p, ctypes.POINTER(Info)]),
+    "relu_qp_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(Prof)]),
     "relu_qp_destroy": (None, [_c_void_p]),
     "relu_qp_last_error": (ctypes.c_char_p, [_c_void_p]),
 }
@@ -95,6 +106,22 @@ def _f64(a, shape=None):
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _buf(a, dtype, shape):
+    """(pointer, keep-alive) for a host NumPy array or a CUDA torch tensor of the given shape."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        want = torch.float32 if dtype == np.float32 else torch.int32
+        if a.dtype != want or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"expected a contiguous {want} tensor of shape {shape}, got {a.dtype} {tuple(a.shape)}")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if arr.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape}, got {arr.shape}")
+    return arr.ctypes.data, arr
 
 
 def _stream_handle(stream):
@@ -186,6 +213,66 @@ class ReluQP:
         out = info.as_dict()
         out.update(x=x, z=z, lam=lam)
         return out
+
+    # -- batched QPs (same P, A; own q, l, u) -------------------------------
+    def update_batch(self, Q, L=None, U=None):
+        """Per-QP data: Q (B, n), L and U (B, m), FP32, host arrays or CUDA tensors."""
+        B = int(Q.shape[0])
+        q, kq = _buf(Q, np.float32, (B, self.n))
+        l, kl = _buf(L, np.float32, (B, self.m)) if self.m else (None, None)
+        u, ku = _buf(U, np.float32, (B, self.m)) if self.m else (None, None)
+        self._check(lib().relu_qp_update_batch(self._h, B, q, l, u))
+        self._batch = B
+
+    def set_parametric(self, F, E, l0, u0):
+        """q = F x0, l = l0 - E x0, u = u0 - E x0 for the x0-driven batched updates."""
+        F = _f64(F)
+        nx = F.shape[1]
+        E = _f64(E, (self.m, nx)) if self.m else None
+        l0 = _f64(l0, (self.m,)) if self.m else None
+        u0 = _f64(u0, (self.m,)) if self.m else None
+        self._check(lib().relu_qp_set_parametric(self._h, nx, _ptr(F), _ptr(E), _ptr(l0), _ptr(u0)))
+        self.nx = nx
+
+    def update_batch_x0(self, X0):
+        B = int(X0.shape[0])
+        x, kx = _buf(X0, np.float32, (B, self.nx))
+        self._check(lib().relu_qp_update_batch_x0(self._h, B, x))
+        self._batch = B
+
+    def solve_batch(self, B=None, X_warm=None, Lam_warm=None, rho_warm=None, eps_abs=1e-3, eps_rel=0.0,
+                    max_iter=4000, out=None, infos=True):
+        """Solve the first B QPs of the last update.  Outputs go to `out` = (X, Z, Lam)
+        (CUDA tensors or host arrays) or to new host arrays."""
+        B = self._batch if B is None else int(B)
+        xw, kxw = _buf(X_warm, np.float32, (B, self.n))
+        lw, klw = _buf(Lam_warm, np.float32, (B, self.m)) if self.m else (None, None)
+        rw, krw = _buf(rho_warm, np.int32, (B,))
+        if out is None:
+            out = (np.empty((B, self.n), np.float32), np.empty((B, self.m), np.float32),
+                   np.empty((B, self.m), np.float32))
+        xo, kxo = _buf(out[0], np.float32, (B, self.n))
+        zo, kzo = _buf(out[1], np.float32, (B, self.m)) if self.m and out[1] is not None else (None, None)
+        lo, klo = _buf(out[2], np.float32, (B, self.m)) if self.m and out[2] is not None else (None, None)
+        inf = (Info * B)() if infos else None
+        self._check(lib().relu_qp_solve_batch(self._h, B, xw, lw, rw, float(eps_abs), float(eps_rel), int(max_iter),
+                                              xo, zo, lo, inf))
+        res = {"x": out[0], "z": out[1], "lam": out[2]}
+        if infos:
+            res["status"] = np.array([i.status for i in inf])
+            res["iters"] = np.array([i.iters for i in inf])
+            res["rho_index"] = np.array([i.rho_index for i in inf])
+            res["rho_switches"] = np.array([i.rho_switches for i in inf])
+            res["r_prim"] = np.array([i.r_prim for i in inf])
+            res["r_dual"] = np.array([i.r_dual for i in inf])
+            res["solve_ms"] = inf[0].solve_ms if B else 0.0
+        return res
+
+    def profile(self, enable=-1, reset=False):
+        """Counters of relu_qp_profile as a dict; enable: 1 on, 0 off, -1 unchanged."""
+        pr = Prof()
+        self._check(lib().relu_qp_profile(self._h, int(enable), int(bool(reset)), ctypes.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in pr._fields_}
 
     def get_layer(self, rho_index):
         R = self.n + self.m

@@ -49,7 +49,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I",
-                     os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
+                     os.path.join(ROOT, "include"), "--expt-relaxed-constexpr",
+                     "-diag-suppress", "177"]
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

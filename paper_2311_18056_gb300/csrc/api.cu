@@ -103,6 +103,7 @@ int setup_impl(relu_qp_t h, const double* P, const double* q, const double* A, c
     RQ_TRY(rq::alloc(h, &w.bar, 2));
     RQ_TRY(rq::alloc(h, &w.out_i, 8));
     RQ_TRY(rq::alloc(h, &w.out_f, 8));
+    if (h->opts.max_batch > 0) RQ_TRY(rq::batch_alloc(h));
     // FP64 inputs for the offline stage (freed at the end of setup)
     double *dP = nullptr, *dA = nullptr;
     cudaError_t e1 = cudaMalloc(&dP, sizeof(double) * n * n);
@@ -119,12 +120,16 @@ int setup_impl(relu_qp_t h, const double* P, const double* q, const double* A, c
         rc = rq::fail(h, RELU_QP_ERR_CUDA, "setup: FP64 input upload failed");
     if (rc == RELU_QP_OK) rc = rq::make_check_matrices(h, dP, dA);
     if (rc == RELU_QP_OK) rc = rq::build_bank(h, dP, dA, row_scale);
+    if (rc == RELU_QP_OK && h->bw.cap > 0 && h->bw.prec == RELU_QP_PREC_BF16X3)
+        rc = rq::pack_bf16_check(h, dP, dA);
     cudaStreamSynchronize(h->stream);
     cudaFree(dP);
     cudaFree(dA);
     if (rc != RELU_QP_OK) return rc;
     RQ_TRY(upload_problem(h));
     RQ_TRY(rq::single_prepare(h));
+    if (h->bw.cap > 0) RQ_TRY(rq::batch_finish_setup(h));
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return RELU_QP_OK;
 }
 
@@ -211,12 +216,15 @@ int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q
     if (opts) o = *opts;
     if (o.check_interval < 0 || !(o.rho0 > 0.0) || !(o.eq_scale > 0.0))
         return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: check_interval >= 0, rho0 > 0, eq_scale > 0");
+    if (o.max_batch < 0 || o.max_batch > (1 << 20) ||
+        (o.batch_precision != RELU_QP_PREC_FP32 && o.batch_precision != RELU_QP_PREC_BF16X3))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: 0 <= max_batch <= 2^20, batch_precision FP32 or BF16X3");
     relu_qp_t h = new (std::nothrow) relu_qp_s;
     if (!h) return rq::fail(nullptr, RELU_QP_ERR_OOM, "host allocation failed");
     h->n = n;
     h->m = m;
     h->R = n + m;
-    h->ldw = (int)rq::round_up(h->R, 4);
+    h->ldw = (int)rq::round_up(h->R, 64);
     h->nr = n_rho;
     h->sigma = sigma;
     h->opts = o;
@@ -343,10 +351,81 @@ void relu_qp_destroy(relu_qp_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    rq::batch_release(h);
+    for (cudaEvent_t e : h->prof_ev)
+        if (e) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;
+}
+
+int relu_qp_update_batch(relu_qp_t h, int B, const float* Q, const float* L, const float* U) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (h->bw.cap <= 0) return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "handle was set up with max_batch = 0");
+    if (B < 1 || B > h->bw.cap || !Q || (h->m > 0 && (!L || !U)))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "update_batch: 1 <= B <= max_batch; Q, L, U required");
+    return rq::batch_update(h, B, Q, L, U);
+}
+
+int relu_qp_set_parametric(relu_qp_t h, int nx, const double* F, const double* E, const double* l0,
+                           const double* u0) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (h->bw.cap <= 0) return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "handle was set up with max_batch = 0");
+    if (nx < 1 || nx > 4096 || !F || (h->m > 0 && (!E || !l0 || !u0)))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "set_parametric: 1 <= nx <= 4096; F, E, l0, u0 required");
+    if (!finite_all(F, (size_t)h->n * nx) || (h->m > 0 && !finite_all(E, (size_t)h->m * nx)))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "F and E must be finite");
+    if (h->m > 0 && !bounds_ok(l0, u0, h->m))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "bounds need l0 <= u0, no NaN, l0 != +inf, u0 != -inf");
+    for (int i = 0; i < h->m; ++i)
+        if ((l0[i] == u0[i]) != (h->eq[i] != 0))
+            return rq::fail(h, RELU_QP_ERR_INVALID, "the equality-row pattern (l_i == u_i) differs from setup");
+    return rq::batch_set_parametric(h, nx, F, E, l0, u0);
+}
+
+int relu_qp_update_batch_x0(relu_qp_t h, int B, const float* X0) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (h->bw.cap <= 0 || h->bw.nx <= 0)
+        return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "needs max_batch > 0 and relu_qp_set_parametric first");
+    if (B < 1 || B > h->bw.cap || !X0) return rq::fail(h, RELU_QP_ERR_INVALID, "update_batch_x0: 1 <= B <= max_batch");
+    return rq::batch_update_x0(h, B, X0);
+}
+
+int relu_qp_solve_batch(relu_qp_t h, int B, const float* X_warm, const float* Lam_warm, const int* rho_warm,
+                        double eps_abs, double eps_rel, int max_iter, float* X_out, float* Z_out, float* Lam_out,
+                        relu_qp_info* infos) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (h->bw.cap <= 0) return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "handle was set up with max_batch = 0");
+    if (B < 1 || B > h->bw.B || !X_out || max_iter < 1 || !(eps_abs >= 0.0) || !(eps_rel >= 0.0))
+        return rq::fail(h, RELU_QP_ERR_INVALID,
+                        "solve_batch: 1 <= B <= the last update's batch, X_out required, max_iter >= 1, eps >= 0");
+    if (rho_warm && !X_warm) return rq::fail(h, RELU_QP_ERR_INVALID, "rho_warm needs X_warm");
+    return rq::batch_solve(h, B, X_warm, Lam_warm, rho_warm, eps_abs, eps_rel, max_iter, X_out, Z_out, Lam_out,
+                           infos);
+}
+
+int relu_qp_profile(relu_qp_t h, int enable, int reset, relu_qp_prof* out) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (out) {
+        out->launches = h->launches;
+        out->layer_launches = h->layer_launches;
+        out->layer_timed = h->layer_timed;
+        out->layer_ms = h->layer_ms;
+        out->layer_flops = h->layer_flops;
+    }
+    if (reset) {
+        h->launches = h->layer_launches = h->layer_timed = 0;
+        h->layer_ms = h->layer_flops = 0.0;
+    }
+    if (enable >= 0) {
+        if (enable && h->prof_ev.empty()) {
+            h->prof_ev.resize(2 * 8192, nullptr);
+            for (auto& e : h->prof_ev) RQ_CUDA(h, cudaEventCreate(&e));
+        }
+        h->prof_on = enable ? 1 : 0;
+    }
+    return RELU_QP_OK;
 }
 
 const char* relu_qp_last_error(relu_qp_t h) {

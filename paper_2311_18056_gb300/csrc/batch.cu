@@ -1,0 +1,854 @@
+// Batched online stage of Algorithm 1: B QPs sharing P and A (so every W_rho
+// of the bank) with their own q, l, u, warm start and penalty index.
+//
+// One chunk = check_interval layers (25 by default, Sec. III-C).  Every layer
+// is one GEMM over the active slots with the element-wise layer in its
+// epilogue (batch.h).  At the end of a chunk the residuals of Eqs. primal and
+// dual are formed per QP, the decision kernel applies the stop test and the
+// penalty rule of Eq. rho_update (nearest bank entry, Sec. III-C), converged
+// QPs leave the batch, and the rest are regrouped so that a 128-slot tile
+// holds QPs of one bank entry only.  The host reads one counter per chunk.
+//
+// Backends: FP32 on the CUDA cores (this file) and BF16 hi+lo split operands
+// on the tcgen05 tensor cores (batch_tc.cu) with FP32 accumulation.  In the
+// split form the first layer of a chunk is an accurate (3-way split) product
+// that stores c = Wt s_ref + b, and the other layers apply the 2-way split
+// only to the increment: t = c + Wt (s - s_ref).
+#include "batch.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace rq {
+
+namespace {
+
+struct W32Ptrs {
+    const float* w[RQ_MAX_RHO];
+};
+
+// C[i][j] = alpha * sum_k X[i][k] W[j][k] + (off ? off[j] : 0), bounds-checked
+// (problem updates; not on the per-layer path).
+__global__ void __launch_bounds__(256) sgemm_nt_kernel(int M, int N, int K, const float* __restrict__ X, int ldx,
+                                                       const float* __restrict__ W, int ldw, float alpha,
+                                                       const float* __restrict__ off, float* __restrict__ C,
+                                                       int ldc) {
+    __shared__ float Xs[16][64 + 4];
+    __shared__ float Ws[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < 1024; e += 256) {
+            const int row = e >> 4, k = e & 15;
+            const int gi = i0 + row, gj = j0 + row, gk = k0 + k;
+            Xs[k][row] = (gi < M && gk < K) ? X[(size_t)gi * ldx + gk] : 0.f;
+            Ws[k][row] = (gj < N && gk < K) ? W[(size_t)gj * ldw + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                a[t] = Xs[k][ty + 16 * t];
+                b[t] = Ws[k][tx + 16 * t];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty + 16 * u;
+        if (i >= M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = j0 + tx + 16 * v;
+            if (j >= N) continue;
+            C[(size_t)i * ldc + j] = alpha * acc[u][v] + (off ? off[j] : 0.f);
+        }
+    }
+}
+
+// Shared main loop of the FP32 batched kernels: a 128-slot x 64-row tile of
+// sum_k X[slot, k] W[row, k] over k in [kbeg, kend) (rows of X and W have
+// leading dimension ld, zero padded to a multiple of 64); each thread
+// accumulates 8 slots x 4 rows.
+__device__ __forceinline__ void fp32_tile(const float* __restrict__ X, const float* __restrict__ W, int ld,
+                                          int kbeg, int kend, int nrows, int slot0, int row0, float (&acc)[8][4]) {
+    __shared__ __align__(16) float Xs[16][128 + 4];
+    __shared__ __align__(16) float Ws[16][64 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = kbeg; k0 < kend; k0 += 16) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int row = e >> 2, kq = (e & 3) * 4;
+            const float4 v = *reinterpret_cast<const float4*>(X + (size_t)(slot0 + row) * ld + k0 + kq);
+            Xs[kq + 0][row] = v.x;
+            Xs[kq + 1][row] = v.y;
+            Xs[kq + 2][row] = v.z;
+            Xs[kq + 3][row] = v.w;
+        }
+        {
+            const int row = threadIdx.x >> 2, kq = (threadIdx.x & 3) * 4;
+            const int gr = row0 + row;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (gr < nrows) v = __ldg(reinterpret_cast<const float4*>(W + (size_t)gr * ld + k0 + kq));
+            Ws[kq + 0][row] = v.x;
+            Ws[kq + 1][row] = v.y;
+            Ws[kq + 2][row] = v.z;
+            Ws[kq + 3][row] = v.w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8 + 4]);
+            const float4 bb = *reinterpret_cast<const float4*>(&Ws[k][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+}
+
+// One layer for every active slot tile (FP32 backend, and the accurate first
+// layer of a chunk in the BF16 split form).
+__global__ void __launch_bounds__(256) batch_layer_fp32_kernel(BatchParams p, W32Ptrs wp) {
+    const int tile = blockIdx.y;
+    if (tile >= p.counters[CNT_TILES]) return;
+    const int ri = p.tile_rho[tile];
+    const int slot0 = tile * kSlotTile, row0 = blockIdx.x * 64;
+    float acc[8][4];
+    fp32_tile(p.Sin, wp.w[ri], p.ldk, 0, p.ldk, p.R, slot0, row0, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int slot = slot0 + ty * 8 + a;
+        const int qp = p.perm[slot];
+        if (qp < 0) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = row0 + tx * 4 + b;
+            if (r < p.R) layer_elem(p, slot, qp, ri, r, acc[a][b]);
+        }
+    }
+}
+
+// Residual products (FP32 backend).  Phase 1: [P; A] x over the x columns of
+// the check operand; phase 2: A^T lam_std over its multiplier columns.
+__global__ void __launch_bounds__(256) batch_check_fp32_kernel(BatchParams p, const float* __restrict__ Wc, int phase) {
+    const int tile = blockIdx.y;
+    if (tile >= p.counters[CNT_TILES]) return;
+    const int ri = p.tile_rho[tile];
+    const int slot0 = tile * kSlotTile, row0 = blockIdx.x * 64;
+    const int rows = phase == 1 ? p.n + p.m : p.n;
+    float acc[8][4];
+    if (phase == 1)
+        fp32_tile(p.CK32, Wc, p.ldkc, 0, p.n64, rows, slot0, row0, acc);
+    else
+        fp32_tile(p.CK32, Wc, p.ldkc, p.n64, p.ldkc, rows, slot0, row0, acc);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int slot = slot0 + ty * 8 + a;
+        const int qp = p.perm[slot];
+        if (qp < 0) continue;
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int r = row0 + tx * 4 + b;
+            if (r >= rows) continue;
+            if (phase == 1) check1_elem(p, slot, qp, ri, r, acc[a][b], r0, r1, r2, r3);
+            else check2_elem(p, qp, r, acc[a][b], r0, r1);
+        }
+        if (phase == 1) {
+            red_slot(p.RED, qp, RW_RP, r0);
+            red_slot(p.RED, qp, RW_AX, r1);
+            red_slot(p.RED, qp, RW_Z, r2);
+            red_slot(p.RED, qp, RW_PX, r3);
+        } else {
+            red_slot(p.RED, qp, RW_RD, r0);
+            red_slot(p.RED, qp, RW_ATL, r1);
+        }
+    }
+}
+
+struct DecideArgs {
+    int B, it, final_iter, adaptive;
+    double eps_abs, eps_rel;
+    float *XO, *ZO, *LO;
+    int *status, *iters, *rho_idx, *nsw;
+    float *rpo, *rdo;
+};
+
+// Stop test and penalty rule per QP (one warp per QP).
+__global__ void batch_decide_kernel(BatchParams p, DecideArgs d) {
+    const int qp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (qp >= d.B || d.status[qp] != QP_ACTIVE) return;
+    unsigned* red = p.RED + (size_t)qp * RW_WORDS;
+    const double rp = __uint_as_float(red[RW_RP]), rd = __uint_as_float(red[RW_RD]);
+    const double nax = __uint_as_float(red[RW_AX]), nz = __uint_as_float(red[RW_Z]);
+    const double npx = __uint_as_float(red[RW_PX]), natl = __uint_as_float(red[RW_ATL]);
+    const double qn = p.QN[qp];
+    const int ri = d.rho_idx[qp];
+    const bool numerical = !(isfinite(rp) && isfinite(rd) && isfinite(npx) && isfinite(natl));
+    const double eps_p = d.eps_abs + d.eps_rel * fmax(nax, nz);
+    const double eps_d = d.eps_abs + d.eps_rel * fmax(fmax(npx, natl), qn);
+    const bool converged = !numerical && rp <= eps_p && rd <= eps_d;
+    if (converged || numerical || d.final_iter) {
+        for (int k = lane; k < p.n; k += 32) d.XO[(size_t)qp * p.n + k] = p.Y[(size_t)qp * p.ldn + k];
+        for (int i = lane; i < p.m; i += 32) {
+            d.ZO[(size_t)qp * p.m + i] = p.Z[(size_t)qp * p.ldm + i];
+            d.LO[(size_t)qp * p.m + i] = p.LSTD[(size_t)qp * p.ldm + i];
+        }
+        if (lane == 0) {
+            d.status[qp] = numerical ? RELU_QP_NUMERICAL : (converged ? RELU_QP_SOLVED : RELU_QP_MAX_ITER);
+            d.iters[qp] = d.it;
+            d.rpo[qp] = (float)rp;
+            d.rdo[qp] = (float)rd;
+        }
+    } else if (d.adaptive) {
+        const double num = rp * fmax(fmax(npx, natl), fmax(qn, 1e-4));
+        const double den = rd * fmax(fmax(nax, nz), 1e-4);
+        int nri = ri;
+        if (num > 0.0 && den > 0.0) {
+            const double est = p.rhod[ri] * sqrt(num / den);
+            if (isfinite(est) && est > 0.0) {
+                const double le = log(est);
+                double best = 1e300;
+                for (int k = 0; k < p.nr; ++k) {
+                    const double dd = fabs(le - log(p.rhod[k]));
+                    if (dd < best) { best = dd; nri = k; }
+                }
+            }
+        }
+        if (nri != ri) {
+            // rebase lam' so that the next layer is standard ADMM with the new rho
+            for (int i = lane; i < p.m; i += 32) {
+                const size_t o = (size_t)qp * p.ldm + i;
+                const float rho_i = (float)(p.rhod[nri] * (double)p.rs[i]);
+                p.LAM[o] = p.LSTD[o] - rho_i * (p.AY[o] - p.Z[o]);
+            }
+            if (lane == 0) {
+                d.rho_idx[qp] = nri;
+                d.nsw[qp] += 1;
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < RW_WORDS) red[lane] = 0u;
+}
+
+// Regroup the active QPs by bank index: slots [base_g, base_g + count_g) hold
+// group g in increasing QP id, each group padded to a multiple of 128 slots.
+__global__ void __launch_bounds__(1024) batch_assign_kernel(int B, int slots, int nr, const int* __restrict__ status,
+                                                            const int* __restrict__ rho_idx, int* perm,
+                                                            int* tile_rho, int* counters) {
+    __shared__ int cnt[RQ_MAX_RHO], base[RQ_MAX_RHO], warp_cnt[32], run;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int s = tid; s < slots; s += blockDim.x) perm[s] = -1;
+    if (tid < RQ_MAX_RHO) cnt[tid] = 0;
+    __syncthreads();
+    for (int qp = tid; qp < B; qp += blockDim.x)
+        if (status[qp] == QP_ACTIVE) atomicAdd(&cnt[rho_idx[qp]], 1);
+    __syncthreads();
+    if (tid == 0) {
+        int off = 0, t = 0, tot = 0;
+        for (int g = 0; g < nr; ++g) {
+            base[g] = off;
+            const int tiles = (cnt[g] + kSlotTile - 1) / kSlotTile;
+            for (int k = 0; k < tiles; ++k) tile_rho[t++] = g;
+            off += tiles * kSlotTile;
+            tot += cnt[g];
+        }
+        counters[CNT_TILES] = t;
+        counters[CNT_ACTIVE] = tot;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int g = 0; g < nr; ++g) {
+        if (cnt[g] == 0) continue;
+        for (int c0 = 0; c0 < B; c0 += blockDim.x) {
+            const int qp = c0 + tid;
+            const bool flag = qp < B && status[qp] == QP_ACTIVE && rho_idx[qp] == g;
+            const unsigned ball = __ballot_sync(0xffffffffu, flag);
+            if (lane == 0) warp_cnt[warp] = __popc(ball);
+            __syncthreads();
+            if (tid == 0) {
+                int acc = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                    const int c = warp_cnt[w];
+                    warp_cnt[w] = acc;
+                    acc += c;
+                }
+                run = acc;
+            }
+            __syncthreads();
+            if (flag) perm[base[g] + warp_cnt[warp] + __popc(ball & lt)] = qp;
+            __syncthreads();
+            if (tid == 0) base[g] += run;
+            __syncthreads();
+        }
+    }
+}
+
+// Operand of the first layer of a chunk: s = [x; 2 rho z - lam'] per slot, in
+// FP32 or as a 3-way BF16 split; padding slots get zeros.
+__global__ void batch_fill_kernel(BatchParams p, const int* __restrict__ rho_idx, float* S32, __nv_bfloat16* T,
+                                  size_t part) {
+    const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (slot >= p.counters[CNT_TILES] * kSlotTile) return;
+    const int qp = p.perm[slot];
+    const int ri = qp >= 0 ? rho_idx[qp] : 0;
+    for (int k = lane; k < p.ldk; k += 32) {
+        float v = 0.f;
+        if (qp >= 0) {
+            if (k < p.n) {
+                v = p.Y[(size_t)qp * p.ldn + k];
+            } else if (k < p.R) {
+                const int i = k - p.n;
+                const size_t o = (size_t)qp * p.ldm + i;
+                v = 2.f * (p.rho[ri] * p.rs[i]) * p.Z[o] - p.LAM[o];
+            }
+        }
+        const size_t o = (size_t)slot * p.ldk + k;
+        if (S32) {
+            S32[o] = v;
+        } else {
+            __nv_bfloat16 a, b, c;
+            split3(v, a, b, c);
+            T[o] = a;
+            T[o + part] = b;
+            T[o + 2 * part] = c;
+        }
+    }
+}
+
+// Start state per QP: x given (Y) or 0, z = A x (AY holds A x for warm starts),
+// lam' = lam_warm (staged in LSTD) or 0.
+__global__ void batch_init_kernel(BatchParams p, int B, int warm, int lam_given, const int* __restrict__ rw,
+                                  int rho0, int* status, int* rho_idx, int* iters, int* nsw) {
+    const int qp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (qp >= p.cap) return;
+    if (lane == 0) {
+        status[qp] = qp < B ? QP_ACTIVE : QP_UNUSED;
+        rho_idx[qp] = (qp < B && rw) ? rw[qp] : rho0;
+        iters[qp] = 0;
+        nsw[qp] = 0;
+    }
+    if (lane < RW_WORDS) p.RED[(size_t)qp * RW_WORDS + lane] = 0u;
+    if (qp >= B) return;
+    for (int i = lane; i < p.m; i += 32) {
+        const size_t o = (size_t)qp * p.ldm + i;
+        const float ax = warm ? p.AY[o] : 0.f;
+        p.AY[o] = ax;
+        p.Z[o] = ax;
+        p.LAM[o] = lam_given ? p.LSTD[o] : 0.f;
+    }
+    if (!warm)
+        for (int k = lane; k < p.n; k += 32) p.Y[(size_t)qp * p.ldn + k] = 0.f;
+}
+
+__global__ void row_absmax_kernel(const float* __restrict__ X, int rows, int cols, int ld, float* out) {
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float v = 0.f;
+    for (int k = lane; k < cols; k += 32) v = fmaxf(v, fabsf(X[(size_t)r * ld + k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) out[r] = v;
+}
+
+// Check matrix [[P, A^T], [A, 0]] in FP32: x columns [0, n64), multiplier
+// columns [n64, n64 + m64); rows [0, n) for P and A^T, [n, n + m) for A.
+__global__ void build_wc32_kernel(const float* __restrict__ P32, const float* __restrict__ A32, int ldp,
+                                  const float* __restrict__ At32, int ldt, int n, int m, int n64, int ldkc,
+                                  float* __restrict__ Wc) {
+    const size_t total = (size_t)(n + m) * ldkc;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ldkc), k = (int)(e % ldkc);
+        float v = 0.f;
+        if (j < n) {
+            if (k < n) v = P32[(size_t)j * ldp + k];
+            else if (k >= n64 && k < n64 + m) v = At32[(size_t)j * ldt + (k - n64)];
+        } else if (k < n) {
+            v = A32[(size_t)(j - n) * ldp + k];
+        }
+        Wc[e] = v;
+    }
+}
+
+int sgemm_nt(relu_qp_t h, int M, int N, int K, const float* X, int ldx, const float* W, int ldw, float alpha,
+             const float* off, float* C, int ldc) {
+    if (M <= 0 || N <= 0) return RELU_QP_OK;
+    dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
+    sgemm_nt_kernel<<<grid, 256, 0, h->stream>>>(M, N, K, X, ldx, W, ldw, alpha, off, C, ldc);
+    RQ_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    return RELU_QP_OK;
+}
+
+BatchParams base_params(relu_qp_t h) {
+    BatchWork& w = h->bw;
+    BatchParams p{};
+    p.n = h->n;
+    p.m = h->m;
+    p.R = h->R;
+    p.ldn = w.ldn;
+    p.ldm = w.ldm;
+    p.ldR = w.ldR;
+    p.ldk = w.ldk;
+    p.n64 = w.n64;
+    p.ldkc = w.ldkc;
+    p.cap = w.cap;
+    p.slots = w.slots;
+    p.nr = h->nr;
+    for (int r = 0; r < h->nr; ++r) {
+        p.rho[r] = (float)h->be[r].rho;
+        p.rhod[r] = h->be[r].rho;
+    }
+    p.rs = h->rs32;
+    p.Y = w.Y; p.Z = w.Z; p.LAM = w.LAM; p.AY = w.AY; p.LSTD = w.LSTD; p.C = w.C; p.SREF = w.SREF; p.PY = w.PY;
+    p.L = w.L; p.U = w.U; p.Q = w.Q; p.BIAS = w.BIAS; p.QN = w.QN;
+    p.perm = w.perm; p.tile_rho = w.tile_rho; p.counters = w.counters; p.RED = w.RED;
+    return p;
+}
+
+int copy_rows_in(relu_qp_t h, float* dst, int ld, const float* src, int rows, int cols) {
+    if (rows <= 0 || cols <= 0) return RELU_QP_OK;
+    RQ_CUDA(h, cudaMemcpy2DAsync(dst, sizeof(float) * ld, src, sizeof(float) * cols, sizeof(float) * cols, rows,
+                                 cudaMemcpyDefault, h->stream));
+    return RELU_QP_OK;
+}
+
+}  // namespace
+
+int batch_alloc(relu_qp_t h) {
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m, R = h->R, nr = h->nr;
+    const int mm = m > 0 ? m : 1;
+    w.cap = h->opts.max_batch;
+    w.prec = h->opts.batch_precision;
+    w.slots = (int)round_up(w.cap, kSlotTile) + nr * kSlotTile;
+    w.ldn = (int)round_up(n, 4);
+    w.ldm = (int)round_up(mm, 4);
+    w.ldR = (int)round_up(R, 4);
+    w.ldk = h->ldw;
+    w.n64 = (int)round_up(n, 64);
+    w.m64 = (int)round_up(mm, 64);
+    w.ldkc = w.n64 + w.m64;
+    w.Rpad = (int)round_up(R, 256);
+    w.npad = (int)round_up(n + m, 256);
+    const size_t cap = w.cap;
+    RQ_TRY(alloc(h, &w.Y, cap * w.ldn));
+    RQ_TRY(alloc(h, &w.Q, cap * w.ldn));
+    RQ_TRY(alloc(h, &w.PY, cap * w.ldn));
+    RQ_TRY(alloc(h, &w.QN, cap));
+    RQ_TRY(alloc(h, &w.Z, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.LAM, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.AY, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.LSTD, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.L, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.U, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.BIAS, (size_t)nr * cap * w.ldR));
+    RQ_TRY(alloc(h, &w.XO, cap * n));
+    RQ_TRY(alloc(h, &w.ZO, cap * mm));
+    RQ_TRY(alloc(h, &w.LO, cap * mm));
+    RQ_TRY(alloc(h, &w.RED, cap * RW_WORDS));
+    RQ_TRY(alloc(h, &w.rho_idx, cap));
+    RQ_TRY(alloc(h, &w.status, cap));
+    RQ_TRY(alloc(h, &w.iters, cap));
+    RQ_TRY(alloc(h, &w.nsw, cap));
+    RQ_TRY(alloc(h, &w.rp, cap));
+    RQ_TRY(alloc(h, &w.rd, cap));
+    RQ_TRY(alloc(h, &w.perm, (size_t)w.slots));
+    RQ_TRY(alloc(h, &w.tile_rho, (size_t)w.slots / kSlotTile));
+    RQ_TRY(alloc(h, &w.counters, CNT_WORDS));
+    if (w.prec == RELU_QP_PREC_BF16X3) {
+        RQ_TRY(alloc(h, &w.C, cap * w.ldR));
+        RQ_TRY(alloc(h, &w.SREF, cap * w.ldR));
+        RQ_TRY(alloc(h, &w.S32, (size_t)w.slots * w.ldk));   // FP32 operand of the accurate layer
+        RQ_TRY(dev_alloc(h, &w.OPND, sizeof(uint16_t) * 7 * (size_t)w.slots * w.ldk + 1024));
+        RQ_TRY(dev_alloc(h, &w.CK, sizeof(uint16_t) * 3 * (size_t)w.slots * w.ldkc + 1024));
+        RQ_TRY(dev_alloc(h, &w.WB, sizeof(uint16_t) * (size_t)nr * 3 * w.Rpad * w.ldk + 1024));
+        RQ_TRY(dev_alloc(h, &w.WCB, sizeof(uint16_t) * 3 * (size_t)w.npad * w.ldkc + 1024));
+    } else {
+        RQ_TRY(alloc(h, &w.S32, 2 * (size_t)w.slots * w.ldk));
+        RQ_TRY(alloc(h, &w.CK32, (size_t)w.slots * w.ldkc));
+        RQ_TRY(alloc(h, &w.Wc32, (size_t)(n + m) * w.ldkc));
+    }
+    return RELU_QP_OK;
+}
+
+__global__ void tune_perm_kernel(int slots, int cap, int* perm, int* tile_rho, int* counters) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += gridDim.x * blockDim.x) {
+        perm[s] = s < cap ? s : -1;
+        if (s % kSlotTile == 0) tile_rho[s / kSlotTile] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counters[CNT_TILES] = (cap + kSlotTile - 1) / kSlotTile;
+        counters[CNT_ACTIVE] = cap;
+    }
+}
+
+// Choose the BN (rows per tile) of the tcgen05 layer and check kernels by
+// timing them on the full batch capacity (state values do not matter here;
+// every buffer they touch is re-initialised by the next solve).
+int tc_tune(relu_qp_t h) {
+    BatchWork& w = h->bw;
+    tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, w.perm, w.tile_rho, w.counters);
+    RQ_CUDA(h, cudaGetLastError());
+    BatchParams p = base_params(h);
+    const size_t opart = (size_t)w.slots * w.ldk;
+    __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
+    p.flags = EPI_REFINE;
+    p.Dhi = OP + 2 * opart;
+    p.Dlo = OP + 3 * opart;
+    p.CK = static_cast<__nv_bfloat16*>(w.CK);
+    const int tiles = w.slots / kSlotTile;
+    const int cands[4] = {64, 128, 192, 256};
+    float best = 1e30f;
+    int best_bn = 128;
+    for (int bn : cands) {
+        RQ_TRY(tc_set_tiles(h, bn, 128));
+        for (int rep = 0; rep < 2; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles));
+        RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+        for (int rep = 0; rep < 5; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles));
+        RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+        RQ_CUDA(h, cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        if (ms < best) { best = ms; best_bn = bn; }
+    }
+    float bestc = 1e30f;
+    int best_cbn = 128;
+    for (int bn : {64, 128}) {
+        RQ_TRY(tc_set_tiles(h, best_bn, bn));
+        for (int rep = 0; rep < 2; ++rep) {
+            RQ_TRY(tc_check(h, p, 1, tiles));
+            RQ_TRY(tc_check(h, p, 2, tiles));
+        }
+        RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+        for (int rep = 0; rep < 5; ++rep) {
+            RQ_TRY(tc_check(h, p, 1, tiles));
+            RQ_TRY(tc_check(h, p, 2, tiles));
+        }
+        RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+        RQ_CUDA(h, cudaEventSynchronize(h->ev1));
+        float ms = 0.f;
+        RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        if (ms < bestc) { bestc = ms; best_cbn = bn; }
+    }
+    RQ_TRY(tc_set_tiles(h, best_bn, best_cbn));
+    if (tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "tensor-core kernel wait passed its deadline while tuning");
+    RQ_CUDA(h, cudaMemsetAsync(w.RED, 0, sizeof(unsigned) * (size_t)w.cap * RW_WORDS, h->stream));
+    RQ_CUDA(h, cudaMemsetAsync(w.counters, 0, sizeof(int) * CNT_WORDS, h->stream));
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RELU_QP_OK;
+}
+
+void batch_release(relu_qp_t h) {
+    if (h->bw.tc) tc_release(h);
+}
+
+// After the FP64 stage: FP32 check matrix (FP32 backend) or tensor maps and
+// tile tuning (BF16 backend).
+int batch_finish_setup(relu_qp_t h) {
+    BatchWork& w = h->bw;
+    if (w.prec == RELU_QP_PREC_BF16X3) {
+        RQ_TRY(tc_prepare(h));
+        return tc_tune(h);
+    }
+    const int ldp = (int)round_up(h->n, 4), ldt = (int)round_up(h->m > 0 ? h->m : 1, 4);
+    const size_t total = (size_t)(h->n + h->m) * w.ldkc;
+    int g = (int)std::min<size_t>((total + 255) / 256, 8192);
+    build_wc32_kernel<<<g, 256, 0, h->stream>>>(h->P32, h->A32, ldp, h->At32, ldt, h->n, h->m, w.n64, w.ldkc,
+                                                w.Wc32);
+    RQ_CUDA(h, cudaGetLastError());
+    return RELU_QP_OK;
+}
+
+int batch_update(relu_qp_t h, int B, const float* Q, const float* L, const float* U) {
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m, R = h->R;
+    if (Q) RQ_TRY(copy_rows_in(h, w.Q, w.ldn, Q, B, n));
+    if (L && m > 0) RQ_TRY(copy_rows_in(h, w.L, w.ldm, L, B, m));
+    if (U && m > 0) RQ_TRY(copy_rows_in(h, w.U, w.ldm, U, B, m));
+    if (Q) {
+        for (int r = 0; r < h->nr; ++r)
+            RQ_TRY(sgemm_nt(h, B, R, n, w.Q, w.ldn, h->be[r].Bop, n, 1.f, nullptr,
+                            w.BIAS + (size_t)r * w.cap * w.ldR, w.ldR));
+        row_absmax_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(w.Q, B, n, w.ldn, w.QN);
+        RQ_CUDA(h, cudaGetLastError());
+        ++h->launches;
+    }
+    w.B = B;
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RELU_QP_OK;
+}
+
+int batch_set_parametric(relu_qp_t h, int nx, const double* F, const double* E, const double* l0,
+                         const double* u0) {
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m, R = h->R;
+    if (w.nx != nx) {
+        w.nx = nx;
+        w.ldx = (int)round_up(nx, 4);
+        RQ_TRY(alloc(h, &w.F32, (size_t)n * w.ldx));
+        RQ_TRY(alloc(h, &w.Ft32, (size_t)nx * w.ldn));
+        RQ_TRY(alloc(h, &w.E32, (size_t)(m > 0 ? m : 1) * w.ldx));
+        RQ_TRY(alloc(h, &w.l0, (size_t)(m > 0 ? m : 1)));
+        RQ_TRY(alloc(h, &w.u0, (size_t)(m > 0 ? m : 1)));
+        RQ_TRY(alloc(h, &w.X0, (size_t)w.cap * w.ldx));
+        for (int r = 0; r < h->nr; ++r) RQ_TRY(alloc(h, &w.G[r], (size_t)R * w.ldx));
+    }
+    std::vector<float> f((size_t)n * w.ldx, 0.f), ft((size_t)nx * w.ldn, 0.f);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < nx; ++k) {
+            f[(size_t)i * w.ldx + k] = (float)F[(size_t)i * nx + k];
+            ft[(size_t)k * w.ldn + i] = (float)F[(size_t)i * nx + k];
+        }
+    RQ_CUDA(h, cudaMemcpy(w.F32, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+    RQ_CUDA(h, cudaMemcpy(w.Ft32, ft.data(), sizeof(float) * ft.size(), cudaMemcpyHostToDevice));
+    if (m > 0) {
+        std::vector<float> e((size_t)m * w.ldx, 0.f), lo(m), up(m);
+        for (int i = 0; i < m; ++i) {
+            for (int k = 0; k < nx; ++k) e[(size_t)i * w.ldx + k] = (float)E[(size_t)i * nx + k];
+            lo[i] = (float)l0[i];
+            up[i] = (float)u0[i];
+        }
+        RQ_CUDA(h, cudaMemcpy(w.E32, e.data(), sizeof(float) * e.size(), cudaMemcpyHostToDevice));
+        RQ_CUDA(h, cudaMemcpy(w.l0, lo.data(), sizeof(float) * m, cudaMemcpyHostToDevice));
+        RQ_CUDA(h, cudaMemcpy(w.u0, up.data(), sizeof(float) * m, cudaMemcpyHostToDevice));
+    }
+    for (int r = 0; r < h->nr; ++r)   // G_r = Bop_r F
+        RQ_TRY(sgemm_nt(h, R, nx, n, h->be[r].Bop, n, w.Ft32, w.ldn, 1.f, nullptr, w.G[r], w.ldx));
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RELU_QP_OK;
+}
+
+int batch_update_x0(relu_qp_t h, int B, const float* X0) {
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m, R = h->R, nx = w.nx;
+    RQ_TRY(copy_rows_in(h, w.X0, w.ldx, X0, B, nx));
+    RQ_TRY(sgemm_nt(h, B, n, nx, w.X0, w.ldx, w.F32, w.ldx, 1.f, nullptr, w.Q, w.ldn));
+    if (m > 0) {
+        RQ_TRY(sgemm_nt(h, B, m, nx, w.X0, w.ldx, w.E32, w.ldx, -1.f, w.l0, w.L, w.ldm));
+        RQ_TRY(sgemm_nt(h, B, m, nx, w.X0, w.ldx, w.E32, w.ldx, -1.f, w.u0, w.U, w.ldm));
+    }
+    for (int r = 0; r < h->nr; ++r)
+        RQ_TRY(sgemm_nt(h, B, R, nx, w.X0, w.ldx, w.G[r], w.ldx, 1.f, nullptr, w.BIAS + (size_t)r * w.cap * w.ldR,
+                        w.ldR));
+    row_absmax_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(w.Q, B, n, w.ldn, w.QN);
+    RQ_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    w.B = B;
+    return RELU_QP_OK;
+}
+
+int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int* rw, double eps_abs,
+                double eps_rel, int max_iter, float* Xo, float* Zo, float* Lo, relu_qp_info* infos) {
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m, R = h->R;
+    const bool bf16 = w.prec == RELU_QP_PREC_BF16X3;
+    BatchParams p = base_params(h);
+    const int tiles_max = w.slots / kSlotTile;
+    // ---- start state ----
+    int rho0 = 0;
+    {
+        double bd = 1e300;
+        for (int k = 0; k < h->nr; ++k) {
+            const double d = std::fabs(std::log(h->opts.rho0) - std::log(h->bank[k]));
+            if (d < bd) { bd = d; rho0 = k; }
+        }
+    }
+    int* rw_dev = nullptr;
+    if (rw) {
+        RQ_CUDA(h, cudaMemcpyAsync(w.iters, rw, sizeof(int) * B, cudaMemcpyDefault, h->stream));
+        rw_dev = w.iters;   // staged; batch_init copies it into rho_idx before resetting iters
+    }
+    if (Xw) {
+        RQ_TRY(copy_rows_in(h, w.Y, w.ldn, Xw, B, n));
+        if (m > 0) RQ_TRY(sgemm_nt(h, B, m, n, w.Y, w.ldn, h->A32, (int)round_up(n, 4), 1.f, nullptr, w.AY, w.ldm));
+    }
+    if (Lw && m > 0) RQ_TRY(copy_rows_in(h, w.LSTD, w.ldm, Lw, B, m));
+    RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+    batch_init_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, h->stream>>>(p, B, Xw != nullptr, Lw != nullptr && m > 0,
+                                                                        rw_dev, rho0, w.status, w.rho_idx, w.iters,
+                                                                        w.nsw);
+    RQ_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    const size_t opart = (size_t)w.slots * w.ldk;
+    __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
+    auto regroup = [&](bool assign) -> int {
+        if (assign) {
+            batch_assign_kernel<<<1, 1024, 0, h->stream>>>(B, w.slots, h->nr, w.status, w.rho_idx, w.perm, w.tile_rho,
+                                                           w.counters);
+            RQ_CUDA(h, cudaGetLastError());
+            ++h->launches;
+        }
+        const bool split_operand = bf16 && w.rebase_tc;
+        batch_fill_kernel<<<ceil_div(w.slots * 32, 256), 256, 0, h->stream>>>(
+            p, w.rho_idx, split_operand ? nullptr : w.S32, split_operand ? OP + 4 * opart : nullptr, opart);
+        RQ_CUDA(h, cudaGetLastError());
+        ++h->launches;
+        return RELU_QP_OK;
+    };
+    RQ_TRY(regroup(true));
+    if (bf16) RQ_CUDA(h, cudaMemsetAsync(w.counters + CNT_ERR, 0, sizeof(int), h->stream));
+    const int ci = h->opts.check_interval;
+    const int chunk = ci > 0 ? ci : 25;
+    W32Ptrs wp{};
+    for (int r = 0; r < h->nr; ++r) wp.w[r] = h->be[r].Wt;
+    int it = 0;
+    int active = B;              // QPs in the batch (known to the host after each check)
+    size_t prof_used = 0;
+    while (it < max_iter) {
+        const int len = std::min(chunk, max_iter - it);
+        const bool last_chunk = it + len == max_iter;
+        const bool check = (ci > 0 && (it + len) % ci == 0) || last_chunk;
+        for (int j = 0; j < len; ++j) {
+            BatchParams q = p;
+            q.flags = 0;
+            if (j == len - 1) q.flags |= EPI_LAST | (check ? EPI_CHECK : 0u);
+            if (bf16) {
+                q.flags |= EPI_REFINE | (j == 0 ? EPI_REBASE : 0u);
+                q.Dhi = OP + (size_t)(2 * (j & 1)) * opart;
+                q.Dlo = q.Dhi + opart;
+                q.CK = static_cast<__nv_bfloat16*>(w.CK);
+                if (j == 0 && !w.rebase_tc) {
+                    // accurate layer c = Wt s_ref + b in FP32 on the CUDA cores (round to
+                    // nearest); the tensor core's truncating accumulation of the full
+                    // operand would set the fixed point's accuracy instead
+                    q.Sin = w.S32;
+                    dim3 grid(ceil_div(R, 64), tiles_max);
+                    batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
+                    RQ_CUDA(h, cudaGetLastError());
+                    ++h->launches;
+                } else {
+                    // operand set read by this layer: 4..6 = s (3-way), else pair ((j-1)&1)
+                    const bool timed = h->prof_on && j > 0 && prof_used + 2 <= h->prof_ev.size();
+                    if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+                    RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max));
+                    ++h->launches;
+                    if (j > 0) {
+                        ++h->layer_launches;
+                        // three BF16 products of the (n+m) x (n+m) factored layer per active QP
+                        h->layer_flops += 2.0 * 3.0 * (double)R * (double)R * (double)active;
+                    }
+                    if (timed) {
+                        RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                        prof_used += 2;
+                    }
+                }
+            } else {
+                q.Sin = w.S32 + (size_t)(j & 1) * opart;
+                q.Sout = w.S32 + (size_t)((j + 1) & 1) * opart;
+                q.CK32 = w.CK32;
+                dim3 grid(ceil_div(R, 64), tiles_max);
+                const bool timed = h->prof_on && prof_used + 2 <= h->prof_ev.size();
+                if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+                batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
+                RQ_CUDA(h, cudaGetLastError());
+                ++h->launches;
+                ++h->layer_launches;
+                h->layer_flops += 2.0 * (double)R * (double)R * (double)active;   // one FP32 product per QP
+                if (timed) {
+                    RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                    prof_used += 2;
+                }
+            }
+        }
+        it += len;
+        if (check) {
+            BatchParams q = p;
+            if (bf16) {
+                q.CK = static_cast<__nv_bfloat16*>(w.CK);
+                RQ_TRY(tc_check(h, q, 1, tiles_max));
+                RQ_TRY(tc_check(h, q, 2, tiles_max));
+                h->launches += 2;
+            } else {
+                q.CK32 = w.CK32;
+                batch_check_fp32_kernel<<<dim3(ceil_div(n + m, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 1);
+                RQ_CUDA(h, cudaGetLastError());
+                batch_check_fp32_kernel<<<dim3(ceil_div(n, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 2);
+                RQ_CUDA(h, cudaGetLastError());
+                h->launches += 2;
+            }
+            DecideArgs d{B, it, last_chunk ? 1 : 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO,
+                         w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd};
+            batch_decide_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(p, d);
+            RQ_CUDA(h, cudaGetLastError());
+            ++h->launches;
+        }
+        if (last_chunk) break;
+        RQ_TRY(regroup(check));
+        if (check) {
+            int cnt[CNT_WORDS] = {0, 0, 0, 0};
+            RQ_CUDA(h, cudaMemcpyAsync(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+            RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (cnt[CNT_ERR]) break;     // reported below
+            if (cnt[CNT_ACTIVE] == 0) break;
+            active = cnt[CNT_ACTIVE];
+        }
+    }
+    RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (bf16 && tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "a tensor-core kernel wait passed its deadline");
+    for (size_t e = 0; e + 1 < prof_used; e += 2) {
+        float ms = 0.f;
+        RQ_CUDA(h, cudaEventElapsedTime(&ms, h->prof_ev[e], h->prof_ev[e + 1]));
+        h->layer_ms += ms;
+        ++h->layer_timed;
+    }
+    // ---- outputs ----
+    RQ_CUDA(h, cudaMemcpyAsync(Xo, w.XO, sizeof(float) * B * n, cudaMemcpyDefault, h->stream));
+    if (Zo && m > 0) RQ_CUDA(h, cudaMemcpyAsync(Zo, w.ZO, sizeof(float) * B * m, cudaMemcpyDefault, h->stream));
+    if (Lo && m > 0) RQ_CUDA(h, cudaMemcpyAsync(Lo, w.LO, sizeof(float) * B * m, cudaMemcpyDefault, h->stream));
+    if (infos) {
+        std::vector<int> st(B), itv(B), ri(B), sw(B);
+        std::vector<float> rp(B), rd(B);
+        RQ_CUDA(h, cudaMemcpyAsync(st.data(), w.status, sizeof(int) * B, cudaMemcpyDeviceToHost, h->stream));
+        RQ_CUDA(h, cudaMemcpyAsync(itv.data(), w.iters, sizeof(int) * B, cudaMemcpyDeviceToHost, h->stream));
+        RQ_CUDA(h, cudaMemcpyAsync(ri.data(), w.rho_idx, sizeof(int) * B, cudaMemcpyDeviceToHost, h->stream));
+        RQ_CUDA(h, cudaMemcpyAsync(sw.data(), w.nsw, sizeof(int) * B, cudaMemcpyDeviceToHost, h->stream));
+        RQ_CUDA(h, cudaMemcpyAsync(rp.data(), w.rp, sizeof(float) * B, cudaMemcpyDeviceToHost, h->stream));
+        RQ_CUDA(h, cudaMemcpyAsync(rd.data(), w.rd, sizeof(float) * B, cudaMemcpyDeviceToHost, h->stream));
+        RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        for (int b = 0; b < B; ++b) {
+            infos[b].status = st[b];
+            infos[b].iters = itv[b];
+            infos[b].rho_index = ri[b];
+            infos[b].rho_switches = sw[b];
+            infos[b].r_prim = rp[b];
+            infos[b].r_dual = rd[b];
+            infos[b].solve_ms = ms;
+        }
+    }
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    return RELU_QP_OK;
+}
+
+}  // namespace rq

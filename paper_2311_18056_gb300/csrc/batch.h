@@ -1,0 +1,178 @@
+// Batched solves: many QPs that share P and A (hence every W_rho) but each
+// have their own q, l, u and iterate.  Internal to librelu_qp.so.
+//
+// Layout.  Per-QP state is indexed by the QP id (rows of length n, m or
+// R = n + m, padded).  The GEMM operand is indexed by *slot*: the slots of a
+// tile of 128 consecutive slots all use the same bank entry, so after every
+// check the active QPs are regrouped by their rho index (perm[slot] = QP id,
+// -1 for padding) and converged QPs leave the batch.
+//
+// Each layer is one GEMM  T[slot, r] = sum_k S[slot, k] Wt_rho[r, k]  followed
+// by the element-wise part of the layer (bias, clamp, multiplier step) in the
+// epilogue; see layer_elem below.
+#pragma once
+
+#include "common.h"
+
+#include <cuda_bf16.h>
+
+namespace rq {
+
+constexpr int kSlotTile = 128;        // slots per GEMM tile (the tcgen05 M dimension)
+
+enum : unsigned {
+    EPI_REBASE = 1u,   // first layer of a chunk: accurate product of s, stores c and s_ref
+    EPI_LAST = 2u,     // last layer of a chunk: the next operand is written by the fill kernel
+    EPI_CHECK = 4u,    // last layer before a check: write x into the check operand
+    EPI_REFINE = 8u,   // BF16 split form: t = c + Wt (s - s_ref)
+};
+
+enum { QP_ACTIVE = -1, QP_UNUSED = -2 };
+enum { RW_RP = 0, RW_RD, RW_AX, RW_Z, RW_PX, RW_ATL, RW_WORDS = 8 };
+enum { CNT_TILES = 0, CNT_ACTIVE = 1, CNT_ERR = 2, CNT_WORDS = 4 };
+
+struct BatchParams {
+    int n, m, R, ldn, ldm, ldR, ldk, n64, ldkc, cap, slots, nr;
+    float rho[RQ_MAX_RHO];
+    double rhod[RQ_MAX_RHO];
+    const float* rs;                         // per-row penalty scale (1 or eq_scale)
+    float *Y, *Z, *LAM, *AY, *LSTD, *C, *SREF, *PY;
+    const float *L, *U, *Q, *BIAS, *QN;
+    const int* perm;
+    const int* tile_rho;
+    const int* counters;
+    unsigned* RED;
+    const float* Sin;                        // FP32 operand in  [slots][ldk]
+    float* Sout;                             // FP32 operand out [slots][ldk]
+    __nv_bfloat16 *Dhi, *Dlo;                // BF16 split operand out (refined form)
+    float* CK32;                             // FP32 check operand [slots][ldkc]
+    __nv_bfloat16* CK;                       // BF16 3-way check operand [3][slots][ldkc]
+    unsigned flags;
+};
+
+// max that keeps a NaN (fmaxf would drop it)
+__device__ __forceinline__ float nmax(float a, float b) { return (b > a || b != b) ? b : a; }
+
+__device__ __forceinline__ void split2(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// v = a + b + c + O(2^-27 |v|); each difference is exact in FP32.
+__device__ __forceinline__ void split3(float v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(a);
+    b = __float2bfloat16_rn(r1);
+    c = __float2bfloat16_rn(r1 - __bfloat162float(b));
+}
+
+__device__ __forceinline__ void put_check(const BatchParams& p, int slot, int col, float v) {
+    const size_t o = (size_t)slot * p.ldkc + col;
+    if (p.CK) {
+        __nv_bfloat16 a, b, c;
+        split3(v, a, b, c);
+        const size_t part = (size_t)p.slots * p.ldkc;
+        p.CK[o] = a;
+        p.CK[o + part] = b;
+        p.CK[o + 2 * part] = c;
+    } else {
+        p.CK32[o] = v;
+    }
+}
+
+// The element-wise part of one layer for output row r of the QP in `slot`
+// (Eq. gpu_update in the factored form; see setup_fp64.cu):
+//   t = acc + b (or + c in the refined form), x rows: x+ = t;
+//   Ax rows i:  r_i = (Ax)_i - z_i + lam'_i/rho_i,  z+ = clamp(t + r_i, l_i, u_i),
+//               lam'+ = rho_i r_i,  (Ax)+ = t,  operand entry 2 rho_i z+ - lam'+.
+// With EPI_CHECK the new x also goes into the check operand.
+__device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int qp, int ri, int r, float acc) {
+    const unsigned f = p.flags;
+    const size_t oR = (size_t)qp * p.ldR + r;
+    const float* bias = p.BIAS + (size_t)ri * p.cap * p.ldR;
+    float t;
+    if (f & EPI_REBASE) {
+        t = acc + bias[oR];
+        p.C[oR] = t;
+    } else if (f & EPI_REFINE) {
+        t = acc + p.C[oR];
+    } else {
+        t = acc + bias[oR];
+    }
+    float s_new;
+    if (r < p.n) {
+        const size_t o = (size_t)qp * p.ldn + r;
+        if (f & EPI_REBASE) p.SREF[oR] = p.Y[o];
+        p.Y[o] = t;
+        s_new = t;
+        if (f & EPI_CHECK) put_check(p, slot, r, t);
+    } else {
+        const int i = r - p.n;
+        const size_t o = (size_t)qp * p.ldm + i;
+        const float rho_i = p.rho[ri] * p.rs[i];
+        const float ay = p.AY[o], zi = p.Z[o], li = p.LAM[o];
+        if (f & EPI_REBASE) p.SREF[oR] = 2.f * rho_i * zi - li;
+        const float rr = ay - zi + li / rho_i;
+        const float zn = fminf(fmaxf(t + rr, p.L[o]), p.U[o]);
+        const float ln = rho_i * rr;
+        p.AY[o] = t;
+        p.Z[o] = zn;
+        p.LAM[o] = ln;
+        s_new = 2.f * rho_i * zn - ln;
+    }
+    if (!(f & EPI_LAST)) {
+        const size_t so = (size_t)slot * p.ldk + r;
+        if (f & EPI_REFINE) {
+            __nv_bfloat16 hi, lo;
+            split2(s_new - p.SREF[oR], hi, lo);
+            p.Dhi[so] = hi;
+            p.Dlo[so] = lo;
+        } else {
+            p.Sout[so] = s_new;
+        }
+    }
+}
+
+__device__ __forceinline__ void red_slot(unsigned* RED, int qp, int word, float v) {
+    atomicMax(RED + (size_t)qp * RW_WORDS + word, __float_as_uint(fabsf(v)));
+}
+
+// First residual product, row r of [P; A] x (Eqs. primal, dual): P x is kept
+// for the second product; A x refreshes the carried Ax, gives the primal
+// residual A x - z and the multiplier lam_std = lam' + rho (A x - z), which
+// goes into the check operand.
+__device__ __forceinline__ void check1_elem(const BatchParams& p, int slot, int qp, int ri, int r, float acc,
+                                            float& rp, float& nax, float& nz, float& npx) {
+    if (r < p.n) {
+        p.PY[(size_t)qp * p.ldn + r] = acc;
+        npx = nmax(npx, fabsf(acc));
+    } else {
+        const int i = r - p.n;
+        const size_t o = (size_t)qp * p.ldm + i;
+        const float zi = p.Z[o];
+        const float d = acc - zi;
+        const float ls = p.LAM[o] + p.rho[ri] * p.rs[i] * d;
+        p.AY[o] = acc;
+        p.LSTD[o] = ls;
+        put_check(p, slot, p.n64 + i, ls);
+        rp = nmax(rp, fabsf(d));
+        nax = nmax(nax, fabsf(acc));
+        nz = nmax(nz, fabsf(zi));
+    }
+}
+
+// Second residual product, row j of A^T lam_std: dual residual P x + q + A^T lam_std.
+__device__ __forceinline__ void check2_elem(const BatchParams& p, int qp, int j, float acc, float& rd, float& natl) {
+    rd = nmax(rd, fabsf(p.PY[(size_t)qp * p.ldn + j] + p.Q[(size_t)qp * p.ldn + j] + acc));
+    natl = nmax(natl, fabsf(acc));
+}
+
+// --- entry points of the tcgen05 backend (batch_tc.cu) ---------------------
+int tc_prepare(relu_qp_t h);                     // BF16 splits of every W_rho and of [P | A^T]
+int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles);
+int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phase 1: [P; A] x, 2: A^T lam
+void tc_release(relu_qp_t h);
+int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);
+int tc_error(relu_qp_t h);    // device error word of the backend (0 = none); clears it
+
+}  // namespace rq

@@ -1,0 +1,475 @@
+// tcgen05 (5th-generation tensor core) backend of the batched layer.
+//
+// Each layer is T[slot, r] = sum_k S[slot, k] Wt[r, k] for a 128-slot x BN-row
+// tile, with S and Wt given as BF16 parts and the FP32 accumulator in TMEM:
+//   refined layers   S = d_hi + d_lo (d = s - s_ref), Wt = w1 + w2:
+//                    T = d_hi w1 + d_hi w2 + d_lo w1                 (3 MMAs / k-step)
+//   accurate layers  S = s1 + s2 + s3, Wt = w1 + w2 + w3 (3-way splits):
+//                    T = s1 w1 + s1 w2 + s2 w1 + s1 w3 + s2 w2 + s3 w1 (6 MMAs / k-step)
+// The residual products [P; A] x and A^T lam_std (and, optionally, the first
+// layer of every chunk) use the accurate form; the layers the refined one
+// (see batch.cu).
+//
+// Accumulation by significance: the tensor core adds into its FP32
+// accumulator with truncation, so every MMA that lands on a large partial sum
+// costs up to one unit in its last place, biased in one direction.  The hi*hi
+// product goes to one TMEM accumulator and every correction product (2^-9 of
+// it or smaller) to a second one; the epilogue adds the two in FP32.  This
+// keeps the truncation of the ~K/16 correction MMAs 2^-9 smaller.
+//
+// Warp roles (192 threads): warp 0 issues TMA loads (128B-swizzled K-major
+// tiles, one mbarrier per stage), warp 1 allocates TMEM and one lane issues
+// the MMAs, warps 2-5 run the epilogue: tcgen05.ld of their 32 TMEM lanes
+// (one slot per thread) and the element-wise layer of batch.h.  Every
+// mbarrier wait has a deadline; on expiry the kernel records an error, waits
+// (bounded) for its own copies and MMAs, frees TMEM and returns.
+#include "batch.h"
+
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+namespace rq {
+
+namespace {
+
+constexpr int kThreadsTC = 192;
+constexpr int kBK = 64;                        // bf16 elements per 128-byte swizzled row
+constexpr int kTileBytesA = kSlotTile * 128;   // one A part: 128 rows x 128 B
+constexpr long long kWaitNs = 1000000000LL;    // 1 s deadline for any single wait
+
+enum Mode { MODE_LAYER_REFINED = 0, MODE_LAYER_ACCURATE = 1, MODE_CHECK1 = 2, MODE_CHECK2 = 3 };
+
+struct TcArgs {
+    int num_kb;        // k-blocks of 64
+    int k_off;         // first column (x coordinate) of both operands
+    int a_row[3];      // row offset of each A part in the operand tensor (+ slot0)
+    int b_row[3];      // row offset of each B part in the weight tensor (+ row0)
+    int b_rho_stride;  // LAYER: rows between bank entries in the weight tensor
+    int rows;          // valid output rows (R for layers, n for the check)
+    int* err;          // device error word
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ long long gtime() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase with the given parity to complete; false after the deadline.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = gtime();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try(bar, parity)) return true;
+        if (gtime() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // version
+    d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
+
+template <int NA, int NB, int BN, int STAGES>
+struct TcSmem {
+    static constexpr int kA = NA * kTileBytesA;
+    static constexpr int kB = NB * BN * 128;
+    static constexpr int kStage = kA + kB;
+    static constexpr int kBytes = STAGES * kStage + 1024 /* align */ + 256 /* barriers */;
+};
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+template <int MODE, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchParams p,
+                   TcArgs g) {
+    constexpr int NA = MODE == MODE_LAYER_REFINED ? 2 : 3;
+    constexpr int NB = NA;
+    constexpr int NPROD = NA == 2 ? 3 : 6;
+    constexpr int ACC = 2;   // significance accumulators of BN columns each
+    constexpr int TCOLS = tmem_cols(ACC * BN);
+    using L = TcSmem<NA, NB, BN, STAGES>;
+    constexpr uint32_t kTx = L::kStage;
+    constexpr uint32_t IDESC = idesc_bf16(BN);
+
+    const int tile = blockIdx.y;
+    if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA
+    const int slot0 = tile * kSlotTile;
+    const int row0 = blockIdx.x * BN;
+    const int ri = p.tile_rho[tile];
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage);
+    // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready; then the TMEM address
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[STAGES + s]), 1);
+        }
+        mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------- TMA producer -------------------------
+        if (lane == 0) {
+            int issued = 0;
+            bool ok = true;
+            for (int kb = 0; kb < g.num_kb && ok; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (kb / STAGES) & 1;
+                if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1)) { ok = false; break; }
+                const uint32_t full = smem_u32(&bars[s]);
+                mbar_expect_tx(full, kTx);
+                uint8_t* st = smem + s * L::kStage;
+                const int k0 = kb * kBK + g.k_off;
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+                    tma_load_2d(smem_u32(st + a * kTileBytesA), &tmA, k0, g.a_row[a] + slot0, full);
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    tma_load_2d(smem_u32(st + L::kA + b * BN * 128), &tmB, k0,
+                                g.b_row[b] + ri * g.b_rho_stride + row0, full);
+                issued = kb + 1;
+            }
+            if (!ok) {
+                atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                s_fail = 1;
+                // wait (bounded) for the copies already in flight
+                for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+                    mbar_wait(smem_u32(&bars[kb % STAGES]), (kb / STAGES) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------- MMA issuer -------------------------
+        if (lane == 0) {
+            bool ok = true;
+            for (int kb = 0; kb < g.num_kb; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (kb / STAGES) & 1;
+                if (!mbar_wait(smem_u32(&bars[s]), ph)) { ok = false; break; }
+                fence_after();
+                const int kb_local = kb;
+                const uint32_t dt = tmem;
+                const uint32_t sa = smem_u32(smem + s * L::kStage);
+                const uint32_t sb = sa + L::kA;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        // product list: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0)
+                        const int ia = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
+                        const int ib = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+                        const uint64_t ad = sdesc(sa + ia * kTileBytesA + kk * 32);
+                        const uint64_t bd = sdesc(sb + ib * BN * 128 + kk * 32);
+                        const bool first = kb_local == 0 && kk == 0 && pr <= 1;   // first MMA of either accumulator
+                        mma_bf16(dt + (pr == 0 ? 0 : BN), ad, bd, IDESC, first ? 0u : 1u);
+                    }
+                }
+                mma_commit(smem_u32(&bars[STAGES + s]));
+            }
+            if (ok) {
+                mma_commit(smem_u32(&bars[2 * STAGES]));
+                // keep TMEM alive until the MMAs have landed
+                if (!mbar_wait(smem_u32(&bars[2 * STAGES]), 0)) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
+            } else {
+                atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                s_fail = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------- epilogue -------------------------
+        const int q = warp & 3;                         // TMEM lane quadrant of this warp
+        const int slot = slot0 + q * 32 + lane;
+        const int qp = p.perm[slot];
+        bool ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+        ready = __all_sync(0xffffffffu, ready);
+        if (!ready) {
+            if (lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
+        } else {
+            fence_after();
+            const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+            float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16], w[16];
+                tmem_ld16(tl + c0, v);
+                tmem_ld16(tl + BN + c0, w);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) v[t] += w[t];
+                if (qp >= 0) {
+#pragma unroll 4
+                    for (int t = 0; t < 16; ++t) {
+                        const int r = row0 + c0 + t;
+                        if (r >= g.rows) continue;
+                        if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
+                        else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
+                        else layer_elem(p, slot, qp, ri, r, v[t]);
+                    }
+                }
+            }
+            if (qp >= 0) {
+                if (MODE == MODE_CHECK1) {
+                    red_slot(p.RED, qp, RW_RP, ra);
+                    red_slot(p.RED, qp, RW_AX, rb);
+                    red_slot(p.RED, qp, RW_Z, rc);
+                    red_slot(p.RED, qp, RW_PX, rd);
+                } else if (MODE == MODE_CHECK2) {
+                    red_slot(p.RED, qp, RW_RD, ra);
+                    red_slot(p.RED, qp, RW_ATL, rb);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct TcState {
+    EncodeTiledFn encode = nullptr;
+    int bn_layer = 128, bn_check = 128;
+    int* err = nullptr;                  // = counters + CNT_ERR
+    // encoded maps, keyed by box rows
+    CUtensorMap opnd_map, ck_map;
+    CUtensorMap wb_map[4], wcb_map[4];   // for BN in {64, 128, 192, 256}
+};
+
+int encode_2d(relu_qp_t h, TcState* st, CUtensorMap* map, void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {kBK, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = st->encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, RELU_QP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return RELU_QP_OK;
+}
+
+template <int MODE, int BN>
+constexpr int stages_for() {
+    using L1 = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, 1>;
+    constexpr int budget = 220 * 1024;
+    constexpr int s = (budget - 1024 - 256) / L1::kStage;
+    return s > 4 ? 4 : s;
+}
+
+template <int MODE, int BN>
+int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
+              int tiles) {
+    constexpr int S = stages_for<MODE, BN>();
+    static_assert(S >= 2, "not enough shared memory for two stages");
+    using L = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, S>;
+    auto kern = tc_gemm_kernel<MODE, BN, S>;
+    RQ_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
+    dim3 grid(ceil_div(g.rows, BN), tiles);
+    kern<<<grid, kThreadsTC, L::kBytes, h->stream>>>(a, b, p, g);
+    RQ_CUDA(h, cudaGetLastError());
+    return RELU_QP_OK;
+}
+
+// The refined layer (2 parts per operand) fits two or more stages up to
+// BN = 256; the 3-part modes are limited to BN <= 128 for two stages.
+template <int MODE>
+int dispatch_bn(relu_qp_t h, int bn, const CUtensorMap* maps, const BatchParams& p, const TcArgs& g,
+                const CUtensorMap& a, int tiles) {
+    if (MODE == MODE_LAYER_REFINED) {
+        switch (bn) {
+            case 64: return launch_tc<MODE_LAYER_REFINED, 64>(h, a, maps[0], p, g, tiles);
+            case 128: return launch_tc<MODE_LAYER_REFINED, 128>(h, a, maps[1], p, g, tiles);
+            case 192: return launch_tc<MODE_LAYER_REFINED, 192>(h, a, maps[2], p, g, tiles);
+            default: return launch_tc<MODE_LAYER_REFINED, 256>(h, a, maps[3], p, g, tiles);
+        }
+    }
+    if (bn <= 64) return launch_tc<MODE, 64>(h, a, maps[0], p, g, tiles);
+    return launch_tc<MODE, 128>(h, a, maps[1], p, g, tiles);
+}
+
+}  // namespace
+
+int tc_prepare(relu_qp_t h) {
+    BatchWork& w = h->bw;
+    TcState* st = new (std::nothrow) TcState();
+    if (!st) return fail(h, RELU_QP_ERR_OOM, "host allocation failed");
+    w.tc = st;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    RQ_CUDA(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (!fn || q != cudaDriverEntryPointSuccess)
+        return fail(h, RELU_QP_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+    st->encode = reinterpret_cast<EncodeTiledFn>(fn);
+    st->err = w.counters + CNT_ERR;
+    RQ_TRY(encode_2d(h, st, &st->opnd_map, w.OPND, 7ull * w.slots, w.ldk, kSlotTile));
+    RQ_TRY(encode_2d(h, st, &st->ck_map, w.CK, 3ull * w.slots, w.ldkc, kSlotTile));
+    const int bns[4] = {64, 128, 192, 256};
+    for (int i = 0; i < 4; ++i) {
+        RQ_TRY(encode_2d(h, st, &st->wb_map[i], w.WB, (uint64_t)h->nr * 3 * w.Rpad, w.ldk, bns[i]));
+        RQ_TRY(encode_2d(h, st, &st->wcb_map[i], w.WCB, 3ull * w.npad, w.ldkc, bns[i]));
+    }
+    return RELU_QP_OK;
+}
+
+void tc_release(relu_qp_t h) {
+    delete static_cast<TcState*>(h->bw.tc);
+    h->bw.tc = nullptr;
+}
+
+int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
+    TcState* st = static_cast<TcState*>(h->bw.tc);
+    st->bn_layer = bn_layer;
+    st->bn_check = bn_check;
+    return RELU_QP_OK;
+}
+
+int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles) {
+    BatchWork& w = h->bw;
+    TcState* st = static_cast<TcState*>(w.tc);
+    TcArgs g{};
+    g.num_kb = w.ldk / kBK;
+    g.rows = h->R;
+    g.err = st->err;
+    g.b_rho_stride = 3 * w.Rpad;
+    for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
+    const int bn = st->bn_layer;
+    if (operand_set < 0) {   // accurate: s1, s2, s3 are parts 4..6
+        for (int a = 0; a < 3; ++a) g.a_row[a] = (4 + a) * w.slots;
+        return dispatch_bn<MODE_LAYER_ACCURATE>(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
+    }
+    g.a_row[0] = (2 * operand_set) * w.slots;
+    g.a_row[1] = (2 * operand_set + 1) * w.slots;
+    return dispatch_bn<MODE_LAYER_REFINED>(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
+}
+
+int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
+    BatchWork& w = h->bw;
+    TcState* st = static_cast<TcState*>(w.tc);
+    TcArgs g{};
+    g.num_kb = (phase == 1 ? w.n64 : w.m64) / kBK;
+    g.k_off = phase == 1 ? 0 : w.n64;
+    g.rows = phase == 1 ? h->n + h->m : h->n;
+    g.err = st->err;
+    g.b_rho_stride = 0;
+    for (int a = 0; a < 3; ++a) {
+        g.a_row[a] = a * w.slots;
+        g.b_row[a] = a * w.npad;
+    }
+    if (phase == 1) return dispatch_bn<MODE_CHECK1>(h, st->bn_check, st->wcb_map, p, g, st->ck_map, tiles);
+    return dispatch_bn<MODE_CHECK2>(h, st->bn_check, st->wcb_map, p, g, st->ck_map, tiles);
+}
+
+int tc_error(relu_qp_t h) {
+    TcState* st = static_cast<TcState*>(h->bw.tc);
+    if (!st) return 0;
+    int e = 0;
+    cudaMemcpy(&e, st->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e) cudaMemset(st->err, 0, sizeof(int));
+    return e;
+}
+
+}  // namespace rq

@@ -73,6 +73,34 @@ struct SingleWork {
     int rows_per_cta = 0;
 };
 
+// Workspace of batched solves (allocated when opts.max_batch > 0).
+struct BatchWork {
+    int cap = 0, slots = 0, prec = 0, B = 0;
+    int rebase_tc = 0;   // BF16 form: 1 = accurate layer on the tensor cores (3-way split),
+                         // 0 = on the CUDA cores in FP32 (default; see batch.cu)
+    int ldn = 0, ldm = 0, ldR = 0, ldk = 0, n64 = 0, m64 = 0, ldkc = 0, Rpad = 0, npad = 0;
+    // check matrix [[P, A^T], [A, 0]]: (n + m) rows (padded to npad), ldkc = n64 + m64 columns
+    // per-QP state (QP-indexed rows)
+    float *Y = nullptr, *Z = nullptr, *LAM = nullptr, *AY = nullptr, *LSTD = nullptr;
+    float *L = nullptr, *U = nullptr, *Q = nullptr, *QN = nullptr, *C = nullptr, *SREF = nullptr, *PY = nullptr;
+    float* BIAS = nullptr;                 // [nr][cap][ldR]
+    float *XO = nullptr, *ZO = nullptr, *LO = nullptr;   // dense outputs [cap][n|m]
+    unsigned* RED = nullptr;               // [cap][8] per-QP reduction words
+    int *rho_idx = nullptr, *status = nullptr, *iters = nullptr, *nsw = nullptr;
+    float *rp = nullptr, *rd = nullptr;
+    // slot data
+    int *perm = nullptr, *tile_rho = nullptr, *counters = nullptr;
+    // FP32 backend
+    float *S32 = nullptr, *CK32 = nullptr, *Wc32 = nullptr;
+    // BF16 split backend (tcgen05); 2-byte elements
+    void *OPND = nullptr, *CK = nullptr, *WB = nullptr, *WCB = nullptr;
+    void* tc = nullptr;                    // backend state (tensor maps, tuned tiles)
+    // parametric problem: q = F x0, l = l0 - E x0, u = u0 - E x0
+    int nx = 0, ldx = 0;
+    float *F32 = nullptr, *Ft32 = nullptr, *E32 = nullptr, *l0 = nullptr, *u0 = nullptr, *X0 = nullptr;
+    float* G[RQ_MAX_RHO] = {};             // G_r = Bop_r F
+};
+
 }  // namespace rq
 
 struct relu_qp_s {
@@ -89,7 +117,14 @@ struct relu_qp_s {
     float *q32 = nullptr, *l32 = nullptr, *u32 = nullptr, *rs32 = nullptr;
     double qnorm = 0.0;
     rq::SingleWork sw;
+    rq::BatchWork bw;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // profiling (relu_qp_profile): launch counter and event pairs around the
+    // batched layer kernel launches
+    long long launches = 0, layer_launches = 0, layer_timed = 0;
+    double layer_ms = 0.0, layer_flops = 0.0;
+    int prof_on = 0;
+    std::vector<cudaEvent_t> prof_ev;
     std::string err;
     std::vector<void*> allocs;               // every cudaMalloc of the handle
 };
@@ -114,6 +149,19 @@ int compute_bias(relu_qp_t h);
 int single_solve(relu_qp_t h, const float* x_warm_dev, const float* lam_warm_dev, int rho_index,
                  double eps_abs, double eps_rel, int max_iter, relu_qp_info* info);
 int single_prepare(relu_qp_t h);
+// Batched solves (batch.cu).
+int batch_alloc(relu_qp_t h);
+int batch_update(relu_qp_t h, int B, const float* Q, const float* L, const float* U);
+int batch_set_parametric(relu_qp_t h, int nx, const double* F, const double* E, const double* l0,
+                         const double* u0);
+int batch_update_x0(relu_qp_t h, int B, const float* X0);
+int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int* rw, double eps_abs,
+                double eps_rel, int max_iter, float* Xo, float* Zo, float* Lo, relu_qp_info* infos);
+// BF16 hi/mid/lo parts of the FP64 layer for the tcgen05 backend (setup_fp64.cu).
+int pack_bf16_layer(relu_qp_t h, int r, const double* X, const double* AX);
+int pack_bf16_check(relu_qp_t h, const double* dP, const double* dA);
+int batch_finish_setup(relu_qp_t h);
+void batch_release(relu_qp_t h);
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 inline size_t round_up(size_t a, size_t b) { return (a + b - 1) / b * b; }

@@ -18,6 +18,8 @@
 // the x row plus [A, -I, rho^{-1}], and [A, -I, rho^{-1}] v = A x - z + lam'/rho.
 #include "common.h"
 
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 namespace rq {
@@ -225,6 +227,55 @@ __global__ void transpose_f32_kernel(const double* __restrict__ in, float* __res
     }
 }
 
+// v = a + b + c with each part the BF16 rounding of what is left (FP64 arithmetic).
+__device__ __forceinline__ void split3_f64(double v, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+    a = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(a);
+    b = __double2bfloat16(r1);
+    c = __double2bfloat16(r1 - (double)__bfloat162float(b));
+}
+
+// The three BF16 parts of the factored layer (rows [x; Ax], K-major rows of ldk).
+__global__ void pack_bf16_layer_kernel(const double* __restrict__ X, const double* __restrict__ AX, int n, int m,
+                                       int ldk, size_t part, __nv_bfloat16* __restrict__ out) {
+    const int R = n + m, NR = 2 * n + m;
+    const size_t total = (size_t)R * ldk;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ldk), k = (int)(e % ldk);
+        double v = 0.0;
+        if (k < R) v = (r < n) ? X[(size_t)r * NR + k] : AX[(size_t)(r - n) * NR + k];
+        __nv_bfloat16 a, b, c;
+        split3_f64(v, a, b, c);
+        out[e] = a;
+        out[e + part] = b;
+        out[e + 2 * part] = c;
+    }
+}
+
+// The three BF16 parts of the check matrix [[P, A^T], [A, 0]] (x columns
+// [0, n64), multiplier columns [n64, n64 + m); rows [0, n) and [n, n + m)).
+__global__ void pack_bf16_check_kernel(const double* __restrict__ P, const double* __restrict__ A, int n, int m,
+                                       int n64, int ldkc, size_t part, __nv_bfloat16* __restrict__ out) {
+    const size_t total = (size_t)(n + m) * ldkc;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / ldkc), k = (int)(e % ldkc);
+        double v = 0.0;
+        if (j < n) {
+            if (k < n) v = P[(size_t)j * n + k];
+            else if (k >= n64 && k < n64 + m) v = A[(size_t)(k - n64) * n + j];
+        } else if (k < n) {
+            v = A[(size_t)(j - n) * n + k];
+        }
+        __nv_bfloat16 a, b, c;
+        split3_f64(v, a, b, c);
+        out[e] = a;
+        out[e + part] = b;
+        out[e + 2 * part] = c;
+    }
+}
+
 int grid1d(size_t total) {
     size_t g = (total + 255) / 256;
     if (g > 16384) g = 16384;
@@ -334,6 +385,24 @@ int make_check_matrices(relu_qp_t h, const double* dP, const double* dA) {
     return RELU_QP_OK;
 }
 
+int pack_bf16_layer(relu_qp_t h, int r, const double* X, const double* AX) {
+    BatchWork& w = h->bw;
+    const size_t part = (size_t)w.Rpad * w.ldk;
+    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(w.WB) + (size_t)r * 3 * part;
+    pack_bf16_layer_kernel<<<grid1d((size_t)h->R * w.ldk), 256, 0, h->stream>>>(X, AX, h->n, h->m, w.ldk, part, out);
+    RQ_CUDA(h, cudaGetLastError());
+    return RELU_QP_OK;
+}
+
+int pack_bf16_check(relu_qp_t h, const double* dP, const double* dA) {
+    BatchWork& w = h->bw;
+    const size_t part = (size_t)w.npad * w.ldkc;
+    pack_bf16_check_kernel<<<grid1d((size_t)(h->n + h->m) * w.ldkc), 256, 0, h->stream>>>(
+        dP, dA, h->n, h->m, w.n64, w.ldkc, part, static_cast<__nv_bfloat16*>(w.WCB));
+    RQ_CUDA(h, cudaGetLastError());
+    return RELU_QP_OK;
+}
+
 int build_bank(relu_qp_t h, const double* dP, const double* dA, const std::vector<double>& row_scale) {
     const int n = h->n, m = h->m, R = h->R, NR = 2 * n + m;
     const int nblk = ceil_div(n, NB);
@@ -376,6 +445,7 @@ int build_bank(relu_qp_t h, const double* dP, const double* dA, const std::vecto
         pack_layer_kernel<<<grid1d((size_t)R * (h->ldw + n)), 256, 0, h->stream>>>(
             Rhs, AX, n, m, h->ldw, be.Wt, be.Bop, be.Wt64, be.Bop64);
         RQ_CUDA(h, cudaGetLastError());
+        if (h->bw.cap > 0 && h->bw.prec == RELU_QP_PREC_BF16X3) RQ_TRY(pack_bf16_layer(h, r, Rhs, AX));
         int hflag = 0;
         RQ_CUDA(h, cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         RQ_CUDA(h, cudaStreamSynchronize(h->stream));

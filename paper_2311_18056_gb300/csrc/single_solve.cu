@@ -502,6 +502,7 @@ int single_solve(relu_qp_t h, const float* x_warm, const float* lam_warm, int rh
     RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
     RQ_TRY(launch(h, w.grid, w.cached_rows, rho_index, eps_abs, eps_rel, max_iter, h->opts.check_interval,
                   h->opts.adaptive_rho));
+    h->launches += 2;
     RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
     int oi[OUT_WORDS];
     float of[2];

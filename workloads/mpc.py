@@ -266,7 +266,7 @@ def poisson_arrivals(rate_hz: float, duration_s: float, mix=(0.6, 0.3, 0.1), wor
 #: peak unconstrained LQR control / limit for the |u| <= 1 workloads
 LIMIT_RATIO = 4.0
 #: same for the humanoid-sized workload (|u| <= 50 plus dense rows)
-LIMIT_RATIO_HUMANOID = 1.5
+LIMIT_RATIO_HUMANOID = 1.25
 
 
 def x0_scale(pq: ParametricQP, ratio: float, draws: int = 64, sub_id: int = 9) -> float:
