@@ -141,6 +141,34 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
                   double* lam_out, relu_qp_info* info);
 
 /*
+ * relu_qp_solve_noalloc -- relu_qp_solve for callers that cannot allocate
+ * device memory when they solve, e.g. a real-time control loop whose cycle
+ * must not stall on cudaMalloc (it can synchronise the device and take an
+ * unbounded time) or an application whose own allocator owns device memory.
+ * The paper has no counterpart; it is a deployment variant of the same solve.
+ *
+ * It allocates nothing: the solve's scratch (iterate, layer operands,
+ * residual vectors, grid-barrier and reduction words) lives in one fixed
+ * 192 KiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.  The layer bank and problem data
+ * come from relu_qp_setup / relu_qp_update on h as usual.
+ *   x_warm, lam_warm  device FP32 (n / m) warm start, or NULL (lam_warm needs x_warm)
+ *   rho_index_warm, eps_abs, eps_rel, max_iter, info: as relu_qp_solve
+ *   x_out (n, required), z_out, lam_out (m, may be NULL): device FP32 outputs
+ * Limits and rules: n + m <= 4096 (larger problems return RELU_QP_ERR_INVALID
+ * before any GPU work).  All calls share the one array, so calls whose GPU
+ * work overlaps (other streams or threads) race; order them.  The array keeps
+ * the last call's contents; each call clears what must start at zero.  The
+ * first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ * Errors: INVALID, UNSUPPORTED (device ordinal >= 64), CUDA, TIMEOUT.
+ */
+int relu_qp_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index_warm,
+                          double eps_abs, double eps_rel, int max_iter, float* x_out, float* z_out,
+                          float* lam_out, relu_qp_info* info);
+
+/*
  * relu_qp_get_layer -- export the layer of bank entry rho_index for checking:
  *   Wt   (n+m)*(n+m) FP64: rows [x; Ax] of the layer in the factored form
  *        [x+; (A x)+] = Wt [x; 2 rho z - lam'] + Bop q.  With D the KKT inverse,

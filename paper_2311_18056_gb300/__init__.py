@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 __all__ = ["ReluQP", "ReluQPError", "lib", "library_path", "OK", "SOLVED", "MAX_ITER", "NUMERICAL",
-           "PREC_FP32", "PREC_BF16X3", "EXPORTED_SYMBOLS"]
+           "PREC_FP32", "PREC_BF16X3", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "librelu_qp.so")
@@ -54,6 +54,8 @@ _SIGNATURES = {
     "relu_qp_update": (_c_int, [_c_void_p, _dp, _dp, _dp]),
     "relu_qp_solve": (_c_int, [_c_void_p, _dp, _dp, _c_int, _c_double, _c_double, _c_int, _dp, _dp, _dp,
                                ctypes.POINTER(Info)]),
+    "relu_qp_solve_noalloc": (_c_int, [_c_void_p, _c_void_p, _c_void_p, _c_int, _c_double, _c_double, _c_int,
+                                       _c_void_p, _c_void_p, _c_void_p, ctypes.POINTER(Info)]),
     "relu_qp_get_layer": (_c_int, [_c_void_p, _c_int, _dp, _dp]),
     "relu_qp_set_opts": (_c_int, [_c_void_p, ctypes.POINTER(Opts)]),
     "relu_qp_dims": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),

@@ -302,6 +302,19 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
     return RELU_QP_OK;
 }
 
+int relu_qp_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index_warm,
+                          double eps_abs, double eps_rel, int max_iter, float* x_out, float* z_out, float* lam_out,
+                          relu_qp_info* info) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    if (!x_out || max_iter < 1 || !(eps_abs >= 0.0) || !(eps_rel >= 0.0) || rho_index_warm < -1 ||
+        rho_index_warm >= h->nr || (lam_warm && !x_warm))
+        return rq::fail(h, RELU_QP_ERR_INVALID, "solve_noalloc: x_out required, max_iter >= 1, eps >= 0, "
+                                                "rho_index_warm in [-1, n_rho), lam_warm needs x_warm");
+    const int ri = rho_index_warm >= 0 ? rho_index_warm : nearest_index(h, h->opts.rho0);
+    return rq::single_solve_noalloc(h, x_warm, lam_warm, ri, eps_abs, eps_rel, max_iter, x_out, z_out, lam_out,
+                                    info);
+}
+
 int relu_qp_get_layer(relu_qp_t h, int rho_index, double* Wt, double* Bop) {
     if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
     if (rho_index < 0 || rho_index >= h->nr) return rq::fail(h, RELU_QP_ERR_INVALID, "rho_index out of range");

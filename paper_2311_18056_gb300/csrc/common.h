@@ -149,6 +149,10 @@ int compute_bias(relu_qp_t h);
 int single_solve(relu_qp_t h, const float* x_warm_dev, const float* lam_warm_dev, int rho_index,
                  double eps_abs, double eps_rel, int max_iter, relu_qp_info* info);
 int single_prepare(relu_qp_t h);
+// Same solve with its scratch in a fixed device array (single_solve.cu).
+int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index, double eps_abs,
+                         double eps_rel, int max_iter, float* x_out, float* z_out, float* lam_out,
+                         relu_qp_info* info);
 // Batched solves (batch.cu).
 int batch_alloc(relu_qp_t h);
 int batch_update(relu_qp_t h, int B, const float* Q, const float* L, const float* U);

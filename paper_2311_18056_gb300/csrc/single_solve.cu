@@ -18,6 +18,7 @@
 #include "common.h"
 
 #include <cmath>
+#include <mutex>
 
 namespace rq {
 
@@ -510,6 +511,140 @@ int single_solve(relu_qp_t h, const float* x_warm, const float* lam_warm, int rh
     RQ_CUDA(h, cudaMemcpyAsync(of, w.out_f, sizeof(of), cudaMemcpyDeviceToHost, h->stream));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     if (oi[OUT_ERR]) return fail(h, RELU_QP_ERR_TIMEOUT, "grid barrier deadline passed in relu_qp_solve");
+    if (info) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+        info->status = oi[OUT_STATUS];
+        info->iters = oi[OUT_ITERS];
+        info->rho_index = oi[OUT_RHO];
+        info->rho_switches = oi[OUT_SWITCHES];
+        info->r_prim = of[0];
+        info->r_dual = of[1];
+        info->solve_ms = ms;
+    }
+    return RELU_QP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Solve without allocating: the scratch of the cooperative solve lives in a
+// fixed, file-scope device array instead of buffers allocated at setup.
+//
+// Some callers cannot allocate device memory at the time they solve: a
+// real-time control loop whose cycle must not stall on cudaMalloc (which can
+// synchronise the device and take unbounded time), or a host application
+// whose allocator owns all device memory.  They set the problem up once (the
+// layer bank is still built by relu_qp_setup) and then solve with
+// relu_qp_solve_noalloc, which only launches kernels and copies.
+//
+// Every GPU that loads the library holds this array until the process exits.
+// All calls share it, so two calls whose GPU work overlaps (on different
+// streams, or from different threads) race on it; calls must be ordered.
+// It keeps the contents of the last call; each call clears the parts that
+// must start at zero.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 3 * ldw + ldp + 6 * ldt + 64 words for n + m <= kNoAllocMaxRows (see
+// noalloc_words); 49152 floats = 192 KiB.
+constexpr int kNoAllocMaxRows = 4096;
+constexpr size_t kNoAllocWords = 49152;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+float* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+size_t noalloc_words(int ldw, int ldp, int ldt) { return 3 * (size_t)ldw + ldp + 6 * (size_t)ldt + 64; }
+
+// Device address of the array on the current device, looked up once per
+// device (a host-side use of the symbol itself would not be a device address).
+int noalloc_scratch(relu_qp_t h, float** out) {
+    int dev = 0;
+    RQ_CUDA(h, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(h, RELU_QP_ERR_UNSUPPORTED, "device ordinal >= 64");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return fail(h, RELU_QP_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[dev] = static_cast<float*>(ptr);
+    }
+    *out = g_noalloc_ptr[dev];
+    return RELU_QP_OK;
+}
+
+}  // namespace
+
+int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index, double eps_abs,
+                         double eps_rel, int max_iter, float* x_out, float* z_out, float* lam_out,
+                         relu_qp_info* info) {
+    const int n = h->n, m = h->m;
+    const int ldp = (int)round_up(n, 4), ldt = (int)round_up(m > 0 ? m : 1, 4), ldw = h->ldw;
+    if (h->R > kNoAllocMaxRows || noalloc_words(ldw, ldp, ldt) > kNoAllocWords)
+        return fail(h, RELU_QP_ERR_INVALID, "relu_qp_solve_noalloc supports n + m <= " +
+                                                std::to_string(kNoAllocMaxRows) + " (fixed scratch of " +
+                                                std::to_string(kNoAllocWords * 4 / 1024) + " KiB)");
+    float* base = nullptr;
+    RQ_TRY(noalloc_scratch(h, &base));
+    // carve the scratch: vectors first (16-byte aligned offsets), then the words
+    float* y = base;
+    float* s0 = y + ldw;
+    float* s1 = s0 + ldw;
+    float* Py = s1 + ldw;
+    float* z = Py + ldp;
+    float* lam = z + ldt;
+    float* Ay = lam + ldt;
+    float* Axf = Ay + ldt;
+    float* lstd = Axf + ldt;
+    float* spare = lstd + ldt;            // ldt floats, unused
+    unsigned* red = reinterpret_cast<unsigned*>(spare + ldt);   // 3 x 8 words
+    unsigned* bar = red + 3 * RED_WORDS;                        // 2 words (+6 pad)
+    int* out_i = reinterpret_cast<int*>(bar + 8);               // OUT_WORDS
+    float* out_f = reinterpret_cast<float*>(out_i + OUT_WORDS); // 8 words
+    SP p{};
+    fill_params(h, p, h->sw.grid);
+    p.y = y; p.z = z; p.lam = lam; p.Ay = Ay; p.s0 = s0; p.s1 = s1;
+    p.Py = Py; p.Axf = Axf; p.lstd = lstd;
+    p.red = red; p.bar = bar; p.out_i = out_i; p.out_f = out_f;
+    p.cached_rows = h->sw.cached_rows;
+    p.rho_index0 = rho_index;
+    p.check_interval = h->opts.check_interval;
+    p.adaptive = h->opts.adaptive_rho;
+    p.max_iter = max_iter;
+    p.eps_abs = eps_abs;
+    p.eps_rel = eps_rel;
+    p.qnorm = h->qnorm;
+    // parts that must start at zero: x and lam_std padding (read as whole
+    // padded vectors by the check), reduction slots, barrier and result words
+    RQ_CUDA(h, cudaMemsetAsync(y, 0, sizeof(float) * ldw, h->stream));
+    RQ_CUDA(h, cudaMemsetAsync(lstd, 0, sizeof(float) * ldt, h->stream));
+    RQ_CUDA(h, cudaMemsetAsync(red, 0, sizeof(unsigned) * (3 * RED_WORDS + 8) + sizeof(int) * OUT_WORDS +
+                                           sizeof(float) * 8, h->stream));
+    const int blocks = ceil_div(ldw * 32, 256) < 1024 ? ceil_div(ldw * 32, 256) : 1024;
+    init_state_kernel<<<blocks, 256, 0, h->stream>>>(n, m, ldp, ldw, h->A32, x_warm, lam_warm, h->rs32,
+                                                      h->be[rho_index].rho, y, z, lam, Ay, s0, s1);
+    RQ_CUDA(h, cudaGetLastError());
+    const size_t smem = smem_bytes(p.cached_rows, ldw);
+    RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+    void* args[] = {&p};
+    RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)single_solve_kernel, dim3(h->sw.grid), dim3(kThreads),
+                                           args, smem, h->stream));
+    RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+    RQ_CUDA(h, cudaMemcpyAsync(x_out, y, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream));
+    if (z_out && m > 0) RQ_CUDA(h, cudaMemcpyAsync(z_out, z, sizeof(float) * m, cudaMemcpyDeviceToDevice, h->stream));
+    if (lam_out && m > 0)
+        RQ_CUDA(h, cudaMemcpyAsync(lam_out, lstd, sizeof(float) * m, cudaMemcpyDeviceToDevice, h->stream));
+    int oi[OUT_WORDS];
+    float of[2];
+    RQ_CUDA(h, cudaMemcpyAsync(oi, out_i, sizeof(oi), cudaMemcpyDeviceToHost, h->stream));
+    RQ_CUDA(h, cudaMemcpyAsync(of, out_f, sizeof(of), cudaMemcpyDeviceToHost, h->stream));
+    RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (oi[OUT_ERR]) return fail(h, RELU_QP_ERR_TIMEOUT, "grid barrier deadline passed in relu_qp_solve_noalloc");
     if (info) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev0, h->ev1);
