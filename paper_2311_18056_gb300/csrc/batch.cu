@@ -81,7 +81,11 @@ __global__ void __launch_bounds__(256) sgemm_nt_kernel(int M, int N, int K, cons
 // Shared main loop of the FP32 batched kernels: a 128-slot x 64-row tile of
 // sum_k X[slot, k] W[row, k] over k in [kbeg, kend) (rows of X and W have
 // leading dimension ld, zero padded to a multiple of 64); each thread
-// accumulates 8 slots x 4 rows.
+// accumulates 8 slots x 4 rows.  Every 16-wide k step is summed into a fresh
+// partial that is then added to the running sum: with multipliers of ~1e3
+// the terms of these dot products cancel heavily, and one long sequential
+// FP32 sum would lose ~sqrt(K) units in the last place of its largest
+// partial sum (measured: dual residuals off by 1e-3 on the humanoid workload).
 __device__ __forceinline__ void fp32_tile(const float* __restrict__ X, const float* __restrict__ W, int ld,
                                           int kbeg, int kend, int nrows, int slot0, int row0, float (&acc)[8][4]) {
     __shared__ __align__(16) float Xs[16][128 + 4];
@@ -91,26 +95,36 @@ __device__ __forceinline__ void fp32_tile(const float* __restrict__ X, const flo
     for (int a = 0; a < 8; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    // global -> register staging of one k-tile (2 float4 of X, 1 of W per thread),
+    // issued one tile ahead so that the loads overlap the arithmetic
+    const int xrow0 = threadIdx.x >> 2, xrow1 = (threadIdx.x + 256) >> 2, xk = (threadIdx.x & 3) * 4;
+    const int wrow = threadIdx.x >> 2, wk = (threadIdx.x & 3) * 4;
+    const bool wvalid = row0 + wrow < nrows;
+    const float* xp0 = X + (size_t)(slot0 + xrow0) * ld + xk;
+    const float* xp1 = X + (size_t)(slot0 + xrow1) * ld + xk;
+    const float* wp = W + (size_t)(row0 + wrow) * ld + wk;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 x0 = zero4, x1 = zero4, w0 = zero4;
+    if (kbeg < kend) {
+        x0 = *reinterpret_cast<const float4*>(xp0 + kbeg);
+        x1 = *reinterpret_cast<const float4*>(xp1 + kbeg);
+        if (wvalid) w0 = __ldg(reinterpret_cast<const float4*>(wp + kbeg));
+    }
     for (int k0 = kbeg; k0 < kend; k0 += 16) {
-        for (int e = threadIdx.x; e < 512; e += 256) {
-            const int row = e >> 2, kq = (e & 3) * 4;
-            const float4 v = *reinterpret_cast<const float4*>(X + (size_t)(slot0 + row) * ld + k0 + kq);
-            Xs[kq + 0][row] = v.x;
-            Xs[kq + 1][row] = v.y;
-            Xs[kq + 2][row] = v.z;
-            Xs[kq + 3][row] = v.w;
-        }
-        {
-            const int row = threadIdx.x >> 2, kq = (threadIdx.x & 3) * 4;
-            const int gr = row0 + row;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gr < nrows) v = __ldg(reinterpret_cast<const float4*>(W + (size_t)gr * ld + k0 + kq));
-            Ws[kq + 0][row] = v.x;
-            Ws[kq + 1][row] = v.y;
-            Ws[kq + 2][row] = v.z;
-            Ws[kq + 3][row] = v.w;
-        }
+        Xs[xk + 0][xrow0] = x0.x; Xs[xk + 1][xrow0] = x0.y; Xs[xk + 2][xrow0] = x0.z; Xs[xk + 3][xrow0] = x0.w;
+        Xs[xk + 0][xrow1] = x1.x; Xs[xk + 1][xrow1] = x1.y; Xs[xk + 2][xrow1] = x1.z; Xs[xk + 3][xrow1] = x1.w;
+        Ws[wk + 0][wrow] = w0.x; Ws[wk + 1][wrow] = w0.y; Ws[wk + 2][wrow] = w0.z; Ws[wk + 3][wrow] = w0.w;
         __syncthreads();
+        if (k0 + 16 < kend) {
+            x0 = *reinterpret_cast<const float4*>(xp0 + k0 + 16);
+            x1 = *reinterpret_cast<const float4*>(xp1 + k0 + 16);
+            if (wvalid) w0 = __ldg(reinterpret_cast<const float4*>(wp + k0 + 16));
+        }
+        float part[8][4];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             const float4 a0 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8]);
@@ -121,8 +135,12 @@ __device__ __forceinline__ void fp32_tile(const float* __restrict__ X, const flo
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < 4; ++b) part[a][b] = fmaf(av[a], bv[b], part[a][b]);
         }
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += part[a][b];
         __syncthreads();
     }
 }
@@ -488,6 +506,8 @@ int batch_alloc(relu_qp_t h) {
         RQ_TRY(alloc(h, &w.C, cap * w.ldR));
         RQ_TRY(alloc(h, &w.SREF, cap * w.ldR));
         RQ_TRY(alloc(h, &w.S32, (size_t)w.slots * w.ldk));   // FP32 operand of the accurate layer
+        RQ_TRY(alloc(h, &w.CK32, (size_t)w.slots * w.ldkc));  // FP32 check operand
+        RQ_TRY(alloc(h, &w.Wc32, (size_t)(n + m) * w.ldkc));
         RQ_TRY(dev_alloc(h, &w.OPND, sizeof(uint16_t) * 7 * (size_t)w.slots * w.ldk + 1024));
         RQ_TRY(dev_alloc(h, &w.CK, sizeof(uint16_t) * 3 * (size_t)w.slots * w.ldkc + 1024));
         RQ_TRY(dev_alloc(h, &w.WB, sizeof(uint16_t) * (size_t)nr * 3 * w.Rpad * w.ldk + 1024));
@@ -531,9 +551,9 @@ int tc_tune(relu_qp_t h) {
     int best_bn = 128;
     for (int bn : cands) {
         RQ_TRY(tc_set_tiles(h, bn, 128));
-        for (int rep = 0; rep < 2; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles));
+        for (int rep = 0; rep < 2; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, tiles));
         RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-        for (int rep = 0; rep < 5; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles));
+        for (int rep = 0; rep < 5; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, tiles));
         RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
         RQ_CUDA(h, cudaEventSynchronize(h->ev1));
         float ms = 0.f;
@@ -577,7 +597,7 @@ int batch_finish_setup(relu_qp_t h) {
     BatchWork& w = h->bw;
     if (w.prec == RELU_QP_PREC_BF16X3) {
         RQ_TRY(tc_prepare(h));
-        return tc_tune(h);
+        RQ_TRY(tc_tune(h));
     }
     const int ldp = (int)round_up(h->n, 4), ldt = (int)round_up(h->m > 0 ? h->m : 1, 4);
     const size_t total = (size_t)(h->n + h->m) * w.ldkc;
@@ -735,7 +755,8 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
                 q.flags |= EPI_REFINE | (j == 0 ? EPI_REBASE : 0u);
                 q.Dhi = OP + (size_t)(2 * (j & 1)) * opart;
                 q.Dlo = q.Dhi + opart;
-                q.CK = static_cast<__nv_bfloat16*>(w.CK);
+                if (w.check_tc) q.CK = static_cast<__nv_bfloat16*>(w.CK);
+                else q.CK32 = w.CK32;
                 if (j == 0 && !w.rebase_tc) {
                     // accurate layer c = Wt s_ref + b in FP32 on the CUDA cores (round to
                     // nearest); the tensor core's truncating accumulation of the full
@@ -749,7 +770,8 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
                     // operand set read by this layer: 4..6 = s (3-way), else pair ((j-1)&1)
                     const bool timed = h->prof_on && j > 0 && prof_used + 2 <= h->prof_ev.size();
                     if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
-                    RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max));
+                    RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max,
+                                    ceil_div(active, kSlotTile) + h->nr - 1));
                     ++h->launches;
                     if (j > 0) {
                         ++h->layer_launches;
@@ -782,7 +804,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         it += len;
         if (check) {
             BatchParams q = p;
-            if (bf16) {
+            if (bf16 && w.check_tc) {
                 q.CK = static_cast<__nv_bfloat16*>(w.CK);
                 RQ_TRY(tc_check(h, q, 1, tiles_max));
                 RQ_TRY(tc_check(h, q, 2, tiles_max));

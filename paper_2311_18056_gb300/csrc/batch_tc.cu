@@ -17,10 +17,11 @@
 // it or smaller) to a second one; the epilogue adds the two in FP32.  This
 // keeps the truncation of the ~K/16 correction MMAs 2^-9 smaller.
 //
-// Warp roles (192 threads): warp 0 issues TMA loads (128B-swizzled K-major
+// Warp roles (320 threads): warp 0 issues TMA loads (128B-swizzled K-major
 // tiles, one mbarrier per stage), warp 1 allocates TMEM and one lane issues
-// the MMAs, warps 2-5 run the epilogue: tcgen05.ld of their 32 TMEM lanes
-// (one slot per thread) and the element-wise layer of batch.h.  Every
+// the MMAs, warps 2-9 run the epilogue: each reads its 32 TMEM lanes (one slot
+// per thread; warps w and w+4 share a lane quadrant and split the columns)
+// and applies the element-wise layer of batch.h, 16 rows at a time.  Every
 // mbarrier wait has a deadline; on expiry the kernel records an error, waits
 // (bounded) for its own copies and MMAs, frees TMEM and returns.
 #include "batch.h"
@@ -35,7 +36,7 @@ namespace rq {
 
 namespace {
 
-constexpr int kThreadsTC = 192;
+constexpr int kThreadsTC = 320;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kBK = 64;                        // bf16 elements per 128-byte swizzled row
 constexpr int kTileBytesA = kSlotTile * 128;   // one A part: 128 rows x 128 B
 constexpr long long kWaitNs = 1000000000LL;    // 1 s deadline for any single wait
@@ -276,6 +277,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else {
         // ------------------------- epilogue -------------------------
         const int q = warp & 3;                         // TMEM lane quadrant of this warp
+        const int half = (warp - 2) >> 2;               // which half of the columns
         const int slot = slot0 + q * 32 + lane;
         const int qp = p.perm[slot];
         bool ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
@@ -286,21 +288,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             fence_after();
             const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
             float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
-            for (int c0 = 0; c0 < BN; c0 += 16) {
+            const bool n_aligned = (p.n & 3) == 0;
+            for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
                 float v[16], w[16];
                 tmem_ld16(tl + c0, v);
                 tmem_ld16(tl + BN + c0, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
-                if (qp >= 0) {
+                if (qp < 0) continue;
+                const int r0 = row0 + c0;
+                const bool whole = MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows &&
+                                   (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
+                if (whole) {
+                    layer_chunk16(p, slot, qp, ri, r0, v);
+                    continue;
+                }
 #pragma unroll 4
-                    for (int t = 0; t < 16; ++t) {
-                        const int r = row0 + c0 + t;
-                        if (r >= g.rows) continue;
-                        if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
-                        else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
-                        else layer_elem(p, slot, qp, ri, r, v[t]);
-                    }
+                for (int t = 0; t < 16; ++t) {
+                    const int r = r0 + t;
+                    if (r >= g.rows) continue;
+                    if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
+                    else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
+                    else layer_elem(p, slot, qp, ri, r, v[t]);
                 }
             }
             if (qp >= 0) {
@@ -427,7 +436,7 @@ int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
     return RELU_QP_OK;
 }
 
-int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles) {
+int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles) {
     BatchWork& w = h->bw;
     TcState* st = static_cast<TcState*>(w.tc);
     TcArgs g{};
@@ -436,7 +445,10 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles) {
     g.err = st->err;
     g.b_rho_stride = 3 * w.Rpad;
     for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
-    const int bn = st->bn_layer;
+    // with few active slot tiles (the convergence tail) narrower row tiles
+    // give more CTAs; the tuned width is for a full batch
+    int bn = st->bn_layer;
+    while (bn > 64 && (long)active_tiles * ceil_div(h->R, bn) < h->num_sms) bn = bn > 128 ? 128 : 64;
     if (operand_set < 0) {   // accurate: s1, s2, s3 are parts 4..6
         for (int a = 0; a < 3; ++a) g.a_row[a] = (4 + a) * w.slots;
         return dispatch_bn<MODE_LAYER_ACCURATE>(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
