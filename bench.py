@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-extras", action="store_true", help="skip the FP32 comparison arms")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the served stream (Poisson arrivals over three resident families) instead")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served stream: requests per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="served stream: measured seconds")
+    ap.add_argument("--profile-window", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -300,6 +306,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     unsolved, iters = 0, []
+    if args.profile_window:
+        torch.cuda.profiler.start()
     for k in range(K):
         flush.fill_(float(k))
         ev[k][0].record()
@@ -308,6 +316,8 @@ def run_ours(args):
         unsolved += int(np.sum(out["status"] != rq.SOLVED))
         iters.append(out["iters"])
     torch.cuda.synchronize()
+    if args.profile_window:
+        torch.cuda.profiler.stop()
     barrier(world)
     clk = clocks.stop()
     prof = solver.profile(enable=0)
@@ -405,9 +415,91 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Served stream: Poisson arrivals at `rate` req/s from three resident families
+    (n = 80, 600, 1600; 60/30/10 %), each request a new x0 for one of 64 clients
+    per family, warm-started from that client's previous solution."""
+    import torch
+    import paper_2311_18056_gb300 as rq
+    from paper_2311_18056_gb300 import build as _build
+    from workloads import mpc
+    _build.build()
+    torch.cuda.set_device(0)
+    names, slots, clients = ("family0", "family1", "family2"), (512, 256, 128), 64
+    fams = []
+    for name, sl in zip(names, slots):
+        pq, X0, std = mpc.workload(name, 1)
+        q, l, u = pq.instance(X0[0])
+        h = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, max_batch=sl, precision=rq.PREC_BF16X3)
+        h.set_parametric(pq.F, pq.E, pq.l0, pq.u0)
+        fams.append((pq, std, h))
+    warm_s = 1.0
+    times, fam = mpc.poisson_arrivals(args.rate, warm_s + args.duration, mix=(0.6, 0.3, 0.1))
+    rng = mpc.rng_for(4, 6)
+    x0s = [(fams[f][1] * rng.standard_normal(fams[f][0].nx)).astype(np.float32) for f in fam]
+    cl = rng.integers(0, clients, len(times))
+    srv = rq.Server([h for _, _, h in fams], clients=[clients] * 3, eps_abs=EPS)
+    t_base = srv.clock()
+    i, done, lat, lat_f, status = 0, 0, [], [[], [], []], []
+    while done < len(times):
+        now = srv.clock() - t_base
+        while i < len(times) and times[i] <= now:
+            srv.submit(int(fam[i]), x0s[i], client=int(cl[i]), tag=i)
+            i += 1
+        active, waiting = srv.step()
+        for r in srv.poll():
+            done += 1
+            k = r["tag"]
+            if times[k] >= warm_s:
+                ms = 1e3 * (r["t_done"] - t_base - times[k])
+                lat.append(ms)
+                lat_f[r["family"]].append(ms)
+                status.append(r["status"])
+        if active == 0 and waiting == 0 and i < len(times):
+            time.sleep(max(0.0, min(0.001, times[i] - (srv.clock() - t_base))))
+    t_end = srv.clock() - t_base
+    srv.close()
+    measured = sum(1 for t in times if t >= warm_s)
+    value = measured / max(t_end - warm_s, 1e-9)
+    # one-at-a-time plain FP32 single-QP solves of the same families
+    single_ms = []
+    for (pq, std, h), name in zip(fams, names):
+        h.close()
+        q, l, u = pq.instance(std * mpc.initial_states(pq.nx, 1, pq.meta["workload_id"], sub_id=11)[0])
+        sq = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+        X = std * mpc.initial_states(pq.nx, 12, pq.meta["workload_id"], sub_id=12)
+        t = []
+        for x0 in X:
+            sq.update(*pq.instance(x0))
+            t0 = time.perf_counter()
+            sq.solve(eps_abs=EPS)
+            t.append(1e3 * (time.perf_counter() - t0))
+        sq.close()
+        single_ms.append(float(np.mean(t)))
+    mix = np.array([0.6, 0.3, 0.1])
+    util = float(args.rate * np.sum(mix * np.array(single_ms)) / 1e3)
+    line = {"metric": "served MPC stream: solves/s and arrival-to-result latency (BF16-split, one GB300)",
+            "value": value, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "bf16",
+            "data": "synthetic", "impl": "ours",
+            "config": {"workload": f"Poisson {args.rate:g} req/s for {args.duration:g} s after {warm_s:g} s warm-up; "
+                                   "families n=80 (nx12 nu4 N20), 600/1000 (humanoid), 1600 (nx120 nu40 N40) at "
+                                   "60/30/10 %, 64 clients per family, warm start = the client's previous solution",
+                       "slots": list(slots), "eps_abs": EPS},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_by_family": [float(np.percentile(v, 50)) if v else None for v in lat_f],
+            "p99_ms_by_family": [float(np.percentile(v, 99)) if v else None for v in lat_f],
+            "unsolved": int(sum(1 for s_ in status if s_ != 0)), "requests": measured,
+            "fp32_one_at_a_time": {"mean_solve_ms_by_family": single_ms, "utilization_at_rate": util,
+                                   "max_rate_req_per_s": float(1e3 / np.sum(mix * np.array(single_ms))),
+                                   "stable": util < 1.0}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.serve:
+        run_serve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

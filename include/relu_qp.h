@@ -229,6 +229,57 @@ int relu_qp_solve_batch(relu_qp_t h, int B, const float* X_warm, const float* La
                         float* Lam_out, relu_qp_info* infos);
 
 /*
+ * ---- serving: continuous batching of MPC requests -------------------------
+ * A server owns several problem families (handles set up with max_batch > 0,
+ * check_interval > 0 and relu_qp_set_parametric), each with its layer bank
+ * and max_batch QP slots resident on the device.  A request is a new initial
+ * state x0 (nx floats) for one client of one family.  Requests wait in a host
+ * queue until their family has a free slot: admission is by device memory,
+ * since every slot's state is allocated once, up front.  Each
+ * relu_qp_server_step admits waiting requests into free slots (the parametric
+ * update of q, l, u and b, and a warm start from that client's previous
+ * solution, which stays on the device: x, lam and the bank index, with
+ * z = A x, paper Sec. II-B "Warm Starting"), runs one chunk of check_interval
+ * layers and the residual check for every family with work, each family on
+ * its own stream so that their chunks overlap on the GPU, and retires the
+ * QPs that finished (solved, max_iter reached, or non-finite).  Results keep
+ * the request's tag and its submit and completion times on the server clock.
+ * While a server exists its families' handles run on the server's streams;
+ * do not use them for other calls until relu_qp_server_destroy.
+ */
+typedef struct relu_qp_server_s* relu_qp_server_t;
+
+typedef struct relu_qp_result {
+    long long tag;       /* the caller's id from relu_qp_server_submit */
+    int    family;       /* family index */
+    int    client;       /* client index (-1: none) */
+    int    status;       /* RELU_QP_SOLVED / RELU_QP_MAX_ITER / RELU_QP_NUMERICAL */
+    int    iters;        /* layers run for this request */
+    int    rho_index;    /* bank index at the end */
+    int    rho_switches; /* bank switches during the request */
+    double r_prim, r_dual;      /* residuals at the last check */
+    double t_submit, t_done;    /* seconds on the server clock */
+} relu_qp_result;
+
+/* families: n_families (1..16) distinct handles; clients: per family the
+ * number of clients whose warm starts are kept (NULL = none); eps_abs,
+ * eps_rel, max_iter as relu_qp_solve.  Errors: INVALID, OOM, CUDA. */
+int relu_qp_server_create(relu_qp_server_t* out, relu_qp_t const* families, int n_families, const int* clients,
+                          double eps_abs, double eps_rel, int max_iter);
+/* Queue one request: x0 host FP32 (nx of the family), client in [-1, clients). */
+int relu_qp_server_submit(relu_qp_server_t s, int family, int client, const float* x0, long long tag);
+/* One admission + chunk + retirement round for every family (blocks until its
+ * chunks are done).  *active / *waiting (may be NULL): requests in slots / queued. */
+int relu_qp_server_step(relu_qp_server_t s, int* active, int* waiting);
+/* Pop up to max_results finished requests; x_out (may be NULL) receives each
+ * result's x (FP32) at row stride x_stride floats.  Returns the number popped. */
+int relu_qp_server_poll(relu_qp_server_t s, int max_results, relu_qp_result* results, float* x_out, int x_stride);
+/* Seconds since the server was created (the clock of t_submit / t_done). */
+double relu_qp_server_clock(relu_qp_server_t s);
+void relu_qp_server_destroy(relu_qp_server_t s);
+const char* relu_qp_server_error(relu_qp_server_t s);
+
+/*
  * Kernel-level counters of a handle, for benchmarks.  `launches` counts every
  * kernel the solve and update paths launched; `layer_*` cover the dominant
  * kernel of a batched solve (the tensor-core refined layer in the BF16 form,

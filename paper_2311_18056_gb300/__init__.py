@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 __all__ = ["ReluQP", "ReluQPError", "lib", "library_path", "OK", "SOLVED", "MAX_ITER", "NUMERICAL",
-           "PREC_FP32", "PREC_BF16X3", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof"]
+           "PREC_FP32", "PREC_BF16X3", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "librelu_qp.so")
@@ -46,6 +46,12 @@ class Info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_longlong), ("family", _c_int), ("client", _c_int), ("status", _c_int),
+                ("iters", _c_int), ("rho_index", _c_int), ("rho_switches", _c_int), ("r_prim", _c_double),
+                ("r_dual", _c_double), ("t_submit", _c_double), ("t_done", _c_double)]
+
+
 # name -> (restype, argtypes); the CPU test checks the library exports each one
 _SIGNATURES = {
     "relu_qp_default_opts": (None, [ctypes.POINTER(Opts)]),
@@ -66,6 +72,14 @@ _SIGNATURES = {
     "relu_qp_solve_batch": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_int,
                                      _c_void_p, _c_void_p, _c_void_p, ctypes.POINTER(Info)]),
     "relu_qp_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(Prof)]),
+    "relu_qp_server_create": (_c_int, [ctypes.POINTER(_c_void_p), ctypes.POINTER(_c_void_p), _c_int,
+                                       ctypes.POINTER(_c_int), _c_double, _c_double, _c_int]),
+    "relu_qp_server_submit": (_c_int, [_c_void_p, _c_int, _c_int, _c_void_p, ctypes.c_longlong]),
+    "relu_qp_server_step": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
+    "relu_qp_server_poll": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(Result), _c_void_p, _c_int]),
+    "relu_qp_server_clock": (_c_double, [_c_void_p]),
+    "relu_qp_server_destroy": (None, [_c_void_p]),
+    "relu_qp_server_error": (ctypes.c_char_p, [_c_void_p]),
     "relu_qp_destroy": (None, [_c_void_p]),
     "relu_qp_last_error": (ctypes.c_char_p, [_c_void_p]),
 }
@@ -290,3 +304,65 @@ class ReluQP:
         o.adaptive_rho = 1 if adaptive_rho is None else int(bool(adaptive_rho))
         o.rho0 = 0.1 if rho0 is None else float(rho0)
         self._check(lib().relu_qp_set_opts(self._h, ctypes.byref(o)))
+
+
+class Server:
+    """Continuous batching of MPC requests over several resident problem families.
+
+    ``families`` are ReluQP handles set up with max_batch > 0 and
+    set_parametric(); a request is a new initial state x0 for one client of one
+    family.  See relu_qp_server_* in include/relu_qp.h.
+    """
+
+    def __init__(self, families, clients=None, eps_abs=1e-3, eps_rel=0.0, max_iter=4000):
+        L = lib()
+        self.families = list(families)
+        nf = len(self.families)
+        hs = (_c_void_p * nf)(*[f.handle for f in self.families])
+        cl = (_c_int * nf)(*([0] * nf if clients is None else [int(c) for c in clients]))
+        s = _c_void_p()
+        rc = L.relu_qp_server_create(ctypes.byref(s), hs, nf, cl, float(eps_abs), float(eps_rel), int(max_iter))
+        if rc != OK:
+            raise ReluQPError(rc, L.relu_qp_last_error(None).decode())
+        self._s = s
+        self._nmax = max(f.n for f in self.families)
+
+    def submit(self, family, x0, client=-1, tag=0):
+        x = np.ascontiguousarray(np.asarray(x0, dtype=np.float32))
+        if x.size != self.families[family].nx:
+            raise ValueError("x0 must have nx entries")
+        rc = lib().relu_qp_server_submit(self._s, int(family), int(client), x.ctypes.data, int(tag))
+        if rc != OK:
+            raise ReluQPError(rc, "invalid request (family, client or non-finite x0)")
+
+    def step(self):
+        a, w = _c_int(), _c_int()
+        rc = lib().relu_qp_server_step(self._s, ctypes.byref(a), ctypes.byref(w))
+        if rc != OK:
+            raise ReluQPError(rc, lib().relu_qp_server_error(self._s).decode())
+        return a.value, w.value
+
+    def poll(self, max_results=4096):
+        res = (Result * max_results)()
+        x = np.empty((max_results, self._nmax), np.float32)
+        k = lib().relu_qp_server_poll(self._s, max_results, res, x.ctypes.data, self._nmax)
+        out = []
+        for i in range(k):
+            r = {f: getattr(res[i], f) for f, _ in Result._fields_}
+            r["x"] = x[i, :self.families[r["family"]].n].copy()
+            out.append(r)
+        return out
+
+    def clock(self):
+        return lib().relu_qp_server_clock(self._s)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().relu_qp_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

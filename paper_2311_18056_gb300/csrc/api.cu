@@ -418,6 +418,60 @@ int relu_qp_solve_batch(relu_qp_t h, int B, const float* X_warm, const float* La
                            infos);
 }
 
+int relu_qp_server_create(relu_qp_server_t* out, relu_qp_t const* families, int n_families, const int* clients,
+                          double eps_abs, double eps_rel, int max_iter) {
+    if (!out) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!families || n_families < 1 || n_families > 16 || max_iter < 1 || !(eps_abs >= 0.0) || !(eps_rel >= 0.0))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "server: 1..16 families, max_iter >= 1, eps >= 0");
+    for (int f = 0; f < n_families; ++f) {
+        relu_qp_t h = families[f];
+        if (!h || h->bw.cap <= 0 || h->bw.nx <= 0 || h->opts.check_interval <= 0)
+            return rq::fail(nullptr, RELU_QP_ERR_INVALID,
+                            "server: every family needs max_batch > 0, check_interval > 0 and relu_qp_set_parametric");
+        if (clients && (clients[f] < 0 || clients[f] > (1 << 20)))
+            return rq::fail(nullptr, RELU_QP_ERR_INVALID, "server: clients per family in [0, 2^20]");
+        for (int g = 0; g < f; ++g)
+            if (families[g] == h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "server: families must be distinct");
+    }
+    relu_qp_server_t s = nullptr;
+    const int rc = rq::server_create(&s, families, n_families, clients, eps_abs, eps_rel, max_iter);
+    if (rc != RELU_QP_OK) {
+        const std::string msg = s ? rq::server_error(s) : "server: host allocation failed";
+        if (s) rq::server_destroy(s);
+        return rq::fail(nullptr, rc, msg);
+    }
+    *out = s;
+    return RELU_QP_OK;
+}
+
+int relu_qp_server_submit(relu_qp_server_t s, int family, int client, const float* x0, long long tag) {
+    if (!s || !x0 || family < 0 || family >= rq::server_families(s) || client < -1 ||
+        client >= rq::server_clients(s, family))
+        return RELU_QP_ERR_INVALID;
+    for (int k = 0; k < rq::server_nx(s, family); ++k)
+        if (!std::isfinite(x0[k])) return RELU_QP_ERR_INVALID;
+    return rq::server_submit(s, family, client, x0, tag);
+}
+
+int relu_qp_server_step(relu_qp_server_t s, int* active, int* waiting) {
+    if (!s) return RELU_QP_ERR_INVALID;
+    return rq::server_step(s, active, waiting);
+}
+
+int relu_qp_server_poll(relu_qp_server_t s, int max_results, relu_qp_result* results, float* x_out, int x_stride) {
+    if (!s || max_results < 0) return RELU_QP_ERR_INVALID;
+    return rq::server_poll(s, max_results, results, x_out, x_stride);
+}
+
+double relu_qp_server_clock(relu_qp_server_t s) { return s ? rq::server_clock(s) : 0.0; }
+
+void relu_qp_server_destroy(relu_qp_server_t s) {
+    if (s) rq::server_destroy(s);
+}
+
+const char* relu_qp_server_error(relu_qp_server_t s) { return s ? rq::server_error(s) : relu_qp_last_error(nullptr); }
+
 int relu_qp_profile(relu_qp_t h, int enable, int reset, relu_qp_prof* out) {
     if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
     if (out) {

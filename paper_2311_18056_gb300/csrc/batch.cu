@@ -17,11 +17,21 @@
 #include "batch.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstring>
+#include <deque>
+#include <new>
 
 namespace rq {
 
 namespace {
+
+inline int __float_as_int_host(float f) {
+    int i;
+    std::memcpy(&i, &f, sizeof(i));
+    return i;
+}
 
 struct W32Ptrs {
     const float* w[RQ_MAX_RHO];
@@ -213,6 +223,11 @@ struct DecideArgs {
     float *XO, *ZO, *LO;
     int *status, *iters, *rho_idx, *nsw;
     float *rpo, *rdo;
+    // continuous batching: layers since the previous check of each QP (0 = whole-batch
+    // solve, where `it` and `final_iter` hold for every QP), per-QP layer budget, and the
+    // list the finished QPs are appended to
+    int serve_len, max_iter;
+    int *done_list, *done_count;
 };
 
 // Stop test and penalty rule per QP (one warp per QP).
@@ -226,11 +241,13 @@ __global__ void batch_decide_kernel(BatchParams p, DecideArgs d) {
     const double npx = __uint_as_float(red[RW_PX]), natl = __uint_as_float(red[RW_ATL]);
     const double qn = p.QN[qp];
     const int ri = d.rho_idx[qp];
+    const int it_qp = d.serve_len > 0 ? d.iters[qp] + d.serve_len : d.it;
+    const bool final_qp = d.serve_len > 0 ? it_qp >= d.max_iter : d.final_iter != 0;
     const bool numerical = !(isfinite(rp) && isfinite(rd) && isfinite(npx) && isfinite(natl));
     const double eps_p = d.eps_abs + d.eps_rel * fmax(nax, nz);
     const double eps_d = d.eps_abs + d.eps_rel * fmax(fmax(npx, natl), qn);
     const bool converged = !numerical && rp <= eps_p && rd <= eps_d;
-    if (converged || numerical || d.final_iter) {
+    if (converged || numerical || final_qp) {
         for (int k = lane; k < p.n; k += 32) d.XO[(size_t)qp * p.n + k] = p.Y[(size_t)qp * p.ldn + k];
         for (int i = lane; i < p.m; i += 32) {
             d.ZO[(size_t)qp * p.m + i] = p.Z[(size_t)qp * p.ldm + i];
@@ -238,9 +255,10 @@ __global__ void batch_decide_kernel(BatchParams p, DecideArgs d) {
         }
         if (lane == 0) {
             d.status[qp] = numerical ? RELU_QP_NUMERICAL : (converged ? RELU_QP_SOLVED : RELU_QP_MAX_ITER);
-            d.iters[qp] = d.it;
+            d.iters[qp] = it_qp;
             d.rpo[qp] = (float)rp;
             d.rdo[qp] = (float)rd;
+            if (d.done_list) d.done_list[atomicAdd(d.done_count, 1)] = qp;
         }
     } else if (d.adaptive) {
         const double num = rp * fmax(fmax(npx, natl), fmax(qn, 1e-4));
@@ -270,6 +288,7 @@ __global__ void batch_decide_kernel(BatchParams p, DecideArgs d) {
             }
         }
     }
+    if (d.serve_len > 0 && !(converged || numerical || final_qp) && lane == 0) d.iters[qp] = it_qp;
     __syncwarp();
     if (lane < RW_WORDS) red[lane] = 0u;
 }
@@ -686,6 +705,127 @@ int batch_update_x0(relu_qp_t h, int B, const float* X0) {
     return RELU_QP_OK;
 }
 
+// Regroup the active QPs among the first nqp QP indices into slots (assign)
+// and write the FP32 operand of the next chunk's first layer (fill).
+int regroup_slots(relu_qp_t h, const BatchParams& p, int nqp, bool assign) {
+    BatchWork& w = h->bw;
+    const bool bf16 = w.prec == RELU_QP_PREC_BF16X3;
+    const size_t opart = (size_t)w.slots * w.ldk;
+    __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
+    if (assign) {
+        batch_assign_kernel<<<1, 1024, 0, h->stream>>>(nqp, w.slots, h->nr, w.status, w.rho_idx, w.perm, w.tile_rho,
+                                                       w.counters);
+        RQ_CUDA(h, cudaGetLastError());
+        ++h->launches;
+    }
+    const bool split_operand = bf16 && w.rebase_tc;
+    batch_fill_kernel<<<ceil_div(w.slots * 32, 256), 256, 0, h->stream>>>(
+        p, w.rho_idx, split_operand ? nullptr : w.S32, split_operand ? OP + 4 * opart : nullptr, opart);
+    RQ_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    return RELU_QP_OK;
+}
+
+// `len` layers of one chunk over the slots of the last regroup; with `check`
+// the last layer also writes x into the check operand.  `active` is the
+// number of QPs in the batch (for the tile-width choice and the FLOP count).
+int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int active, size_t& prof_used) {
+    BatchWork& w = h->bw;
+    const int R = h->R;
+    const bool bf16 = w.prec == RELU_QP_PREC_BF16X3;
+    const int tiles_max = w.slots / kSlotTile;
+    const size_t opart = (size_t)w.slots * w.ldk;
+    __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
+    W32Ptrs wp{};
+    for (int r = 0; r < h->nr; ++r) wp.w[r] = h->be[r].Wt;
+    for (int j = 0; j < len; ++j) {
+        BatchParams q = p;
+        q.flags = 0;
+        if (j == len - 1) q.flags |= EPI_LAST | (check ? EPI_CHECK : 0u);
+        if (bf16) {
+            q.flags |= EPI_REFINE | (j == 0 ? EPI_REBASE : 0u);
+            q.Dhi = OP + (size_t)(2 * (j & 1)) * opart;
+            q.Dlo = q.Dhi + opart;
+            if (w.check_tc) q.CK = static_cast<__nv_bfloat16*>(w.CK);
+            else q.CK32 = w.CK32;
+            if (j == 0 && !w.rebase_tc) {
+                // accurate layer c = Wt s_ref + b in FP32 on the CUDA cores (round to
+                // nearest); the tensor core's truncating accumulation of the full
+                // operand would set the fixed point's accuracy instead
+                q.Sin = w.S32;
+                dim3 grid(ceil_div(R, 64), tiles_max);
+                batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
+                RQ_CUDA(h, cudaGetLastError());
+                ++h->launches;
+            } else {
+                // operand set read by this layer: 4..6 = s (3-way), else pair ((j-1)&1)
+                const bool timed = h->prof_on && j > 0 && prof_used + 2 <= h->prof_ev.size();
+                if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+                RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max,
+                                ceil_div(active, kSlotTile) + h->nr - 1));
+                ++h->launches;
+                if (j > 0) {
+                    ++h->layer_launches;
+                    // three BF16 products of the (n+m) x (n+m) factored layer per active QP
+                    h->layer_flops += 2.0 * 3.0 * (double)R * (double)R * (double)active;
+                }
+                if (timed) {
+                    RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                    prof_used += 2;
+                }
+            }
+        } else {
+            q.Sin = w.S32 + (size_t)(j & 1) * opart;
+            q.Sout = w.S32 + (size_t)((j + 1) & 1) * opart;
+            q.CK32 = w.CK32;
+            dim3 grid(ceil_div(R, 64), tiles_max);
+            const bool timed = h->prof_on && prof_used + 2 <= h->prof_ev.size();
+            if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+            batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
+            RQ_CUDA(h, cudaGetLastError());
+            ++h->launches;
+            ++h->layer_launches;
+            h->layer_flops += 2.0 * (double)R * (double)R * (double)active;   // one FP32 product per QP
+            if (timed) {
+                RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                prof_used += 2;
+            }
+        }
+    }
+    return RELU_QP_OK;
+}
+
+// Residual products of a check: [P; A] x, then A^T lam_std (Eqs. primal, dual).
+int run_check(relu_qp_t h, const BatchParams& p) {
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m;
+    const int tiles_max = w.slots / kSlotTile;
+    BatchParams q = p;
+    if (w.prec == RELU_QP_PREC_BF16X3 && w.check_tc) {
+        q.CK = static_cast<__nv_bfloat16*>(w.CK);
+        RQ_TRY(tc_check(h, q, 1, tiles_max));
+        RQ_TRY(tc_check(h, q, 2, tiles_max));
+    } else {
+        q.CK32 = w.CK32;
+        batch_check_fp32_kernel<<<dim3(ceil_div(n + m, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 1);
+        RQ_CUDA(h, cudaGetLastError());
+        batch_check_fp32_kernel<<<dim3(ceil_div(n, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 2);
+        RQ_CUDA(h, cudaGetLastError());
+    }
+    h->launches += 2;
+    return RELU_QP_OK;
+}
+
+int nearest_rho(relu_qp_t h, double rho) {
+    int best = 0;
+    double bd = 1e300;
+    for (int k = 0; k < h->nr; ++k) {
+        const double d = std::fabs(std::log(rho) - std::log(h->bank[k]));
+        if (d < bd) { bd = d; best = k; }
+    }
+    return best;
+}
+
 int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int* rw, double eps_abs,
                 double eps_rel, int max_iter, float* Xo, float* Zo, float* Lo, relu_qp_info* infos) {
     BatchWork& w = h->bw;
@@ -694,14 +834,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     BatchParams p = base_params(h);
     const int tiles_max = w.slots / kSlotTile;
     // ---- start state ----
-    int rho0 = 0;
-    {
-        double bd = 1e300;
-        for (int k = 0; k < h->nr; ++k) {
-            const double d = std::fabs(std::log(h->opts.rho0) - std::log(h->bank[k]));
-            if (d < bd) { bd = d; rho0 = k; }
-        }
-    }
+    const int rho0 = nearest_rho(h, h->opts.rho0);
     int* rw_dev = nullptr;
     if (rw) {
         RQ_CUDA(h, cudaMemcpyAsync(w.iters, rw, sizeof(int) * B, cudaMemcpyDefault, h->stream));
@@ -718,28 +851,10 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
                                                                         w.nsw);
     RQ_CUDA(h, cudaGetLastError());
     ++h->launches;
-    const size_t opart = (size_t)w.slots * w.ldk;
-    __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
-    auto regroup = [&](bool assign) -> int {
-        if (assign) {
-            batch_assign_kernel<<<1, 1024, 0, h->stream>>>(B, w.slots, h->nr, w.status, w.rho_idx, w.perm, w.tile_rho,
-                                                           w.counters);
-            RQ_CUDA(h, cudaGetLastError());
-            ++h->launches;
-        }
-        const bool split_operand = bf16 && w.rebase_tc;
-        batch_fill_kernel<<<ceil_div(w.slots * 32, 256), 256, 0, h->stream>>>(
-            p, w.rho_idx, split_operand ? nullptr : w.S32, split_operand ? OP + 4 * opart : nullptr, opart);
-        RQ_CUDA(h, cudaGetLastError());
-        ++h->launches;
-        return RELU_QP_OK;
-    };
-    RQ_TRY(regroup(true));
+    RQ_TRY(regroup_slots(h, p, B, true));
     if (bf16) RQ_CUDA(h, cudaMemsetAsync(w.counters + CNT_ERR, 0, sizeof(int), h->stream));
     const int ci = h->opts.check_interval;
     const int chunk = ci > 0 ? ci : 25;
-    W32Ptrs wp{};
-    for (int r = 0; r < h->nr; ++r) wp.w[r] = h->be[r].Wt;
     int it = 0;
     int active = B;              // QPs in the batch (known to the host after each check)
     size_t prof_used = 0;
@@ -747,84 +862,18 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         const int len = std::min(chunk, max_iter - it);
         const bool last_chunk = it + len == max_iter;
         const bool check = (ci > 0 && (it + len) % ci == 0) || last_chunk;
-        for (int j = 0; j < len; ++j) {
-            BatchParams q = p;
-            q.flags = 0;
-            if (j == len - 1) q.flags |= EPI_LAST | (check ? EPI_CHECK : 0u);
-            if (bf16) {
-                q.flags |= EPI_REFINE | (j == 0 ? EPI_REBASE : 0u);
-                q.Dhi = OP + (size_t)(2 * (j & 1)) * opart;
-                q.Dlo = q.Dhi + opart;
-                if (w.check_tc) q.CK = static_cast<__nv_bfloat16*>(w.CK);
-                else q.CK32 = w.CK32;
-                if (j == 0 && !w.rebase_tc) {
-                    // accurate layer c = Wt s_ref + b in FP32 on the CUDA cores (round to
-                    // nearest); the tensor core's truncating accumulation of the full
-                    // operand would set the fixed point's accuracy instead
-                    q.Sin = w.S32;
-                    dim3 grid(ceil_div(R, 64), tiles_max);
-                    batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
-                    RQ_CUDA(h, cudaGetLastError());
-                    ++h->launches;
-                } else {
-                    // operand set read by this layer: 4..6 = s (3-way), else pair ((j-1)&1)
-                    const bool timed = h->prof_on && j > 0 && prof_used + 2 <= h->prof_ev.size();
-                    if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
-                    RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max,
-                                    ceil_div(active, kSlotTile) + h->nr - 1));
-                    ++h->launches;
-                    if (j > 0) {
-                        ++h->layer_launches;
-                        // three BF16 products of the (n+m) x (n+m) factored layer per active QP
-                        h->layer_flops += 2.0 * 3.0 * (double)R * (double)R * (double)active;
-                    }
-                    if (timed) {
-                        RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
-                        prof_used += 2;
-                    }
-                }
-            } else {
-                q.Sin = w.S32 + (size_t)(j & 1) * opart;
-                q.Sout = w.S32 + (size_t)((j + 1) & 1) * opart;
-                q.CK32 = w.CK32;
-                dim3 grid(ceil_div(R, 64), tiles_max);
-                const bool timed = h->prof_on && prof_used + 2 <= h->prof_ev.size();
-                if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
-                batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
-                RQ_CUDA(h, cudaGetLastError());
-                ++h->launches;
-                ++h->layer_launches;
-                h->layer_flops += 2.0 * (double)R * (double)R * (double)active;   // one FP32 product per QP
-                if (timed) {
-                    RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
-                    prof_used += 2;
-                }
-            }
-        }
+        RQ_TRY(run_layers(h, p, len, check, active, prof_used));
         it += len;
         if (check) {
-            BatchParams q = p;
-            if (bf16 && w.check_tc) {
-                q.CK = static_cast<__nv_bfloat16*>(w.CK);
-                RQ_TRY(tc_check(h, q, 1, tiles_max));
-                RQ_TRY(tc_check(h, q, 2, tiles_max));
-                h->launches += 2;
-            } else {
-                q.CK32 = w.CK32;
-                batch_check_fp32_kernel<<<dim3(ceil_div(n + m, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 1);
-                RQ_CUDA(h, cudaGetLastError());
-                batch_check_fp32_kernel<<<dim3(ceil_div(n, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 2);
-                RQ_CUDA(h, cudaGetLastError());
-                h->launches += 2;
-            }
+            RQ_TRY(run_check(h, p));
             DecideArgs d{B, it, last_chunk ? 1 : 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO,
-                         w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd};
+                         w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, 0, max_iter, nullptr, nullptr};
             batch_decide_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(p, d);
             RQ_CUDA(h, cudaGetLastError());
             ++h->launches;
         }
         if (last_chunk) break;
-        RQ_TRY(regroup(check));
+        RQ_TRY(regroup_slots(h, p, B, check));
         if (check) {
             int cnt[CNT_WORDS] = {0, 0, 0, 0};
             RQ_CUDA(h, cudaMemcpyAsync(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
@@ -872,5 +921,430 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return RELU_QP_OK;
 }
+
+}  // namespace rq
+
+// ===========================================================================
+// Continuous batching (serving).  A server holds several problem families,
+// each a handle with its own layer bank and batch slots.  Requests (a new
+// initial state x0 for one client of one family) wait in a host queue; at
+// every step each family admits waiting requests into its free QP slots
+// (parametric update of q, l, u, b and a warm start from the client's last
+// solution, kept on the device), runs one chunk (check_interval layers, the
+// residual check, the stop test and penalty rule) on its own stream, and
+// retires the QPs that finished.  Families' chunks overlap on the GPU.
+// ===========================================================================
+namespace rq {
+
+namespace {
+
+struct ServeDev {
+    int *idx = nullptr, *cl = nullptr, *client_of = nullptr, *done = nullptr, *cnt = nullptr;
+    float *x0c = nullptr, *Qc = nullptr, *Lc = nullptr, *Uc = nullptr, *Bc = nullptr, *AYc = nullptr, *Xc = nullptr;
+    float *out = nullptr;
+    float *Wx = nullptr, *Wl = nullptr;
+    int *Wr = nullptr, *Wv = nullptr;
+};
+
+// Admitted request j goes to QP index idx[j]: warm start from its client's
+// last solution (x, lam_std, rho index) if there is one, else cold.
+__global__ void serve_admit_kernel(BatchParams p, int k, const int* __restrict__ idx, const int* __restrict__ cl,
+                                   const float* __restrict__ Wx, const float* __restrict__ Wl,
+                                   const int* __restrict__ Wr, const int* __restrict__ Wv, int rho0, int* status,
+                                   int* rho_idx, int* iters, int* nsw, int* client_of, float* Xc) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= k) return;
+    const int qp = idx[j], c = cl[j];
+    const bool warm = c >= 0 && Wv[c] != 0;
+    for (int t = lane; t < p.n; t += 32) {
+        const float v = warm ? Wx[(size_t)c * p.ldn + t] : 0.f;
+        p.Y[(size_t)qp * p.ldn + t] = v;
+        Xc[(size_t)j * p.ldn + t] = v;
+    }
+    for (int i = lane; i < p.m; i += 32) p.LAM[(size_t)qp * p.ldm + i] = warm ? Wl[(size_t)c * p.ldm + i] : 0.f;
+    if (lane == 0) {
+        status[qp] = QP_ACTIVE;
+        rho_idx[qp] = warm ? Wr[c] : rho0;
+        iters[qp] = 0;
+        nsw[qp] = 0;
+        client_of[qp] = c;
+    }
+    if (lane < RW_WORDS) p.RED[(size_t)qp * RW_WORDS + lane] = 0u;
+}
+
+// Compact rows of the admitted requests -> their QP rows (q, l, u, every b_r,
+// and z = A x for the warm start, which also seeds the carried A x).
+__global__ void serve_scatter_kernel(BatchParams p, int k, const int* __restrict__ idx, const float* __restrict__ Qc,
+                                     const float* __restrict__ Lc, const float* __restrict__ Uc,
+                                     const float* __restrict__ Bc, const float* __restrict__ AYc, float* Q, float* L,
+                                     float* U, float* BIAS, float* QN) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= k) return;
+    const int qp = idx[j];
+    float qn = 0.f;
+    for (int t = lane; t < p.n; t += 32) {
+        const float v = Qc[(size_t)j * p.ldn + t];
+        Q[(size_t)qp * p.ldn + t] = v;
+        qn = fmaxf(qn, fabsf(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) qn = fmaxf(qn, __shfl_xor_sync(0xffffffffu, qn, o));
+    if (lane == 0) QN[qp] = qn;
+    for (int i = lane; i < p.m; i += 32) {
+        const size_t o = (size_t)qp * p.ldm + i, oc = (size_t)j * p.ldm + i;
+        L[o] = Lc[oc];
+        U[o] = Uc[oc];
+        p.AY[o] = AYc[oc];
+        p.Z[o] = AYc[oc];
+    }
+    for (int r = 0; r < p.nr; ++r)
+        for (int t = lane; t < p.R; t += 32)
+            BIAS[((size_t)r * p.cap + qp) * p.ldR + t] = Bc[((size_t)r * p.cap + j) * p.ldR + t];
+}
+
+// Finished QPs: pack [x | qp, status, iters, rho, switches, r_prim, r_dual] per
+// result, store the client's warm start, free the QP index.
+__global__ void serve_gather_kernel(BatchParams p, const int* __restrict__ done, const int* __restrict__ cnt,
+                                    const int* __restrict__ client_of, int* status, const int* __restrict__ iters,
+                                    const int* __restrict__ rho_idx, const int* __restrict__ nsw,
+                                    const float* __restrict__ rp, const float* __restrict__ rd,
+                                    const float* __restrict__ XO, float* Wx, float* Wl, int* Wr, int* Wv, float* out,
+                                    int ldo) {
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (j >= *cnt) return;
+    const int qp = done[j];
+    const int c = client_of[qp];
+    float* o = out + (size_t)j * ldo;
+    for (int t = lane; t < p.n; t += 32) o[t] = XO[(size_t)qp * p.n + t];
+    if (c >= 0) {
+        for (int t = lane; t < p.n; t += 32) Wx[(size_t)c * p.ldn + t] = p.Y[(size_t)qp * p.ldn + t];
+        for (int i = lane; i < p.m; i += 32) Wl[(size_t)c * p.ldm + i] = p.LSTD[(size_t)qp * p.ldm + i];
+    }
+    if (lane == 0) {
+        o[p.n + 0] = __int_as_float(qp);
+        o[p.n + 1] = __int_as_float(status[qp]);
+        o[p.n + 2] = __int_as_float(iters[qp]);
+        o[p.n + 3] = __int_as_float(rho_idx[qp]);
+        o[p.n + 4] = __int_as_float(nsw[qp]);
+        o[p.n + 5] = rp[qp];
+        o[p.n + 6] = rd[qp];
+        if (c >= 0) {
+            Wr[c] = rho_idx[qp];
+            Wv[c] = 1;
+        }
+        status[qp] = QP_UNUSED;
+    }
+}
+
+}  // namespace
+
+struct ServeRequest {
+    int client;
+    long long tag;
+    double t_submit;
+    std::vector<float> x0;
+};
+
+struct ServeFamily {
+    relu_qp_t h = nullptr;
+    cudaStream_t stream = nullptr, saved_stream = nullptr;
+    int cap = 0, clients = 0, active = 0, ldo = 0, rho0 = 0;
+    std::deque<ServeRequest> queue;
+    std::vector<int> free_idx;
+    std::vector<long long> tag_of;
+    std::vector<double> t_submit_of;
+    std::vector<int> client_of;
+    ServeDev d;
+    float* h_x0c = nullptr;
+    int *h_idx = nullptr, *h_cl = nullptr, *h_cnt = nullptr;
+    float* h_out = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool launched = false;
+    std::vector<void*> dev_allocs, host_allocs;
+};
+
+struct ServeResult {
+    relu_qp_result r;
+    std::vector<float> x;
+};
+
+}  // namespace rq
+
+struct relu_qp_server_s {
+    std::vector<rq::ServeFamily> fam;
+    std::deque<rq::ServeResult> results;
+    double eps_abs = 1e-3, eps_rel = 0.0;
+    int max_iter = 4000;
+    std::chrono::steady_clock::time_point t0;
+    std::string err;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace rq {
+
+namespace {
+
+int sfail(relu_qp_server_t s, int code, const std::string& msg) {
+    s->err = msg;
+    return code;
+}
+
+template <typename T>
+int sdev(relu_qp_server_t s, ServeFamily& f, T** p, size_t count) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(s, RELU_QP_ERR_OOM, std::string("server device buffer: ") + cudaGetErrorString(e));
+    }
+    cudaMemset(q, 0, count * sizeof(T) + 16);
+    f.dev_allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return RELU_QP_OK;
+}
+
+template <typename T>
+int shost(relu_qp_server_t s, ServeFamily& f, T** p, size_t count) {
+    void* q = nullptr;
+    const cudaError_t e = cudaMallocHost(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(s, RELU_QP_ERR_OOM, std::string("server pinned buffer: ") + cudaGetErrorString(e));
+    }
+    f.host_allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return RELU_QP_OK;
+}
+
+#define RQ_SCUDA(s, call)                                                                        \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            cudaGetLastError();                                                                  \
+            return sfail((s), RELU_QP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                        \
+    } while (0)
+
+int family_launch(relu_qp_server_t s, ServeFamily& f) {
+    relu_qp_t h = f.h;
+    BatchWork& w = h->bw;
+    const int n = h->n, m = h->m, R = h->R, nx = w.nx;
+    BatchParams p = base_params(h);
+    // ---- admission ----
+    const int k = (int)std::min(f.queue.size(), f.free_idx.size());
+    if (k > 0) {
+        for (int j = 0; j < k; ++j) {
+            ServeRequest rq_ = std::move(f.queue.front());
+            f.queue.pop_front();
+            const int qp = f.free_idx.back();
+            f.free_idx.pop_back();
+            f.h_idx[j] = qp;
+            f.h_cl[j] = rq_.client;
+            std::memcpy(f.h_x0c + (size_t)j * w.ldx, rq_.x0.data(), sizeof(float) * nx);
+            f.tag_of[qp] = rq_.tag;
+            f.t_submit_of[qp] = rq_.t_submit;
+            f.client_of[qp] = rq_.client;
+        }
+        f.active += k;
+        RQ_SCUDA(s, cudaMemcpyAsync(f.d.x0c, f.h_x0c, sizeof(float) * k * w.ldx, cudaMemcpyHostToDevice, f.stream));
+        RQ_SCUDA(s, cudaMemcpyAsync(f.d.idx, f.h_idx, sizeof(int) * k, cudaMemcpyHostToDevice, f.stream));
+        RQ_SCUDA(s, cudaMemcpyAsync(f.d.cl, f.h_cl, sizeof(int) * k, cudaMemcpyHostToDevice, f.stream));
+        serve_admit_kernel<<<ceil_div(k * 32, 256), 256, 0, f.stream>>>(p, k, f.d.idx, f.d.cl, f.d.Wx, f.d.Wl, f.d.Wr,
+                                                                       f.d.Wv, f.rho0, w.status, w.rho_idx, w.iters,
+                                                                       w.nsw, f.d.client_of, f.d.Xc);
+        RQ_SCUDA(s, cudaGetLastError());
+        ++h->launches;
+        RQ_TRY(sgemm_nt(h, k, n, nx, f.d.x0c, w.ldx, w.F32, w.ldx, 1.f, nullptr, f.d.Qc, w.ldn));
+        if (m > 0) {
+            RQ_TRY(sgemm_nt(h, k, m, nx, f.d.x0c, w.ldx, w.E32, w.ldx, -1.f, w.l0, f.d.Lc, w.ldm));
+            RQ_TRY(sgemm_nt(h, k, m, nx, f.d.x0c, w.ldx, w.E32, w.ldx, -1.f, w.u0, f.d.Uc, w.ldm));
+            RQ_TRY(sgemm_nt(h, k, m, n, f.d.Xc, w.ldn, h->A32, (int)round_up(n, 4), 1.f, nullptr, f.d.AYc, w.ldm));
+        }
+        for (int r = 0; r < h->nr; ++r)
+            RQ_TRY(sgemm_nt(h, k, R, nx, f.d.x0c, w.ldx, w.G[r], w.ldx, 1.f, nullptr,
+                            f.d.Bc + (size_t)r * w.cap * w.ldR, w.ldR));
+        serve_scatter_kernel<<<ceil_div(k * 32, 256), 256, 0, f.stream>>>(p, k, f.d.idx, f.d.Qc, f.d.Lc, f.d.Uc,
+                                                                         f.d.Bc, f.d.AYc, w.Q, w.L, w.U, w.BIAS,
+                                                                         w.QN);
+        RQ_SCUDA(s, cudaGetLastError());
+        ++h->launches;
+    }
+    if (f.active == 0) return RELU_QP_OK;
+    // ---- one chunk ----
+    const int ci = h->opts.check_interval;
+    size_t prof_used = 0;
+    RQ_TRY(regroup_slots(h, p, w.cap, true));
+    RQ_TRY(run_layers(h, p, ci, true, f.active, prof_used));
+    RQ_TRY(run_check(h, p));
+    RQ_SCUDA(s, cudaMemsetAsync(f.d.cnt, 0, sizeof(int), f.stream));
+    DecideArgs dd{w.cap, 0, 0, h->opts.adaptive_rho, s->eps_abs, s->eps_rel, w.XO, w.ZO, w.LO,
+                  w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, ci, s->max_iter, f.d.done, f.d.cnt};
+    batch_decide_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(p, dd);
+    RQ_SCUDA(s, cudaGetLastError());
+    serve_gather_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(
+        p, f.d.done, f.d.cnt, f.d.client_of, w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, w.XO, f.d.Wx, f.d.Wl,
+        f.d.Wr, f.d.Wv, f.d.out, f.ldo);
+    RQ_SCUDA(s, cudaGetLastError());
+    h->launches += 2;
+    RQ_SCUDA(s, cudaMemcpyAsync(f.h_cnt, f.d.cnt, sizeof(int), cudaMemcpyDeviceToHost, f.stream));
+    RQ_SCUDA(s, cudaMemcpyAsync(f.h_cnt + 1, w.counters, sizeof(int) * CNT_WORDS, cudaMemcpyDeviceToHost, f.stream));
+    RQ_SCUDA(s, cudaMemcpyAsync(f.h_out, f.d.out, sizeof(float) * (size_t)w.cap * f.ldo, cudaMemcpyDeviceToHost,
+                                f.stream));
+    RQ_SCUDA(s, cudaEventRecord(f.ev, f.stream));
+    f.launched = true;
+    return RELU_QP_OK;
+}
+
+int family_collect(relu_qp_server_t s, ServeFamily& f, int fi) {
+    if (!f.launched) return RELU_QP_OK;
+    f.launched = false;
+    RQ_SCUDA(s, cudaEventSynchronize(f.ev));
+    const double t = s->now();
+    if (f.h_cnt[1 + CNT_ERR]) return sfail(s, RELU_QP_ERR_TIMEOUT, "a tensor-core kernel wait passed its deadline");
+    const int cnt = f.h_cnt[0];
+    const int n = f.h->n;
+    for (int j = 0; j < cnt; ++j) {
+        const float* o = f.h_out + (size_t)j * f.ldo;
+        ServeResult res;
+        const int qp = __float_as_int_host(o[n + 0]);
+        res.r.tag = f.tag_of[qp];
+        res.r.family = fi;
+        res.r.client = f.client_of[qp];
+        res.r.status = __float_as_int_host(o[n + 1]);
+        res.r.iters = __float_as_int_host(o[n + 2]);
+        res.r.rho_index = __float_as_int_host(o[n + 3]);
+        res.r.rho_switches = __float_as_int_host(o[n + 4]);
+        res.r.r_prim = o[n + 5];
+        res.r.r_dual = o[n + 6];
+        res.r.t_submit = f.t_submit_of[qp];
+        res.r.t_done = t;
+        res.x.assign(o, o + n);
+        s->results.push_back(std::move(res));
+        f.free_idx.push_back(qp);
+        --f.active;
+    }
+    return RELU_QP_OK;
+}
+
+}  // namespace
+
+int server_create(relu_qp_server_t* out, relu_qp_t const* families, int nf, const int* clients, double eps_abs,
+                  double eps_rel, int max_iter) {
+    relu_qp_server_t s = new (std::nothrow) relu_qp_server_s;
+    if (!s) return RELU_QP_ERR_OOM;
+    *out = s;
+    s->eps_abs = eps_abs;
+    s->eps_rel = eps_rel;
+    s->max_iter = max_iter;
+    s->t0 = std::chrono::steady_clock::now();
+    s->fam.resize(nf);
+    for (int fi = 0; fi < nf; ++fi) {
+        ServeFamily& f = s->fam[fi];
+        relu_qp_t h = families[fi];
+        BatchWork& w = h->bw;
+        f.h = h;
+        f.cap = w.cap;
+        f.clients = clients ? clients[fi] : 0;
+        f.ldo = h->n + 8;
+        f.rho0 = nearest_rho(h, h->opts.rho0);
+        f.tag_of.assign(f.cap, 0);
+        f.t_submit_of.assign(f.cap, 0.0);
+        f.client_of.assign(f.cap, -1);
+        for (int q = f.cap - 1; q >= 0; --q) f.free_idx.push_back(q);
+        RQ_SCUDA(s, cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking));
+        RQ_SCUDA(s, cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
+        f.saved_stream = h->stream;
+        h->stream = f.stream;
+        const size_t cap = f.cap, cl = f.clients > 0 ? f.clients : 1;
+        RQ_TRY(sdev(s, f, &f.d.idx, cap));
+        RQ_TRY(sdev(s, f, &f.d.cl, cap));
+        RQ_TRY(sdev(s, f, &f.d.client_of, cap));
+        RQ_TRY(sdev(s, f, &f.d.done, cap));
+        RQ_TRY(sdev(s, f, &f.d.cnt, 4));
+        RQ_TRY(sdev(s, f, &f.d.x0c, cap * w.ldx));
+        RQ_TRY(sdev(s, f, &f.d.Qc, cap * w.ldn));
+        RQ_TRY(sdev(s, f, &f.d.Xc, cap * w.ldn));
+        RQ_TRY(sdev(s, f, &f.d.Lc, cap * w.ldm));
+        RQ_TRY(sdev(s, f, &f.d.Uc, cap * w.ldm));
+        RQ_TRY(sdev(s, f, &f.d.AYc, cap * w.ldm));
+        RQ_TRY(sdev(s, f, &f.d.Bc, (size_t)h->nr * cap * w.ldR));
+        RQ_TRY(sdev(s, f, &f.d.out, cap * f.ldo));
+        RQ_TRY(sdev(s, f, &f.d.Wx, cl * w.ldn));
+        RQ_TRY(sdev(s, f, &f.d.Wl, cl * w.ldm));
+        RQ_TRY(sdev(s, f, &f.d.Wr, cl));
+        RQ_TRY(sdev(s, f, &f.d.Wv, cl));
+        RQ_TRY(shost(s, f, &f.h_x0c, cap * w.ldx));
+        RQ_TRY(shost(s, f, &f.h_idx, cap));
+        RQ_TRY(shost(s, f, &f.h_cl, cap));
+        RQ_TRY(shost(s, f, &f.h_cnt, 8));
+        RQ_TRY(shost(s, f, &f.h_out, cap * f.ldo));
+        // every QP index starts free
+        batch_init_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(base_params(h), 0, 0, 0, nullptr, f.rho0,
+                                                                           w.status, w.rho_idx, w.iters, w.nsw);
+        RQ_SCUDA(s, cudaGetLastError());
+        RQ_SCUDA(s, cudaMemsetAsync(w.counters, 0, sizeof(int) * CNT_WORDS, f.stream));
+        RQ_SCUDA(s, cudaStreamSynchronize(f.stream));
+    }
+    return RELU_QP_OK;
+}
+
+int server_submit(relu_qp_server_t s, int family, int client, const float* x0, long long tag) {
+    ServeFamily& f = s->fam[family];
+    ServeRequest r;
+    r.client = client;
+    r.tag = tag;
+    r.t_submit = s->now();
+    r.x0.assign(x0, x0 + f.h->bw.nx);
+    f.queue.push_back(std::move(r));
+    return RELU_QP_OK;
+}
+
+int server_step(relu_qp_server_t s, int* active, int* waiting) {
+    for (auto& f : s->fam) RQ_TRY(family_launch(s, f));
+    for (size_t fi = 0; fi < s->fam.size(); ++fi) RQ_TRY(family_collect(s, s->fam[fi], (int)fi));
+    int a = 0, q = 0;
+    for (auto& f : s->fam) {
+        a += f.active;
+        q += (int)f.queue.size();
+    }
+    if (active) *active = a;
+    if (waiting) *waiting = q;
+    return RELU_QP_OK;
+}
+
+int server_poll(relu_qp_server_t s, int max_results, relu_qp_result* results, float* x_out, int x_stride) {
+    int k = 0;
+    while (k < max_results && !s->results.empty()) {
+        ServeResult& r = s->results.front();
+        if (results) results[k] = r.r;
+        if (x_out) std::memcpy(x_out + (size_t)k * x_stride, r.x.data(), sizeof(float) * r.x.size());
+        s->results.pop_front();
+        ++k;
+    }
+    return k;
+}
+
+void server_destroy(relu_qp_server_t s) {
+    for (auto& f : s->fam) {
+        if (f.stream) cudaStreamSynchronize(f.stream);
+        if (f.h) f.h->stream = f.saved_stream;
+        for (void* p : f.dev_allocs) cudaFree(p);
+        for (void* p : f.host_allocs) cudaFreeHost(p);
+        if (f.ev) cudaEventDestroy(f.ev);
+        if (f.stream) cudaStreamDestroy(f.stream);
+    }
+    delete s;
+}
+
+const char* server_error(relu_qp_server_t s) { return s->err.c_str(); }
+int server_families(relu_qp_server_t s) { return (int)s->fam.size(); }
+int server_clients(relu_qp_server_t s, int family) { return s->fam[family].clients; }
+int server_nx(relu_qp_server_t s, int family) { return s->fam[family].h->bw.nx; }
+double server_clock(relu_qp_server_t s) { return s->now(); }
 
 }  // namespace rq

@@ -168,6 +168,18 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
 int pack_bf16_layer(relu_qp_t h, int r, const double* X, const double* AX);
 int pack_bf16_check(relu_qp_t h, const double* dP, const double* dA);
 int batch_finish_setup(relu_qp_t h);
+// Continuous batching (batch.cu).
+int server_create(relu_qp_server_t* out, relu_qp_t const* families, int nf, const int* clients, double eps_abs,
+                  double eps_rel, int max_iter);
+int server_submit(relu_qp_server_t s, int family, int client, const float* x0, long long tag);
+int server_step(relu_qp_server_t s, int* active, int* waiting);
+int server_poll(relu_qp_server_t s, int max_results, relu_qp_result* results, float* x_out, int x_stride);
+void server_destroy(relu_qp_server_t s);
+const char* server_error(relu_qp_server_t s);
+double server_clock(relu_qp_server_t s);
+int server_families(relu_qp_server_t s);
+int server_clients(relu_qp_server_t s, int family);
+int server_nx(relu_qp_server_t s, int family);
 void batch_release(relu_qp_t h);
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
