@@ -183,7 +183,7 @@ def profiled_traffic():
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_launch"]), float(vals["algorithmic_flops_per_launch"].split()[0])
     except (KeyError, ValueError):
         return None
 
@@ -350,8 +350,13 @@ def run_ours(args):
     if prof["layer_timed"] > 0 and prof["layer_ms"] > 0:
         flops_per_launch = prof["layer_flops"] / max(prof["layer_launches"], 1)
         achieved = prof["layer_flops"] / (prof["layer_ms"] / 1e3) / 1e12
+        tr = profiled_traffic()
+        # the capture is a full-batch launch; scale its bytes to the average launch by the work it does
+        traffic = None if tr is None else tr[0] * flops_per_launch / tr[1]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
-                "frac": achieved / peak_sus, "traffic": profiled_traffic(),
+                "frac": achieved / peak_sus, "traffic": traffic,
+                "traffic_basis": "ncu dram bytes of a full-batch launch (profiles/tc_layer_refined_batched_n800.md)"
+                                 " scaled by the average launch's QPs",
                 "kernel": "tc_gemm_kernel refined layer (3 BF16 products, FP32 accumulate in TMEM)",
                 "peak_kind": f"bf16 sustained, {peak_kind}",
                 "launches_timed": prof["layer_timed"], "avg_launch_us": 1e3 * prof["layer_ms"] / prof["layer_timed"],
