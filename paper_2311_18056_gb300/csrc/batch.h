@@ -133,59 +133,53 @@ __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int q
     }
 }
 
-__device__ __forceinline__ void ld16(const float* __restrict__ src, float (&v)[16]) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float4 a = s4[k];
-        v[4 * k] = a.x;
-        v[4 * k + 1] = a.y;
-        v[4 * k + 2] = a.z;
-        v[4 * k + 3] = a.w;
-    }
+__device__ __forceinline__ void ld4(const float* __restrict__ src, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4*>(src);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
 }
 
-__device__ __forceinline__ void st16(float* __restrict__ dst, const float (&v)[16]) {
-    float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) d4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+__device__ __forceinline__ void st4(float* __restrict__ dst, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// layer_elem for 16 consecutive rows r0..r0+15 of one QP that are all x rows
-// or all Ax rows, with every row-vector access 16-byte aligned (r0 and, for Ax
-// rows, r0 - n multiples of 4): all loads of the chunk are issued before any
-// arithmetic so that one L2 round trip serves the 16 rows.
-__device__ __forceinline__ void layer_chunk16(const BatchParams& p, int slot, int qp, int ri, int r0,
-                                              const float (&acc)[16]) {
+// layer_elem for 4 consecutive rows r0..r0+3 of one QP, all x rows or all Ax
+// rows, 16-byte aligned.  The tensor-core epilogue maps 4 lanes to the 16
+// rows of one QP so that a warp-wide 128-bit access covers 8 QPs' contiguous
+// 64-byte row segments instead of 32 scattered 16-byte pieces.
+__device__ __forceinline__ void layer_chunk4(const BatchParams& p, int slot, int qp, int ri, int r0,
+                                             const float (&acc)[4]) {
     const unsigned f = p.flags;
     const size_t oR = (size_t)qp * p.ldR + r0;
     const bool refine_only = (f & EPI_REFINE) && !(f & EPI_REBASE);
-    float t[16], sref[16], s_new[16];
-    ld16(refine_only ? p.C + oR : p.BIAS + (size_t)ri * p.cap * p.ldR + oR, t);
-    if (refine_only) ld16(p.SREF + oR, sref);
+    float t[4], sref[4], s_new[4];
+    ld4(refine_only ? p.C + oR : p.BIAS + (size_t)ri * p.cap * p.ldR + oR, t);
+    if (refine_only) ld4(p.SREF + oR, sref);
     if (r0 < p.n) {
         float* y = p.Y + (size_t)qp * p.ldn + r0;
-        if (f & EPI_REBASE) ld16(y, sref);
+        if (f & EPI_REBASE) ld4(y, sref);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 4; ++k) {
             t[k] += acc[k];
             s_new[k] = t[k];
         }
-        st16(y, t);
+        st4(y, t);
         if (f & EPI_CHECK)
-            for (int k = 0; k < 16; ++k) put_check(p, slot, r0 + k, t[k]);
+            for (int k = 0; k < 4; ++k) put_check(p, slot, r0 + k, t[k]);
     } else {
         const int i0 = r0 - p.n;
         const size_t o = (size_t)qp * p.ldm + i0;
-        float ay[16], zz[16], lm[16], lo[16], up[16], rs[16];
-        ld16(p.AY + o, ay);
-        ld16(p.Z + o, zz);
-        ld16(p.LAM + o, lm);
-        ld16(p.L + o, lo);
-        ld16(p.U + o, up);
-        ld16(p.rs + i0, rs);
+        float ay[4], zz[4], lm[4], lo[4], up[4], rs[4];
+        ld4(p.AY + o, ay);
+        ld4(p.Z + o, zz);
+        ld4(p.LAM + o, lm);
+        ld4(p.L + o, lo);
+        ld4(p.U + o, up);
+        ld4(p.rs + i0, rs);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
+        for (int k = 0; k < 4; ++k) {
             t[k] += acc[k];
             const float rho_i = p.rho[ri] * rs[k];
             if (f & EPI_REBASE) sref[k] = 2.f * rho_i * zz[k] - lm[k];
@@ -196,28 +190,29 @@ __device__ __forceinline__ void layer_chunk16(const BatchParams& p, int slot, in
             lm[k] = ln;
             s_new[k] = 2.f * rho_i * zn - ln;
         }
-        st16(p.AY + o, t);
-        st16(p.Z + o, zz);
-        st16(p.LAM + o, lm);
+        st4(p.AY + o, t);
+        st4(p.Z + o, zz);
+        st4(p.LAM + o, lm);
     }
     if (f & EPI_REBASE) {
-        st16(p.C + oR, t);
-        st16(p.SREF + oR, sref);
+        st4(p.C + oR, t);
+        st4(p.SREF + oR, sref);
     }
     if (!(f & EPI_LAST)) {
         const size_t so = (size_t)slot * p.ldk + r0;
         if (f & EPI_REFINE) {
-            __align__(16) __nv_bfloat16 hi[16], lo[16];
+            __nv_bfloat16 hi[4], lo[4];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) split2(s_new[k] - sref[k], hi[k], lo[k]);
-            uint4* dh = reinterpret_cast<uint4*>(p.Dhi + so);
-            uint4* dl = reinterpret_cast<uint4*>(p.Dlo + so);
-            dh[0] = reinterpret_cast<const uint4*>(hi)[0];
-            dh[1] = reinterpret_cast<const uint4*>(hi)[1];
-            dl[0] = reinterpret_cast<const uint4*>(lo)[0];
-            dl[1] = reinterpret_cast<const uint4*>(lo)[1];
+            for (int k = 0; k < 4; ++k) split2(s_new[k] - sref[k], hi[k], lo[k]);
+            uint2 vh, vl;
+            vh.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
+            vh.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
+            vl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
+            vl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
+            *reinterpret_cast<uint2*>(p.Dhi + so) = vh;
+            *reinterpret_cast<uint2*>(p.Dlo + so) = vl;
         } else {
-            st16(p.Sout + so, s_new);
+            st4(p.Sout + so, s_new);
         }
     }
 }

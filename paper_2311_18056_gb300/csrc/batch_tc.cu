@@ -153,7 +153,8 @@ struct TcSmem {
     static constexpr int kA = NA * kTileBytesA;
     static constexpr int kB = NB * BN * 128;
     static constexpr int kStage = kA + kB;
-    static constexpr int kBytes = STAGES * kStage + 1024 /* align */ + 256 /* barriers */;
+    static constexpr int kXpose = 8 * 32 * 17 * 4;      // epilogue transpose buffers (8 warps)
+    static constexpr int kBytes = STAGES * kStage + kXpose + 1024 /* align */ + 256 /* barriers */;
 };
 
 // ---------------------------------------------------------------------------
@@ -180,7 +181,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage);
+    float* xpose = reinterpret_cast<float*>(smem + STAGES * L::kStage);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose);
     // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready; then the TMEM address
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
     __shared__ int s_fail;
@@ -289,20 +291,37 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
             float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
             const bool n_aligned = (p.n & 3) == 0;
+            float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
             for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
                 float v[16], w[16];
                 tmem_ld16(tl + c0, v);
                 tmem_ld16(tl + BN + c0, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
-                if (qp < 0) continue;
                 const int r0 = row0 + c0;
                 const bool whole = MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows &&
                                    (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
                 if (whole) {
-                    layer_chunk16(p, slot, qp, ri, r0, v);
+                    // transpose through shared memory: 4 lanes per QP, 4 rows per lane
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
+                    __syncwarp();
+#pragma unroll
+                    for (int pass = 0; pass < 4; ++pass) {
+                        const int sl = pass * 8 + (lane >> 2);          // slot within the warp's 32
+                        const int cg = (lane & 3) * 4;                  // first of this lane's 4 rows
+                        const int qq = __shfl_sync(0xffffffffu, qp, sl);
+                        if (qq >= 0) {
+                            float a4[4];
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) a4[t] = xb[sl * 17 + cg + t];
+                            layer_chunk4(p, slot0 + q * 32 + sl, qq, ri, r0 + cg, a4);
+                        }
+                    }
+                    __syncwarp();
                     continue;
                 }
+                if (qp < 0) continue;
 #pragma unroll 4
                 for (int t = 0; t < 16; ++t) {
                     const int r = r0 + t;
@@ -365,7 +384,7 @@ template <int MODE, int BN>
 constexpr int stages_for() {
     using L1 = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, 1>;
     constexpr int budget = 220 * 1024;
-    constexpr int s = (budget - 1024 - 256) / L1::kStage;
+    constexpr int s = (budget - 1024 - 256 - L1::kXpose) / L1::kStage;
     return s > 4 ? 4 : s;
 }
 
