@@ -539,24 +539,24 @@ int batch_alloc(relu_qp_t h) {
     return RELU_QP_OK;
 }
 
-__global__ void tune_perm_kernel(int slots, int cap, int* perm, int* tile_rho, int* counters) {
+__global__ void tune_perm_kernel(int slots, int cap, int active_tiles, int* perm, int* tile_rho, int* counters) {
+    const int live = min(cap, active_tiles * kSlotTile);
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += gridDim.x * blockDim.x) {
-        perm[s] = s < cap ? s : -1;
+        perm[s] = s < live ? s : -1;
         if (s % kSlotTile == 0) tile_rho[s / kSlotTile] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        counters[CNT_TILES] = (cap + kSlotTile - 1) / kSlotTile;
-        counters[CNT_ACTIVE] = cap;
+        counters[CNT_TILES] = active_tiles;
+        counters[CNT_ACTIVE] = live;
     }
 }
 
-// Choose the BN (rows per tile) of the tcgen05 layer and check kernels by
-// timing them on the full batch capacity (state values do not matter here;
-// every buffer they touch is re-initialised by the next solve).
+// Choose the BN (rows per tile) of the tcgen05 layer for every number of
+// active slot tiles, and of the check kernels on the full capacity, by timing
+// them (state values do not matter here; every buffer they touch is
+// re-initialised by the next solve).
 int tc_tune(relu_qp_t h) {
     BatchWork& w = h->bw;
-    tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, w.perm, w.tile_rho, w.counters);
-    RQ_CUDA(h, cudaGetLastError());
     BatchParams p = base_params(h);
     const size_t opart = (size_t)w.slots * w.ldk;
     __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
@@ -565,20 +565,39 @@ int tc_tune(relu_qp_t h) {
     p.Dlo = OP + 3 * opart;
     p.CK = static_cast<__nv_bfloat16*>(w.CK);
     const int tiles = w.slots / kSlotTile;
-    const int cands[4] = {64, 128, 192, 256};
-    float best = 1e30f;
-    int best_bn = 128;
-    for (int bn : cands) {
-        RQ_TRY(tc_set_tiles(h, bn, 128));
-        for (int rep = 0; rep < 2; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, tiles));
-        RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-        for (int rep = 0; rep < 5; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, tiles));
-        RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
-        RQ_CUDA(h, cudaEventSynchronize(h->ev1));
-        float ms = 0.f;
-        RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-        if (ms < best) { best = ms; best_bn = bn; }
+    int widths[16];
+    const int nw = tc_layer_widths(widths, 16);
+    // measured tile counts: every count up to 8, then every 4th up to 32, then every 16th
+    std::vector<int> counts;
+    for (int t = 1; t <= tiles; ++t)
+        if (t <= 8 || (t <= 32 && t % 4 == 0) || t % 16 == 0 || t == tiles) counts.push_back(t);
+    std::vector<int> table(tiles + 1, 128);
+    int best_full = 128;
+    for (int t : counts) {
+        tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, t, w.perm, w.tile_rho,
+                                                                         w.counters);
+        RQ_CUDA(h, cudaGetLastError());
+        float best = 1e30f;
+        int best_bn = 128;
+        for (int i = 0; i < nw; ++i) {
+            const int bn = widths[i];
+            RQ_TRY(tc_set_tiles(h, bn, 128));
+            RQ_TRY(tc_layer(h, p, 0, tiles, t));
+            RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+            for (int rep = 0; rep < 3; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, t));
+            RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+            RQ_CUDA(h, cudaEventSynchronize(h->ev1));
+            float ms = 0.f;
+            RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+            if (ms < best) { best = ms; best_bn = bn; }
+        }
+        for (int u = t; u <= tiles; ++u) table[u] = best_bn;   // until the next measured count
+        best_full = best_bn;
     }
+    tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, tiles, w.perm, w.tile_rho,
+                                                                     w.counters);
+    RQ_CUDA(h, cudaGetLastError());
+    const int best_bn = best_full;
     float bestc = 1e30f;
     int best_cbn = 128;
     for (int bn : {64, 128}) {
@@ -599,6 +618,7 @@ int tc_tune(relu_qp_t h) {
         if (ms < bestc) { bestc = ms; best_cbn = bn; }
     }
     RQ_TRY(tc_set_tiles(h, best_bn, best_cbn));
+    RQ_TRY(tc_set_tiles_for(h, table));
     if (tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "tensor-core kernel wait passed its deadline while tuning");
     RQ_CUDA(h, cudaMemsetAsync(w.RED, 0, sizeof(unsigned) * (size_t)w.cap * RW_WORDS, h->stream));
     RQ_CUDA(h, cudaMemsetAsync(w.counters, 0, sizeof(int) * CNT_WORDS, h->stream));

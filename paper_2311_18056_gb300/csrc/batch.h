@@ -16,6 +16,8 @@
 
 #include <cuda_bf16.h>
 
+#include <vector>
+
 namespace rq {
 
 constexpr int kSlotTile = 128;        // slots per GEMM tile (the tcgen05 M dimension)
@@ -146,64 +148,77 @@ __device__ __forceinline__ void st4(float* __restrict__ dst, const float (&v)[4]
 }
 
 // layer_elem for 4 consecutive rows r0..r0+3 of one QP, all x rows or all Ax
-// rows, 16-byte aligned.  The tensor-core epilogue maps 4 lanes to the 16
-// rows of one QP so that a warp-wide 128-bit access covers 8 QPs' contiguous
-// 64-byte row segments instead of 32 scattered 16-byte pieces.
-__device__ __forceinline__ void layer_chunk4(const BatchParams& p, int slot, int qp, int ri, int r0,
-                                             const float (&acc)[4]) {
+// rows, 16-byte aligned, in two halves: chunk4_load reads every input the
+// layer needs (none of it depends on the product) and chunk4_apply combines it
+// with the product and writes the new state.  The tensor-core epilogue issues
+// the loads of all its 4-row pieces before the first apply, so one memory
+// round trip covers 16 rows of 8 QPs; 4 lanes per QP make each warp-wide
+// 128-bit access cover 8 QPs' contiguous 64-byte row segments.
+struct Chunk4 {
+    float t[4], sref[4], ay[4], zz[4], lm[4], lo[4], up[4];
+};
+
+__device__ __forceinline__ void chunk4_load(const BatchParams& p, int qp, int ri, int r0, Chunk4& c) {
     const unsigned f = p.flags;
     const size_t oR = (size_t)qp * p.ldR + r0;
     const bool refine_only = (f & EPI_REFINE) && !(f & EPI_REBASE);
-    float t[4], sref[4], s_new[4];
-    ld4(refine_only ? p.C + oR : p.BIAS + (size_t)ri * p.cap * p.ldR + oR, t);
-    if (refine_only) ld4(p.SREF + oR, sref);
+    ld4(refine_only ? p.C + oR : p.BIAS + (size_t)ri * p.cap * p.ldR + oR, c.t);
+    if (refine_only) ld4(p.SREF + oR, c.sref);
     if (r0 < p.n) {
-        float* y = p.Y + (size_t)qp * p.ldn + r0;
-        if (f & EPI_REBASE) ld4(y, sref);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            t[k] += acc[k];
-            s_new[k] = t[k];
-        }
-        st4(y, t);
-        if (f & EPI_CHECK)
-            for (int k = 0; k < 4; ++k) put_check(p, slot, r0 + k, t[k]);
+        if (f & EPI_REBASE) ld4(p.Y + (size_t)qp * p.ldn + r0, c.sref);
     } else {
-        const int i0 = r0 - p.n;
-        const size_t o = (size_t)qp * p.ldm + i0;
-        float ay[4], zz[4], lm[4], lo[4], up[4], rs[4];
-        ld4(p.AY + o, ay);
-        ld4(p.Z + o, zz);
-        ld4(p.LAM + o, lm);
-        ld4(p.L + o, lo);
-        ld4(p.U + o, up);
-        ld4(p.rs + i0, rs);
+        const size_t o = (size_t)qp * p.ldm + (r0 - p.n);
+        ld4(p.AY + o, c.ay);
+        ld4(p.Z + o, c.zz);
+        ld4(p.LAM + o, c.lm);
+        ld4(p.L + o, c.lo);
+        ld4(p.U + o, c.up);
+    }
+}
+
+// rs = p.rs[r0 - n .. r0 - n + 3] for Ax rows (unused for x rows)
+__device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int qp, int ri, int r0,
+                                             const float (&acc)[4], Chunk4& c, const float (&rs)[4]) {
+    const unsigned f = p.flags;
+    const size_t oR = (size_t)qp * p.ldR + r0;
+    float s_new[4];
+    if (r0 < p.n) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            t[k] += acc[k];
+            c.t[k] += acc[k];
+            s_new[k] = c.t[k];
+        }
+        st4(p.Y + (size_t)qp * p.ldn + r0, c.t);
+        if (f & EPI_CHECK)
+            for (int k = 0; k < 4; ++k) put_check(p, slot, r0 + k, c.t[k]);
+    } else {
+        const size_t o = (size_t)qp * p.ldm + (r0 - p.n);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c.t[k] += acc[k];
             const float rho_i = p.rho[ri] * rs[k];
-            if (f & EPI_REBASE) sref[k] = 2.f * rho_i * zz[k] - lm[k];
-            const float rr = ay[k] - zz[k] + lm[k] / rho_i;
-            const float zn = fminf(fmaxf(t[k] + rr, lo[k]), up[k]);
+            if (f & EPI_REBASE) c.sref[k] = 2.f * rho_i * c.zz[k] - c.lm[k];
+            const float rr = c.ay[k] - c.zz[k] + c.lm[k] / rho_i;
+            const float zn = fminf(fmaxf(c.t[k] + rr, c.lo[k]), c.up[k]);
             const float ln = rho_i * rr;
-            zz[k] = zn;
-            lm[k] = ln;
+            c.zz[k] = zn;
+            c.lm[k] = ln;
             s_new[k] = 2.f * rho_i * zn - ln;
         }
-        st4(p.AY + o, t);
-        st4(p.Z + o, zz);
-        st4(p.LAM + o, lm);
+        st4(p.AY + o, c.t);
+        st4(p.Z + o, c.zz);
+        st4(p.LAM + o, c.lm);
     }
     if (f & EPI_REBASE) {
-        st4(p.C + oR, t);
-        st4(p.SREF + oR, sref);
+        st4(p.C + oR, c.t);
+        st4(p.SREF + oR, c.sref);
     }
     if (!(f & EPI_LAST)) {
         const size_t so = (size_t)slot * p.ldk + r0;
         if (f & EPI_REFINE) {
             __nv_bfloat16 hi[4], lo[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) split2(s_new[k] - sref[k], hi[k], lo[k]);
+            for (int k = 0; k < 4; ++k) split2(s_new[k] - c.sref[k], hi[k], lo[k]);
             uint2 vh, vl;
             vh.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
             vh.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
@@ -256,7 +271,9 @@ int tc_prepare(relu_qp_t h);                     // BF16 splits of every W_rho a
 int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles);
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phase 1: [P; A] x, 2: A^T lam
 void tc_release(relu_qp_t h);
-int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);
+int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);           // one refined width for every batch size
+int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles);  // [t] = width for t active slot tiles
+int tc_layer_widths(int* out, int cap);                                 // the refined widths available
 int tc_error(relu_qp_t h);    // device error word of the backend (0 = none); clears it
 
 }  // namespace rq

@@ -84,13 +84,26 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return done != 0;
 }
 
-// Wait for the phase with the given parity to complete; false after the deadline.
+// Wait for the phase with the given parity to complete; false after the
+// deadline.  (The deadline is checked after every unsuccessful try_wait,
+// which itself blocks for a while; a tight loop of tries between clock reads
+// made every pipeline hand-off several times slower.)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const long long t0 = gtime();
+    while (!mbar_try(bar, parity))
+        if (gtime() - t0 > kWaitNs) return false;
+    return true;
+}
+
+// The same for a long wait by a thread that is not on the critical path: poll
+// every `ns` nanoseconds so that the polling does not slow down the barrier
+// operations of the producer and MMA threads.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, unsigned ns) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = gtime();
     while (true) {
-        for (int i = 0; i < 64; ++i)
-            if (mbar_try(bar, parity)) return true;
+        __nanosleep(ns);
+        if (mbar_try(bar, parity)) return true;
         if (gtime() - t0 > kWaitNs) return false;
     }
 }
@@ -158,6 +171,66 @@ struct TcSmem {
 };
 
 // ---------------------------------------------------------------------------
+// producer and MMA loops: separate (not inlined) functions, so that the few
+// values they carry stay in registers whatever the epilogue's register
+// pressure is; both return false when a wait passed its deadline
+// ---------------------------------------------------------------------------
+// bar0: full barriers [0, S), empty barriers [S, 2S); stage s at sbase + s * kStage
+template <int NA, int NB, int BN, int STAGES, int KSTAGE, int KA>
+__device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sbase, uint32_t bar0,
+                                     int nkb, int koff, int a0, int a1, int a2, int b0, int b1, int b2,
+                                     int& issued) {
+    const int arow[3] = {a0, a1, a2}, brow[3] = {b0, b1, b2};
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) return false;
+        const uint32_t full = bar0 + 8 * s;
+        mbar_expect_tx(full, KSTAGE);
+        const uint32_t st = sbase + s * KSTAGE;
+        const int k0 = kb * kBK + koff;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) tma_load_2d(st + a * kTileBytesA, tmA, k0, arow[a], full);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
+        issued = kb + 1;
+    }
+    return true;
+}
+
+// Descriptors are formed once; a stage, part or 16-element k step is a
+// constant byte offset, i.e. an add of offset / 16 to the address field
+// (shared addresses stay below 2^18, so the 14-bit field cannot carry).
+template <int NPROD, int BN, int STAGES, int KSTAGE, int KA>
+__device__ __noinline__ bool issue_mmas(uint32_t sbase, uint32_t bar0, uint32_t tmem, int nkb) {
+    constexpr uint32_t IDESC = idesc_bf16(BN);
+    const uint64_t d0 = sdesc(sbase);
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(bar0 + 8 * s, ph)) return false;
+        fence_after();
+        const uint64_t da = d0 + (uint64_t)((s * KSTAGE) >> 4);
+        const uint64_t db = da + (uint64_t)(KA >> 4);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+            for (int pr = 0; pr < NPROD; ++pr) {
+                // product list: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0)
+                const int ia = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
+                const int ib = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+                const uint64_t ad = da + (uint64_t)((ia * kTileBytesA + kk * 32) >> 4);
+                const uint64_t bd = db + (uint64_t)((ib * BN * 128 + kk * 32) >> 4);
+                const bool first = kb == 0 && kk == 0 && pr <= 1;   // first MMA of either accumulator
+                mma_bf16(tmem + (pr == 0 ? 0 : BN), ad, bd, IDESC, first ? 0u : 1u);
+            }
+        }
+        mma_commit(bar0 + 8 * (STAGES + s));
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
 template <int MODE, int BN, int STAGES>
@@ -170,8 +243,6 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     constexpr int ACC = 2;   // significance accumulators of BN columns each
     constexpr int TCOLS = tmem_cols(ACC * BN);
     using L = TcSmem<NA, NB, BN, STAGES>;
-    constexpr uint32_t kTx = L::kStage;
-    constexpr uint32_t IDESC = idesc_bf16(BN);
 
     const int tile = blockIdx.y;
     if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA
@@ -211,25 +282,15 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     if (warp == 0) {
         // ------------------------- TMA producer -------------------------
         if (lane == 0) {
+            int arow[3] = {0, 0, 0}, brow[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < NA; ++a) arow[a] = g.a_row[a] + slot0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) brow[b] = g.b_row[b] + ri * g.b_rho_stride + row0;
             int issued = 0;
-            bool ok = true;
-            for (int kb = 0; kb < g.num_kb && ok; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (kb / STAGES) & 1;
-                if (!mbar_wait(smem_u32(&bars[STAGES + s]), ph ^ 1)) { ok = false; break; }
-                const uint32_t full = smem_u32(&bars[s]);
-                mbar_expect_tx(full, kTx);
-                uint8_t* st = smem + s * L::kStage;
-                const int k0 = kb * kBK + g.k_off;
-#pragma unroll
-                for (int a = 0; a < NA; ++a)
-                    tma_load_2d(smem_u32(st + a * kTileBytesA), &tmA, k0, g.a_row[a] + slot0, full);
-#pragma unroll
-                for (int b = 0; b < NB; ++b)
-                    tma_load_2d(smem_u32(st + L::kA + b * BN * 128), &tmB, k0,
-                                g.b_row[b] + ri * g.b_rho_stride + row0, full);
-                issued = kb + 1;
-            }
+            const bool ok = produce<NA, NB, BN, STAGES, L::kStage, L::kA>(
+                &tmA, &tmB, smem_u32(smem), smem_u32(bars), g.num_kb, g.k_off, arow[0], arow[1], arow[2], brow[0],
+                brow[1], brow[2], issued);
             if (!ok) {
                 atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
                 s_fail = 1;
@@ -241,31 +302,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
         if (lane == 0) {
-            bool ok = true;
-            for (int kb = 0; kb < g.num_kb; ++kb) {
-                const int s = kb % STAGES;
-                const uint32_t ph = (kb / STAGES) & 1;
-                if (!mbar_wait(smem_u32(&bars[s]), ph)) { ok = false; break; }
-                fence_after();
-                const int kb_local = kb;
-                const uint32_t dt = tmem;
-                const uint32_t sa = smem_u32(smem + s * L::kStage);
-                const uint32_t sb = sa + L::kA;
-#pragma unroll
-                for (int kk = 0; kk < kBK / 16; ++kk) {
-#pragma unroll
-                    for (int pr = 0; pr < NPROD; ++pr) {
-                        // product list: (0,0) | (0,1) (1,0) (0,2) (1,1) (2,0)
-                        const int ia = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
-                        const int ib = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
-                        const uint64_t ad = sdesc(sa + ia * kTileBytesA + kk * 32);
-                        const uint64_t bd = sdesc(sb + ib * BN * 128 + kk * 32);
-                        const bool first = kb_local == 0 && kk == 0 && pr <= 1;   // first MMA of either accumulator
-                        mma_bf16(dt + (pr == 0 ? 0 : BN), ad, bd, IDESC, first ? 0u : 1u);
-                    }
-                }
-                mma_commit(smem_u32(&bars[STAGES + s]));
-            }
+            const bool ok = issue_mmas<NPROD, BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
+                                                                           g.num_kb);
             if (ok) {
                 mma_commit(smem_u32(&bars[2 * STAGES]));
                 // keep TMEM alive until the MMAs have landed
@@ -282,7 +320,36 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         const int half = (warp - 2) >> 2;               // which half of the columns
         const int slot = slot0 + q * 32 + lane;
         const int qp = p.perm[slot];
-        bool ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
+        // whole 16-row pieces are transposed through shared memory so that
+        // lane = 4 * (slot % 8) + (row group): QP slot pass * 8 + lane / 4, rows cg..cg+3
+        const int cg = (lane & 3) * 4;
+        int qq[4];
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) qq[pass] = __shfl_sync(0xffffffffu, qp, pass * 8 + (lane >> 2));
+        const int cbeg = half * (BN / 2), cend = (half + 1) * (BN / 2);
+        const bool n_aligned = (p.n & 3) == 0;
+        auto whole_at = [&](int c0) {
+            const int r0 = row0 + c0;
+            return MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows && (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
+        };
+        Chunk4 in[4];
+        float rs[4] = {1.f, 1.f, 1.f, 1.f};
+        auto prefetch = [&](int c0) {
+            const int r0 = row0 + c0 + cg;
+            if (r0 >= p.n) ld4(p.rs + (r0 - p.n), rs);
+#pragma unroll
+            for (int pass = 0; pass < 4; ++pass)
+                if (qq[pass] >= 0) chunk4_load(p, qq[pass], ri, r0, in[pass]);
+        };
+        // the inputs of the first piece load while the MMAs run
+        if (whole_at(cbeg)) prefetch(cbeg);
+        // one lane per warp polls the accumulator barrier (sleeping between
+        // polls) for the whole main loop; then every lane observes the
+        // completed phase itself
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait_sleep(smem_u32(&bars[2 * STAGES]), 0, 256);
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (ready) ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
         ready = __all_sync(0xffffffffu, ready);
         if (!ready) {
             if (lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
@@ -290,32 +357,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             fence_after();
             const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
             float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
-            const bool n_aligned = (p.n & 3) == 0;
             float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
-            for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+            for (int c0 = cbeg; c0 < cend; c0 += 16) {
+                const int r0 = row0 + c0;
+                const bool whole = whole_at(c0);
+                if (whole && c0 != cbeg) prefetch(c0);
                 float v[16], w[16];
                 tmem_ld16(tl + c0, v);
                 tmem_ld16(tl + BN + c0, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
-                const int r0 = row0 + c0;
-                const bool whole = MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows &&
-                                   (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
                 if (whole) {
-                    // transpose through shared memory: 4 lanes per QP, 4 rows per lane
 #pragma unroll
                     for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
                     __syncwarp();
 #pragma unroll
                     for (int pass = 0; pass < 4; ++pass) {
                         const int sl = pass * 8 + (lane >> 2);          // slot within the warp's 32
-                        const int cg = (lane & 3) * 4;                  // first of this lane's 4 rows
-                        const int qq = __shfl_sync(0xffffffffu, qp, sl);
-                        if (qq >= 0) {
+                        if (qq[pass] >= 0) {
                             float a4[4];
 #pragma unroll
                             for (int t = 0; t < 4; ++t) a4[t] = xb[sl * 17 + cg + t];
-                            layer_chunk4(p, slot0 + q * 32 + sl, qq, ri, r0 + cg, a4);
+                            chunk4_apply(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, in[pass], rs);
                         }
                     }
                     __syncwarp();
@@ -359,13 +422,25 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// tile widths (rows of Wt per CTA) of the refined layer; the 3-part modes use 64 or 128
+constexpr int kLayerBN[] = {32, 64, 96, 128, 160, 192, 256};
+constexpr int kNumLayerBN = sizeof(kLayerBN) / sizeof(int);
+
+int bn_index(int bn) {
+    for (int i = 0; i < kNumLayerBN; ++i)
+        if (kLayerBN[i] == bn) return i;
+    return -1;
+}
+
 struct TcState {
     EncodeTiledFn encode = nullptr;
     int bn_layer = 128, bn_check = 128;
+    std::vector<int> bn_by_tiles;        // refined-layer width per number of active slot tiles
     int* err = nullptr;                  // = counters + CNT_ERR
     // encoded maps, keyed by box rows
     CUtensorMap opnd_map, ck_map;
-    CUtensorMap wb_map[4], wcb_map[4];   // for BN in {64, 128, 192, 256}
+    CUtensorMap wb_map[kNumLayerBN];     // weights, box rows kLayerBN[i]
+    CUtensorMap wcb_map[2];              // check matrix, box rows 64 and 128
 };
 
 int encode_2d(relu_qp_t h, TcState* st, CUtensorMap* map, void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
@@ -403,20 +478,29 @@ int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const Bat
 }
 
 // The refined layer (2 parts per operand) fits two or more stages up to
-// BN = 256; the 3-part modes are limited to BN <= 128 for two stages.
-template <int MODE>
-int dispatch_bn(relu_qp_t h, int bn, const CUtensorMap* maps, const BatchParams& p, const TcArgs& g,
-                const CUtensorMap& a, int tiles) {
-    if (MODE == MODE_LAYER_REFINED) {
-        switch (bn) {
-            case 64: return launch_tc<MODE_LAYER_REFINED, 64>(h, a, maps[0], p, g, tiles);
-            case 128: return launch_tc<MODE_LAYER_REFINED, 128>(h, a, maps[1], p, g, tiles);
-            case 192: return launch_tc<MODE_LAYER_REFINED, 192>(h, a, maps[2], p, g, tiles);
-            default: return launch_tc<MODE_LAYER_REFINED, 256>(h, a, maps[3], p, g, tiles);
-        }
+// BN = 256; the 3-part modes are limited to BN <= 128 for two stages.  Every
+// width keeps BN / 2 a multiple of 16 (the epilogue's column split).
+int dispatch_refined(relu_qp_t h, int bn, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
+                     const CUtensorMap& a, int tiles) {
+    constexpr int M = MODE_LAYER_REFINED;
+    switch (bn) {
+        case 32: return launch_tc<M, 32>(h, a, wmaps[0], p, g, tiles);
+        case 64: return launch_tc<M, 64>(h, a, wmaps[1], p, g, tiles);
+        case 96: return launch_tc<M, 96>(h, a, wmaps[2], p, g, tiles);
+        case 128: return launch_tc<M, 128>(h, a, wmaps[3], p, g, tiles);
+        case 160: return launch_tc<M, 160>(h, a, wmaps[4], p, g, tiles);
+        case 192: return launch_tc<M, 192>(h, a, wmaps[5], p, g, tiles);
+        case 256: return launch_tc<M, 256>(h, a, wmaps[6], p, g, tiles);
+        default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
     }
-    if (bn <= 64) return launch_tc<MODE, 64>(h, a, maps[0], p, g, tiles);
-    return launch_tc<MODE, 128>(h, a, maps[1], p, g, tiles);
+}
+
+// 3-part modes: b64 / b128 are the maps with 64- and 128-row boxes
+template <int MODE>
+int dispatch_3part(relu_qp_t h, int bn, const CUtensorMap& b64, const CUtensorMap& b128, const BatchParams& p,
+                   const TcArgs& g, const CUtensorMap& a, int tiles) {
+    if (bn <= 64) return launch_tc<MODE, 64>(h, a, b64, p, g, tiles);
+    return launch_tc<MODE, 128>(h, a, b128, p, g, tiles);
 }
 
 }  // namespace
@@ -435,11 +519,10 @@ int tc_prepare(relu_qp_t h) {
     st->err = w.counters + CNT_ERR;
     RQ_TRY(encode_2d(h, st, &st->opnd_map, w.OPND, 7ull * w.slots, w.ldk, kSlotTile));
     RQ_TRY(encode_2d(h, st, &st->ck_map, w.CK, 3ull * w.slots, w.ldkc, kSlotTile));
-    const int bns[4] = {64, 128, 192, 256};
-    for (int i = 0; i < 4; ++i) {
-        RQ_TRY(encode_2d(h, st, &st->wb_map[i], w.WB, (uint64_t)h->nr * 3 * w.Rpad, w.ldk, bns[i]));
-        RQ_TRY(encode_2d(h, st, &st->wcb_map[i], w.WCB, 3ull * w.npad, w.ldkc, bns[i]));
-    }
+    for (int i = 0; i < kNumLayerBN; ++i)
+        RQ_TRY(encode_2d(h, st, &st->wb_map[i], w.WB, (uint64_t)h->nr * 3 * w.Rpad, w.ldk, kLayerBN[i]));
+    for (int i = 0; i < 2; ++i)
+        RQ_TRY(encode_2d(h, st, &st->wcb_map[i], w.WCB, 3ull * w.npad, w.ldkc, 64 << i));
     return RELU_QP_OK;
 }
 
@@ -450,9 +533,24 @@ void tc_release(relu_qp_t h) {
 
 int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
+    if (bn_index(bn_layer) < 0) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
     st->bn_layer = bn_layer;
     st->bn_check = bn_check;
+    st->bn_by_tiles.clear();
     return RELU_QP_OK;
+}
+
+int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles) {
+    TcState* st = static_cast<TcState*>(h->bw.tc);
+    for (size_t t = 1; t < bn_by_tiles.size(); ++t)
+        if (bn_index(bn_by_tiles[t]) < 0) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
+    st->bn_by_tiles = bn_by_tiles;
+    return RELU_QP_OK;
+}
+
+int tc_layer_widths(int* out, int cap) {
+    for (int i = 0; i < kNumLayerBN && i < cap; ++i) out[i] = kLayerBN[i];
+    return kNumLayerBN;
 }
 
 int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles) {
@@ -464,17 +562,18 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int 
     g.err = st->err;
     g.b_rho_stride = 3 * w.Rpad;
     for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
-    // with few active slot tiles (the convergence tail) narrower row tiles
-    // give more CTAs; the tuned width is for a full batch
+    // the width tuned for this many active slot tiles (narrower ones give the
+    // convergence tail more CTAs)
     int bn = st->bn_layer;
-    while (bn > 64 && (long)active_tiles * ceil_div(h->R, bn) < h->num_sms) bn = bn > 128 ? 128 : 64;
+    if (!st->bn_by_tiles.empty())
+        bn = st->bn_by_tiles[std::max(1, std::min<int>(active_tiles, (int)st->bn_by_tiles.size() - 1))];
     if (operand_set < 0) {   // accurate: s1, s2, s3 are parts 4..6
         for (int a = 0; a < 3; ++a) g.a_row[a] = (4 + a) * w.slots;
-        return dispatch_bn<MODE_LAYER_ACCURATE>(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
+        return dispatch_3part<MODE_LAYER_ACCURATE>(h, bn, st->wb_map[1], st->wb_map[3], p, g, st->opnd_map, tiles);
     }
     g.a_row[0] = (2 * operand_set) * w.slots;
     g.a_row[1] = (2 * operand_set + 1) * w.slots;
-    return dispatch_bn<MODE_LAYER_REFINED>(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
+    return dispatch_refined(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
 }
 
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
@@ -490,8 +589,9 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
         g.a_row[a] = a * w.slots;
         g.b_row[a] = a * w.npad;
     }
-    if (phase == 1) return dispatch_bn<MODE_CHECK1>(h, st->bn_check, st->wcb_map, p, g, st->ck_map, tiles);
-    return dispatch_bn<MODE_CHECK2>(h, st->bn_check, st->wcb_map, p, g, st->ck_map, tiles);
+    if (phase == 1)
+        return dispatch_3part<MODE_CHECK1>(h, st->bn_check, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
+    return dispatch_3part<MODE_CHECK2>(h, st->bn_check, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
 }
 
 int tc_error(relu_qp_t h) {
