@@ -465,7 +465,7 @@ BatchParams base_params(relu_qp_t h) {
         p.rhod[r] = h->be[r].rho;
     }
     p.rs = h->rs32;
-    p.Y = w.Y; p.Z = w.Z; p.LAM = w.LAM; p.AY = w.AY; p.LSTD = w.LSTD; p.C = w.C; p.SREF = w.SREF; p.PY = w.PY;
+    p.Y = w.Y; p.Z = w.Z; p.LAM = w.LAM; p.AY = w.AY; p.RR = w.RR; p.LSTD = w.LSTD; p.C = w.C; p.SREF = w.SREF; p.PY = w.PY;
     p.L = w.L; p.U = w.U; p.Q = w.Q; p.BIAS = w.BIAS; p.QN = w.QN;
     p.perm = w.perm; p.tile_rho = w.tile_rho; p.counters = w.counters; p.RED = w.RED;
     return p;
@@ -504,6 +504,7 @@ int batch_alloc(relu_qp_t h) {
     RQ_TRY(alloc(h, &w.Z, cap * w.ldm));
     RQ_TRY(alloc(h, &w.LAM, cap * w.ldm));
     RQ_TRY(alloc(h, &w.AY, cap * w.ldm));
+    RQ_TRY(alloc(h, &w.RR, cap * w.ldm));
     RQ_TRY(alloc(h, &w.LSTD, cap * w.ldm));
     RQ_TRY(alloc(h, &w.L, cap * w.ldm));
     RQ_TRY(alloc(h, &w.U, cap * w.ldm));
@@ -566,7 +567,7 @@ int tc_tune(relu_qp_t h) {
     p.CK = static_cast<__nv_bfloat16*>(w.CK);
     const int tiles = w.slots / kSlotTile;
     int widths[16];
-    const int nw = tc_layer_widths(widths, 16);
+    const int nw = tc_layer_widths(h, widths, 16);
     // measured tile counts: every count up to 8, then every 4th up to 32, then every 16th
     std::vector<int> counts;
     for (int t = 1; t <= tiles; ++t)

@@ -39,6 +39,7 @@ struct BatchParams {
     double rhod[RQ_MAX_RHO];
     const float* rs;                         // per-row penalty scale (1 or eq_scale)
     float *Y, *Z, *LAM, *AY, *LSTD, *C, *SREF, *PY;
+    float* RR;                               // refined layers: r = (Ax) - z + lam'/rho for the next layer
     const float *L, *U, *Q, *BIAS, *QN;
     const int* perm;
     const int* tile_rho;
@@ -87,9 +88,14 @@ __device__ __forceinline__ void put_check(const BatchParams& p, int slot, int co
 //   t = acc + b (or + c in the refined form), x rows: x+ = t;
 //   Ax rows i:  r_i = (Ax)_i - z_i + lam'_i/rho_i,  z+ = clamp(t + r_i, l_i, u_i),
 //               lam'+ = rho_i r_i,  (Ax)+ = t,  operand entry 2 rho_i z+ - lam'+.
-// With EPI_CHECK the new x also goes into the check operand.
+// The BF16 split form carries r itself between the layers of a chunk:
+// r+ = (Ax)+ - z+ + lam'+/rho_i = t - z+ + r (array RR); the refined layers
+// read r from RR and write x, Ax, z and lam' only at the last layer of the
+// chunk.  With EPI_CHECK the new x also goes into the check operand.
 __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int qp, int ri, int r, float acc) {
     const unsigned f = p.flags;
+    const bool refine_only = (f & EPI_REFINE) && !(f & EPI_REBASE);
+    const bool store_state = !refine_only || (f & EPI_LAST);
     const size_t oR = (size_t)qp * p.ldR + r;
     const float* bias = p.BIAS + (size_t)ri * p.cap * p.ldR;
     float t;
@@ -105,21 +111,29 @@ __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int q
     if (r < p.n) {
         const size_t o = (size_t)qp * p.ldn + r;
         if (f & EPI_REBASE) p.SREF[oR] = p.Y[o];
-        p.Y[o] = t;
+        if (store_state) p.Y[o] = t;
         s_new = t;
         if (f & EPI_CHECK) put_check(p, slot, r, t);
     } else {
         const int i = r - p.n;
         const size_t o = (size_t)qp * p.ldm + i;
         const float rho_i = p.rho[ri] * p.rs[i];
-        const float ay = p.AY[o], zi = p.Z[o], li = p.LAM[o];
-        if (f & EPI_REBASE) p.SREF[oR] = 2.f * rho_i * zi - li;
-        const float rr = ay - zi + li / rho_i;
+        float rr;
+        if (refine_only) {
+            rr = p.RR[o];
+        } else {
+            const float ay = p.AY[o], zi = p.Z[o], li = p.LAM[o];
+            if (f & EPI_REBASE) p.SREF[oR] = 2.f * rho_i * zi - li;
+            rr = ay - zi + li / rho_i;
+        }
         const float zn = fminf(fmaxf(t + rr, p.L[o]), p.U[o]);
         const float ln = rho_i * rr;
-        p.AY[o] = t;
-        p.Z[o] = zn;
-        p.LAM[o] = ln;
+        if (f & EPI_REFINE) p.RR[o] = t - zn + rr;
+        if (store_state) {
+            p.AY[o] = t;
+            p.Z[o] = zn;
+            p.LAM[o] = ln;
+        }
         s_new = 2.f * rho_i * zn - ln;
     }
     if (!(f & EPI_LAST)) {
@@ -193,6 +207,7 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
             for (int k = 0; k < 4; ++k) put_check(p, slot, r0 + k, c.t[k]);
     } else {
         const size_t o = (size_t)qp * p.ldm + (r0 - p.n);
+        float rn[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             c.t[k] += acc[k];
@@ -201,6 +216,7 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
             const float rr = c.ay[k] - c.zz[k] + c.lm[k] / rho_i;
             const float zn = fminf(fmaxf(c.t[k] + rr, c.lo[k]), c.up[k]);
             const float ln = rho_i * rr;
+            rn[k] = c.t[k] - zn + rr;
             c.zz[k] = zn;
             c.lm[k] = ln;
             s_new[k] = 2.f * rho_i * zn - ln;
@@ -208,6 +224,7 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
         st4(p.AY + o, c.t);
         st4(p.Z + o, c.zz);
         st4(p.LAM + o, c.lm);
+        if (f & EPI_REFINE) st4(p.RR + o, rn);
     }
     if (f & EPI_REBASE) {
         st4(p.C + oR, c.t);
@@ -229,6 +246,72 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
         } else {
             st4(p.Sout + so, s_new);
         }
+    }
+}
+
+// The refined layers' 4-row piece (flags EPI_REFINE without EPI_REBASE): the
+// inputs are c, s_ref and, for Ax rows, r, l, u.
+struct Chunk4R {
+    float t[4], sref[4], rr[4], lo[4], up[4];
+};
+
+__device__ __forceinline__ void chunk4_load(const BatchParams& p, int qp, int ri, int r0, Chunk4R& c) {
+    const size_t oR = (size_t)qp * p.ldR + r0;
+    ld4(p.C + oR, c.t);
+    ld4(p.SREF + oR, c.sref);
+    if (r0 >= p.n) {
+        const size_t o = (size_t)qp * p.ldm + (r0 - p.n);
+        ld4(p.RR + o, c.rr);
+        ld4(p.L + o, c.lo);
+        ld4(p.U + o, c.up);
+    }
+}
+
+__device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int qp, int ri, int r0,
+                                             const float (&acc)[4], Chunk4R& c, const float (&rs)[4]) {
+    const unsigned f = p.flags;
+    const bool last = (f & EPI_LAST) != 0;
+    float s_new[4];
+    if (r0 < p.n) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c.t[k] += acc[k];
+            s_new[k] = c.t[k];
+        }
+        if (last) st4(p.Y + (size_t)qp * p.ldn + r0, c.t);
+        if (f & EPI_CHECK)
+            for (int k = 0; k < 4; ++k) put_check(p, slot, r0 + k, c.t[k]);
+    } else {
+        const size_t o = (size_t)qp * p.ldm + (r0 - p.n);
+        float zn[4], ln[4], rn[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            c.t[k] += acc[k];
+            const float rho_i = p.rho[ri] * rs[k];
+            zn[k] = fminf(fmaxf(c.t[k] + c.rr[k], c.lo[k]), c.up[k]);
+            ln[k] = rho_i * c.rr[k];
+            rn[k] = c.t[k] - zn[k] + c.rr[k];
+            s_new[k] = 2.f * rho_i * zn[k] - ln[k];
+        }
+        st4(p.RR + o, rn);
+        if (last) {
+            st4(p.AY + o, c.t);
+            st4(p.Z + o, zn);
+            st4(p.LAM + o, ln);
+        }
+    }
+    if (!last) {
+        const size_t so = (size_t)slot * p.ldk + r0;
+        __nv_bfloat16 hi[4], lo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) split2(s_new[k] - c.sref[k], hi[k], lo[k]);
+        uint2 vh, vl;
+        vh.x = (uint32_t)__bfloat16_as_ushort(hi[0]) | ((uint32_t)__bfloat16_as_ushort(hi[1]) << 16);
+        vh.y = (uint32_t)__bfloat16_as_ushort(hi[2]) | ((uint32_t)__bfloat16_as_ushort(hi[3]) << 16);
+        vl.x = (uint32_t)__bfloat16_as_ushort(lo[0]) | ((uint32_t)__bfloat16_as_ushort(lo[1]) << 16);
+        vl.y = (uint32_t)__bfloat16_as_ushort(lo[2]) | ((uint32_t)__bfloat16_as_ushort(lo[3]) << 16);
+        *reinterpret_cast<uint2*>(p.Dhi + so) = vh;
+        *reinterpret_cast<uint2*>(p.Dlo + so) = vl;
     }
 }
 
@@ -273,7 +356,7 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phas
 void tc_release(relu_qp_t h);
 int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);           // one refined width for every batch size
 int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles);  // [t] = width for t active slot tiles
-int tc_layer_widths(int* out, int cap);                                 // the refined widths available
+int tc_layer_widths(relu_qp_t h, int* out, int cap);                    // the refined widths available
 int tc_error(relu_qp_t h);    // device error word of the backend (0 = none); clears it
 
 }  // namespace rq

@@ -29,6 +29,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -156,18 +157,69 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// --- thread-block cluster (K-split pair) helpers ---
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the variable at shared::cta address `addr` in CTA `rank`
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster4(uint32_t addr, float a, float b, float c, float d) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// arrive (release at cluster scope) on an mbarrier of another CTA of the cluster
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// wait (acquire at cluster scope) with a deadline, polling every `ns` nanoseconds
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, unsigned ns) {
+    const long long t0 = gtime();
+    while (!mbar_try_cluster(bar, parity)) {
+        if (gtime() - t0 > kWaitNs) return false;
+        if (ns) __nanosleep(ns);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 __host__ __device__ constexpr int tmem_cols(int n) { return n <= 32 ? 32 : n <= 64 ? 64 : n <= 128 ? 128 : n <= 256 ? 256 : 512; }
 
-template <int NA, int NB, int BN, int STAGES>
+template <int NA, int NB, int BN, int STAGES, int KS>
 struct TcSmem {
     static constexpr int kA = NA * kTileBytesA;
     static constexpr int kB = NB * BN * 128;
     static constexpr int kStage = kA + kB;
     static constexpr int kXpose = 8 * 32 * 17 * 4;      // epilogue transpose buffers (8 warps)
-    static constexpr int kBytes = STAGES * kStage + kXpose + 1024 /* align */ + 256 /* barriers */;
+    // partner's partial sums [128 slots][BN / 2 columns], 16-byte chunks swizzled by slot
+    static constexpr int kRecv = KS == 2 ? kSlotTile * (BN / 2) * 4 : 0;
+    static constexpr int kBytes = STAGES * kStage + kXpose + kRecv + 1024 /* align */ + 256 /* barriers */;
 };
 
 // ---------------------------------------------------------------------------
@@ -233,7 +285,20 @@ __device__ __noinline__ bool issue_mmas(uint32_t sbase, uint32_t bar0, uint32_t 
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <int MODE, int BN, int STAGES>
+// float offset of (slot, col) in the receive buffer of OWN columns: the
+// 16-byte chunk index is XORed with slot % 8, so the 32 rows a warp writes or
+// reads at one column hit distinct banks (OWN is a multiple of 32)
+template <int OWN>
+__device__ __forceinline__ int recv_off(int slot, int col) {
+    return slot * OWN + ((((col >> 2) ^ (slot & 7))) << 2) + (col & 3);
+}
+
+// KS = 2 (refined layers): the CTA pair of a cluster splits the k-blocks in
+// two halves; after its main loop each CTA sends the partial sums of the
+// partner's half of the columns into the partner's shared memory and
+// finalises its own half.  The sum of the two halves is the same whatever
+// the batch size, so a QP's arithmetic does not depend on its batch.
+template <int MODE, int BN, int STAGES, int KS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchParams p,
                    TcArgs g) {
@@ -242,20 +307,31 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     constexpr int NPROD = NA == 2 ? 3 : 6;
     constexpr int ACC = 2;   // significance accumulators of BN columns each
     constexpr int TCOLS = tmem_cols(ACC * BN);
-    using L = TcSmem<NA, NB, BN, STAGES>;
+    constexpr int OWN = BN / KS;        // columns this CTA finalises
+    constexpr int PER = OWN / 2;        // columns per epilogue warp
+    static_assert(KS == 1 || KS == 2, "K split of 1 or 2");
+    static_assert(PER % 16 == 0, "the epilogue works on 16-column pieces");
+    using L = TcSmem<NA, NB, BN, STAGES, KS>;
 
     const int tile = blockIdx.y;
-    if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA
+    if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA (and the cluster)
     const int slot0 = tile * kSlotTile;
-    const int row0 = blockIdx.x * BN;
+    const int rank = KS == 2 ? (int)cluster_rank() : 0;
+    const int row0 = (blockIdx.x / KS) * BN;
     const int ri = p.tile_rho[tile];
+    // k-blocks of this CTA: [kb_begin, kb_begin + kb_count)
+    const int kb_half = (g.num_kb + 1) / 2;
+    const int kb_begin = KS == 2 && rank == 1 ? kb_half : 0;
+    const int kb_count = KS == 2 ? (rank == 0 ? kb_half : g.num_kb - kb_half) : g.num_kb;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float* xpose = reinterpret_cast<float*>(smem + STAGES * L::kStage);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose);
-    // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready; then the TMEM address
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    float* recv = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
+    // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready, bars[2S+1] partner's
+    // partial sums received (KS = 2); then the TMEM address
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -265,6 +341,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_init(smem_u32(&bars[STAGES + s]), 1);
         }
         mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+        mbar_init(smem_u32(&bars[2 * STAGES + 1]), 8);   // one arrival per epilogue warp of the partner
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -277,6 +354,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     fence_before();
     __syncthreads();
     fence_after();
+    // the partner's barriers are initialised before anything is sent to it
+    if (KS == 2) cluster_sync();
     const uint32_t tmem = *tmem_holder;
 
     if (warp == 0) {
@@ -289,8 +368,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int b = 0; b < NB; ++b) brow[b] = g.b_row[b] + ri * g.b_rho_stride + row0;
             int issued = 0;
             const bool ok = produce<NA, NB, BN, STAGES, L::kStage, L::kA>(
-                &tmA, &tmB, smem_u32(smem), smem_u32(bars), g.num_kb, g.k_off, arow[0], arow[1], arow[2], brow[0],
-                brow[1], brow[2], issued);
+                &tmA, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK, arow[0], arow[1],
+                arow[2], brow[0], brow[1], brow[2], issued);
             if (!ok) {
                 atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
                 s_fail = 1;
@@ -303,7 +382,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // ------------------------- MMA issuer -------------------------
         if (lane == 0) {
             const bool ok = issue_mmas<NPROD, BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
-                                                                           g.num_kb);
+                                                                           kb_count);
             if (ok) {
                 mma_commit(smem_u32(&bars[2 * STAGES]));
                 // keep TMEM alive until the MMAs have landed
@@ -317,32 +396,41 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else {
         // ------------------------- epilogue -------------------------
         const int q = warp & 3;                         // TMEM lane quadrant of this warp
-        const int half = (warp - 2) >> 2;               // which half of the columns
+        const int half = (warp - 2) >> 2;               // which half of this CTA's columns
         const int slot = slot0 + q * 32 + lane;
         const int qp = p.perm[slot];
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         // whole 16-row pieces are transposed through shared memory so that
         // lane = 4 * (slot % 8) + (row group): QP slot pass * 8 + lane / 4, rows cg..cg+3
         const int cg = (lane & 3) * 4;
         int qq[4];
 #pragma unroll
         for (int pass = 0; pass < 4; ++pass) qq[pass] = __shfl_sync(0xffffffffu, qp, pass * 8 + (lane >> 2));
-        const int cbeg = half * (BN / 2), cend = (half + 1) * (BN / 2);
+        const int own0 = rank * OWN;
+        const int cbeg = own0 + half * PER, cend = cbeg + PER;
         const bool n_aligned = (p.n & 3) == 0;
         auto whole_at = [&](int c0) {
             const int r0 = row0 + c0;
             return MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows && (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
         };
-        Chunk4 in[4];
-        float rs[4] = {1.f, 1.f, 1.f, 1.f};
-        auto prefetch = [&](int c0) {
-            const int r0 = row0 + c0 + cg;
-            if (r0 >= p.n) ld4(p.rs + (r0 - p.n), rs);
-#pragma unroll
-            for (int pass = 0; pass < 4; ++pass)
-                if (qq[pass] >= 0) chunk4_load(p, qq[pass], ri, r0, in[pass]);
+        // refined layers: the lighter refined-only inputs (flags never hold EPI_REBASE)
+        using Piece = typename std::conditional<MODE == MODE_LAYER_REFINED, Chunk4R, Chunk4>::type;
+        Piece in[4];
+        float rs[4] = {1.f, 1.f, 1.f, 1.f}, rs_next[4] = {1.f, 1.f, 1.f, 1.f};
+        // inputs of one 4-row piece of the 16-column chunk at c0 (pass = QP group)
+        auto load_pass = [&](int c0, int pass) {
+            if (qq[pass] >= 0) chunk4_load(p, qq[pass], ri, row0 + c0 + cg, in[pass]);
         };
-        // the inputs of the first piece load while the MMAs run
-        if (whole_at(cbeg)) prefetch(cbeg);
+        auto load_rs = [&](int c0, float (&dst)[4]) {
+            const int r0 = row0 + c0 + cg;
+            if (r0 >= p.n) ld4(p.rs + (r0 - p.n), dst);
+        };
+        // the inputs of the first chunk load while the MMAs run
+        if (whole_at(cbeg)) {
+            load_rs(cbeg, rs);
+#pragma unroll
+            for (int pass = 0; pass < 4; ++pass) load_pass(cbeg, pass);
+        }
         // one lane per warp polls the accumulator barrier (sleeping between
         // polls) for the whole main loop; then every lane observes the
         // completed phase itself
@@ -351,22 +439,65 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         ready = __shfl_sync(0xffffffffu, ready, 0);
         if (ready) ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
         ready = __all_sync(0xffffffffu, ready);
+        if (ready) fence_after();
+        if (KS == 2) {
+            // send the partner's columns of this warp's TMEM lanes: row (q * 32 + lane)
+            // of the partner's receive buffer, columns half * PER ...
+            const int pc0 = (1 - rank) * OWN + half * PER;
+            const uint32_t dst = mapa(smem_u32(recv), (uint32_t)(1 - rank));
+            const int srow = q * 32 + lane;
+            if (ready) {
+#pragma unroll
+                for (int c = 0; c < PER; c += 16) {
+                    float v[16], w[16];
+                    tmem_ld16(tl + pc0 + c, v);
+                    tmem_ld16(tl + BN + pc0 + c, w);
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, half * PER + c + j), v[j] + w[j],
+                                    v[j + 1] + w[j + 1], v[j + 2] + w[j + 2], v[j + 3] + w[j + 3]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa(smem_u32(&bars[2 * STAGES + 1]), (uint32_t)(1 - rank)));
+            // the partner's partial sums of this CTA's columns
+            bool got = true;
+            if (lane == 0) got = mbar_wait_cluster(smem_u32(&bars[2 * STAGES + 1]), 0, 64);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got) got = mbar_wait_cluster(smem_u32(&bars[2 * STAGES + 1]), 0, 0);
+            got = __all_sync(0xffffffffu, got);
+            if (!got && ready && lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
+            ready = ready && got;
+        }
         if (!ready) {
             if (lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
         } else {
-            fence_after();
-            const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
             float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
             float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
+            // inputs of the next whole chunk load pass by pass as this chunk's
+            // passes finish, so that a memory round trip overlaps a chunk of work
             for (int c0 = cbeg; c0 < cend; c0 += 16) {
                 const int r0 = row0 + c0;
                 const bool whole = whole_at(c0);
-                if (whole && c0 != cbeg) prefetch(c0);
+                const int cn = c0 + 16;
+                const bool next_whole = cn < cend && whole_at(cn);
+                if (next_whole) load_rs(cn, rs_next);
                 float v[16], w[16];
                 tmem_ld16(tl + c0, v);
                 tmem_ld16(tl + BN + c0, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
+                if (KS == 2) {
+#pragma unroll
+                    for (int t = 0; t < 16; t += 4) {
+                        const float4 o =
+                            *reinterpret_cast<const float4*>(recv + recv_off<OWN>(q * 32 + lane, c0 - own0 + t));
+                        v[t] += o.x;
+                        v[t + 1] += o.y;
+                        v[t + 2] += o.z;
+                        v[t + 3] += o.w;
+                    }
+                }
                 if (whole) {
 #pragma unroll
                     for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
@@ -380,18 +511,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                             for (int t = 0; t < 4; ++t) a4[t] = xb[sl * 17 + cg + t];
                             chunk4_apply(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, in[pass], rs);
                         }
+                        if (next_whole) load_pass(cn, pass);
                     }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rs[k] = rs_next[k];
                     __syncwarp();
                     continue;
                 }
-                if (qp < 0) continue;
+                if (qp >= 0) {
 #pragma unroll 4
-                for (int t = 0; t < 16; ++t) {
-                    const int r = r0 + t;
-                    if (r >= g.rows) continue;
-                    if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
-                    else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
-                    else layer_elem(p, slot, qp, ri, r, v[t]);
+                    for (int t = 0; t < 16; ++t) {
+                        const int r = r0 + t;
+                        if (r >= g.rows) continue;
+                        if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
+                        else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
+                        else layer_elem(p, slot, qp, ri, r, v[t]);
+                    }
+                }
+                if (next_whole) {
+#pragma unroll
+                    for (int pass = 0; pass < 4; ++pass) load_pass(cn, pass);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) rs[k] = rs_next[k];
                 }
             }
             if (qp >= 0) {
@@ -409,6 +550,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     fence_before();
     __syncthreads();
+    // neither CTA of a pair leaves while the other may still address its shared memory
+    if (KS == 2) cluster_sync();
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
@@ -436,6 +579,7 @@ struct TcState {
     EncodeTiledFn encode = nullptr;
     int bn_layer = 128, bn_check = 128;
     std::vector<int> bn_by_tiles;        // refined-layer width per number of active slot tiles
+    int ks = 1;                          // K split of the refined layer (fixed per handle)
     int* err = nullptr;                  // = counters + CNT_ERR
     // encoded maps, keyed by box rows
     CUtensorMap opnd_map, ck_map;
@@ -455,42 +599,67 @@ int encode_2d(relu_qp_t h, TcState* st, CUtensorMap* map, void* base, uint64_t r
     return RELU_QP_OK;
 }
 
-template <int MODE, int BN>
+template <int MODE, int BN, int KS>
 constexpr int stages_for() {
-    using L1 = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, 1>;
-    constexpr int budget = 220 * 1024;
-    constexpr int s = (budget - 1024 - 256 - L1::kXpose) / L1::kStage;
+    using L1 = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, 1, KS>;
+    constexpr int budget = 227 * 1024 - 512;   // opt-in maximum less the static shared memory
+    constexpr int s = (budget - 1024 - 256 - L1::kXpose - L1::kRecv) / L1::kStage;
     return s > 4 ? 4 : s;
 }
 
-template <int MODE, int BN>
+template <int MODE, int BN, int KS>
 int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
               int tiles) {
-    constexpr int S = stages_for<MODE, BN>();
+    constexpr int S = stages_for<MODE, BN, KS>();
     static_assert(S >= 2, "not enough shared memory for two stages");
-    using L = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, S>;
-    auto kern = tc_gemm_kernel<MODE, BN, S>;
+    using L = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, S, KS>;
+    auto kern = tc_gemm_kernel<MODE, BN, S, KS>;
     RQ_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
-    dim3 grid(ceil_div(g.rows, BN), tiles);
-    kern<<<grid, kThreadsTC, L::kBytes, h->stream>>>(a, b, p, g);
+    const dim3 grid(KS * ceil_div(g.rows, BN), tiles);
+    if (KS == 1) {
+        kern<<<grid, kThreadsTC, L::kBytes, h->stream>>>(a, b, p, g);
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = grid;
+        cfg.blockDim = dim3(kThreadsTC);
+        cfg.dynamicSmemBytes = L::kBytes;
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = KS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        RQ_CUDA(h, cudaLaunchKernelEx(&cfg, kern, a, b, p, g));
+    }
     RQ_CUDA(h, cudaGetLastError());
     return RELU_QP_OK;
 }
 
-// The refined layer (2 parts per operand) fits two or more stages up to
-// BN = 256; the 3-part modes are limited to BN <= 128 for two stages.  Every
-// width keeps BN / 2 a multiple of 16 (the epilogue's column split).
-int dispatch_refined(relu_qp_t h, int bn, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
+// Refined layer: with a K split of 2 (every problem with at least two
+// k-blocks) the widths are 64, 128 and 192 (each epilogue warp finalises
+// BN / 4 columns; BN = 256 would not leave room for the receive buffer);
+// without, any width of kLayerBN (BN / 2 columns per warp).
+int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
                      const CUtensorMap& a, int tiles) {
     constexpr int M = MODE_LAYER_REFINED;
+    if (ks == 2) {
+        switch (bn) {
+            case 64: return launch_tc<M, 64, 2>(h, a, wmaps[1], p, g, tiles);
+            case 128: return launch_tc<M, 128, 2>(h, a, wmaps[3], p, g, tiles);
+            case 192: return launch_tc<M, 192, 2>(h, a, wmaps[5], p, g, tiles);
+            default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
+        }
+    }
     switch (bn) {
-        case 32: return launch_tc<M, 32>(h, a, wmaps[0], p, g, tiles);
-        case 64: return launch_tc<M, 64>(h, a, wmaps[1], p, g, tiles);
-        case 96: return launch_tc<M, 96>(h, a, wmaps[2], p, g, tiles);
-        case 128: return launch_tc<M, 128>(h, a, wmaps[3], p, g, tiles);
-        case 160: return launch_tc<M, 160>(h, a, wmaps[4], p, g, tiles);
-        case 192: return launch_tc<M, 192>(h, a, wmaps[5], p, g, tiles);
-        case 256: return launch_tc<M, 256>(h, a, wmaps[6], p, g, tiles);
+        case 32: return launch_tc<M, 32, 1>(h, a, wmaps[0], p, g, tiles);
+        case 64: return launch_tc<M, 64, 1>(h, a, wmaps[1], p, g, tiles);
+        case 96: return launch_tc<M, 96, 1>(h, a, wmaps[2], p, g, tiles);
+        case 128: return launch_tc<M, 128, 1>(h, a, wmaps[3], p, g, tiles);
+        case 160: return launch_tc<M, 160, 1>(h, a, wmaps[4], p, g, tiles);
+        case 192: return launch_tc<M, 192, 1>(h, a, wmaps[5], p, g, tiles);
+        case 256: return launch_tc<M, 256, 1>(h, a, wmaps[6], p, g, tiles);
         default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
     }
 }
@@ -499,8 +668,8 @@ int dispatch_refined(relu_qp_t h, int bn, const CUtensorMap* wmaps, const BatchP
 template <int MODE>
 int dispatch_3part(relu_qp_t h, int bn, const CUtensorMap& b64, const CUtensorMap& b128, const BatchParams& p,
                    const TcArgs& g, const CUtensorMap& a, int tiles) {
-    if (bn <= 64) return launch_tc<MODE, 64>(h, a, b64, p, g, tiles);
-    return launch_tc<MODE, 128>(h, a, b128, p, g, tiles);
+    if (bn <= 64) return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles);
+    return launch_tc<MODE, 128, 1>(h, a, b128, p, g, tiles);
 }
 
 }  // namespace
@@ -517,6 +686,8 @@ int tc_prepare(relu_qp_t h) {
         return fail(h, RELU_QP_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
     st->encode = reinterpret_cast<EncodeTiledFn>(fn);
     st->err = w.counters + CNT_ERR;
+    // the K split is a property of the problem (never of the batch size)
+    st->ks = w.ldk / kBK >= 2 ? 2 : 1;
     RQ_TRY(encode_2d(h, st, &st->opnd_map, w.OPND, 7ull * w.slots, w.ldk, kSlotTile));
     RQ_TRY(encode_2d(h, st, &st->ck_map, w.CK, 3ull * w.slots, w.ldkc, kSlotTile));
     for (int i = 0; i < kNumLayerBN; ++i)
@@ -531,9 +702,13 @@ void tc_release(relu_qp_t h) {
     h->bw.tc = nullptr;
 }
 
+bool width_ok(const TcState* st, int bn) {
+    return st->ks == 2 ? (bn == 64 || bn == 128 || bn == 192) : bn_index(bn) >= 0;
+}
+
 int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
-    if (bn_index(bn_layer) < 0) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
+    if (!width_ok(st, bn_layer)) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
     st->bn_layer = bn_layer;
     st->bn_check = bn_check;
     st->bn_by_tiles.clear();
@@ -543,14 +718,17 @@ int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
 int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
     for (size_t t = 1; t < bn_by_tiles.size(); ++t)
-        if (bn_index(bn_by_tiles[t]) < 0) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
+        if (!width_ok(st, bn_by_tiles[t])) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
     st->bn_by_tiles = bn_by_tiles;
     return RELU_QP_OK;
 }
 
-int tc_layer_widths(int* out, int cap) {
-    for (int i = 0; i < kNumLayerBN && i < cap; ++i) out[i] = kLayerBN[i];
-    return kNumLayerBN;
+int tc_layer_widths(relu_qp_t h, int* out, int cap) {
+    const TcState* st = static_cast<const TcState*>(h->bw.tc);
+    int k = 0;
+    for (int i = 0; i < kNumLayerBN; ++i)
+        if (width_ok(st, kLayerBN[i]) && k < cap) out[k++] = kLayerBN[i];
+    return k;
 }
 
 int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles) {
@@ -573,7 +751,7 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int 
     }
     g.a_row[0] = (2 * operand_set) * w.slots;
     g.a_row[1] = (2 * operand_set + 1) * w.slots;
-    return dispatch_refined(h, bn, st->wb_map, p, g, st->opnd_map, tiles);
+    return dispatch_refined(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, tiles);
 }
 
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {

@@ -85,6 +85,7 @@ struct BatchWork {
     // check matrix [[P, A^T], [A, 0]]: (n + m) rows (padded to npad), ldkc = n64 + m64 columns
     // per-QP state (QP-indexed rows)
     float *Y = nullptr, *Z = nullptr, *LAM = nullptr, *AY = nullptr, *LSTD = nullptr;
+    float* RR = nullptr;                   // BF16 form: r = (Ax) - z + lam'/rho carried between layers
     float *L = nullptr, *U = nullptr, *Q = nullptr, *QN = nullptr, *C = nullptr, *SREF = nullptr, *PY = nullptr;
     float* BIAS = nullptr;                 // [nr][cap][ldR]
     float *XO = nullptr, *ZO = nullptr, *LO = nullptr;   // dense outputs [cap][n|m]
