@@ -286,7 +286,8 @@ const char* relu_qp_server_error(relu_qp_server_t s);
  * the FP32 layer otherwise): its launches, the algorithmic FLOPs they did
  * (2 x products x (n+m)^2 per active QP) and, while profiling is enabled,
  * their device time from CUDA events recorded on the handle's stream around
- * each launch (up to 8192 launches per solve are timed).
+ * each chunk's run of consecutive layer launches (layer_timed counts the
+ * launches those spans cover; up to 8192 spans per solve are timed).
  */
 typedef struct relu_qp_prof {
     long long launches;

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <new>
@@ -88,123 +90,184 @@ __global__ void __launch_bounds__(256) sgemm_nt_kernel(int M, int N, int K, cons
     }
 }
 
-// Shared main loop of the FP32 batched kernels: a 128-slot x 64-row tile of
+// Shared main loop of the FP32 batched kernels: a TS-slot x TR-row tile of
 // sum_k X[slot, k] W[row, k] over k in [kbeg, kend) (rows of X and W have
-// leading dimension ld, zero padded to a multiple of 64); each thread
-// accumulates 8 slots x 4 rows.  Every 16-wide k step is summed into a fresh
-// partial that is then added to the running sum: with multipliers of ~1e3
-// the terms of these dot products cancel heavily, and one long sequential
-// FP32 sum would lose ~sqrt(K) units in the last place of its largest
-// partial sum (measured: dual residuals off by 1e-3 on the humanoid workload).
+// leading dimension ld, zero padded to a multiple of 64).  256 threads: thread
+// (ty, tx) = (tid / 16, tid % 16) accumulates slots ty + 16 i (i < TS / 16) and
+// rows tx + 16 j (j < TR / 16).  Every 16-wide k step is summed, in k order,
+// into a fresh partial that is then added to the running sum: with
+// multipliers of ~1e3 the terms of these dot products cancel heavily, and one
+// long sequential FP32 sum would lose ~sqrt(K) units in the last place of its
+// largest partial sum (measured: dual residuals off by 1e-3 on the humanoid
+// workload).  The arithmetic of an output does not depend on TS or TR.
+// k tiles stream through a STAGES-deep cp.async pipeline into shared memory
+// laid out [slot or row][k] with a padded stride, so that the copies run
+// ahead of the arithmetic by STAGES - 1 steps.
+template <int TS, int TR>
+struct F32Tile {
+    static constexpr int SA = TS / 16, RA = TR / 16;
+    static constexpr int LDS = 20;           // padded k stride in floats (80 bytes, 16-byte aligned)
+    static constexpr int STAGES = 4;
+    static constexpr int XS = TS * LDS, WS = TR * LDS;
+    static constexpr int BYTES = STAGES * (XS + WS) * 4;
+};
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int TS, int TR>
 __device__ __forceinline__ void fp32_tile(const float* __restrict__ X, const float* __restrict__ W, int ld,
-                                          int kbeg, int kend, int nrows, int slot0, int row0, float (&acc)[8][4]) {
-    __shared__ __align__(16) float Xs[16][128 + 4];
-    __shared__ __align__(16) float Ws[16][64 + 4];
+                                          int kbeg, int kend, int nrows, int slot0, int row0,
+                                          float (&acc)[TS / 16][TR / 16]) {
+    using T = F32Tile<TS, TR>;
+    extern __shared__ __align__(16) float fsm[];
+    float* Xs = fsm;
+    float* Ws = fsm + T::STAGES * T::XS;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+    for (int a = 0; a < T::SA; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    // global -> register staging of one k-tile (2 float4 of X, 1 of W per thread),
-    // issued one tile ahead so that the loads overlap the arithmetic
-    const int xrow0 = threadIdx.x >> 2, xrow1 = (threadIdx.x + 256) >> 2, xk = (threadIdx.x & 3) * 4;
-    const int wrow = threadIdx.x >> 2, wk = (threadIdx.x & 3) * 4;
-    const bool wvalid = row0 + wrow < nrows;
-    const float* xp0 = X + (size_t)(slot0 + xrow0) * ld + xk;
-    const float* xp1 = X + (size_t)(slot0 + xrow1) * ld + xk;
-    const float* wp = W + (size_t)(row0 + wrow) * ld + wk;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 x0 = zero4, x1 = zero4, w0 = zero4;
-    if (kbeg < kend) {
-        x0 = *reinterpret_cast<const float4*>(xp0 + kbeg);
-        x1 = *reinterpret_cast<const float4*>(xp1 + kbeg);
-        if (wvalid) w0 = __ldg(reinterpret_cast<const float4*>(wp + kbeg));
-    }
-    for (int k0 = kbeg; k0 < kend; k0 += 16) {
-        Xs[xk + 0][xrow0] = x0.x; Xs[xk + 1][xrow0] = x0.y; Xs[xk + 2][xrow0] = x0.z; Xs[xk + 3][xrow0] = x0.w;
-        Xs[xk + 0][xrow1] = x1.x; Xs[xk + 1][xrow1] = x1.y; Xs[xk + 2][xrow1] = x1.z; Xs[xk + 3][xrow1] = x1.w;
-        Ws[wk + 0][wrow] = w0.x; Ws[wk + 1][wrow] = w0.y; Ws[wk + 2][wrow] = w0.z; Ws[wk + 3][wrow] = w0.w;
-        __syncthreads();
-        if (k0 + 16 < kend) {
-            x0 = *reinterpret_cast<const float4*>(xp0 + k0 + 16);
-            x1 = *reinterpret_cast<const float4*>(xp1 + k0 + 16);
-            if (wvalid) w0 = __ldg(reinterpret_cast<const float4*>(wp + k0 + 16));
+        for (int b = 0; b < T::RA; ++b) acc[a][b] = 0.f;
+    // one k tile: TS rows of X and TR rows of W, 4 chunks of 16 bytes each
+    auto load = [&](int stage, int k0) {
+        for (int e = threadIdx.x; e < 4 * (TS + TR); e += 256) {
+            const int c = e & 3;
+            if (e < 4 * TS) {
+                const int sl = e >> 2;
+                cp_async16(Xs + stage * T::XS + sl * T::LDS + 4 * c, X + (size_t)(slot0 + sl) * ld + k0 + 4 * c, true);
+            } else {
+                const int rw = (e - 4 * TS) >> 2;
+                const bool ok = row0 + rw < nrows;
+                cp_async16(Ws + stage * T::WS + rw * T::LDS + 4 * c,
+                           ok ? W + (size_t)(row0 + rw) * ld + k0 + 4 * c : W, ok);
+            }
         }
-        float part[8][4];
+    };
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+    for (int s = 0; s < T::STAGES - 1; ++s) {
+        if (kbeg + 16 * s < kend) load(s, kbeg + 16 * s);
+        cp_async_commit();
+    }
+    int it = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += 16, ++it) {
+        cp_async_wait<T::STAGES - 2>();
+        __syncthreads();
+        const int kn = k0 + 16 * (T::STAGES - 1);
+        if (kn < kend) load((it + T::STAGES - 1) % T::STAGES, kn);
+        cp_async_commit();
+        const float* xs = Xs + (it % T::STAGES) * T::XS;
+        const float* ws = Ws + (it % T::STAGES) * T::WS;
+        float part[T::SA][T::RA];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) part[a][b] = 0.f;
+        for (int a = 0; a < T::SA; ++a)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&Xs[k][ty * 8 + 4]);
-            const float4 bb = *reinterpret_cast<const float4*>(&Ws[k][tx * 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[4] = {bb.x, bb.y, bb.z, bb.w};
+            for (int b = 0; b < T::RA; ++b) part[a][b] = 0.f;
 #pragma unroll
-            for (int a = 0; a < 8; ++a)
+        for (int kk = 0; kk < 16; kk += 4) {
+            float4 xa[T::SA], wb[T::RA];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) part[a][b] = fmaf(av[a], bv[b], part[a][b]);
+            for (int a = 0; a < T::SA; ++a) xa[a] = *reinterpret_cast<const float4*>(xs + (ty + 16 * a) * T::LDS + kk);
+#pragma unroll
+            for (int b = 0; b < T::RA; ++b) wb[b] = *reinterpret_cast<const float4*>(ws + (tx + 16 * b) * T::LDS + kk);
+#pragma unroll
+            for (int a = 0; a < T::SA; ++a)
+#pragma unroll
+                for (int b = 0; b < T::RA; ++b) {
+                    part[a][b] = fmaf(xa[a].x, wb[b].x, part[a][b]);
+                    part[a][b] = fmaf(xa[a].y, wb[b].y, part[a][b]);
+                    part[a][b] = fmaf(xa[a].z, wb[b].z, part[a][b]);
+                    part[a][b] = fmaf(xa[a].w, wb[b].w, part[a][b]);
+                }
         }
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < T::SA; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] += part[a][b];
-        __syncthreads();
+            for (int b = 0; b < T::RA; ++b) acc[a][b] += part[a][b];
     }
+    cp_async_wait<0>();
+}
+
+// Slot range of a CTA: TS-slot sub-tiles of the 128-slot tiles; a sub-tile
+// with no active QP has nothing to do (the active QPs of a bank group fill
+// its slots from the first one on, so perm of the first slot decides).
+template <int TS>
+__device__ __forceinline__ bool fp32_slots(const BatchParams& p, int& tile, int& slot0) {
+    tile = (blockIdx.y * TS) / kSlotTile;
+    slot0 = blockIdx.y * TS;
+    if (tile >= p.counters[CNT_TILES]) return false;
+    return TS == kSlotTile || p.perm[slot0] >= 0;
 }
 
 // One layer for every active slot tile (FP32 backend, and the accurate first
 // layer of a chunk in the BF16 split form).
+template <int TS, int TR>
 __global__ void __launch_bounds__(256) batch_layer_fp32_kernel(BatchParams p, W32Ptrs wp) {
-    const int tile = blockIdx.y;
-    if (tile >= p.counters[CNT_TILES]) return;
+    int tile, slot0;
+    if (!fp32_slots<TS>(p, tile, slot0)) return;
     const int ri = p.tile_rho[tile];
-    const int slot0 = tile * kSlotTile, row0 = blockIdx.x * 64;
-    float acc[8][4];
-    fp32_tile(p.Sin, wp.w[ri], p.ldk, 0, p.ldk, p.R, slot0, row0, acc);
+    const int row0 = blockIdx.x * TR;
+    float acc[TS / 16][TR / 16];
+    fp32_tile<TS, TR>(p.Sin, wp.w[ri], p.ldk, 0, p.ldk, p.R, slot0, row0, acc);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int slot = slot0 + ty * 8 + a;
+    for (int a = 0; a < TS / 16; ++a) {
+        const int slot = slot0 + ty + 16 * a;
         const int qp = p.perm[slot];
         if (qp < 0) continue;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int r = row0 + tx * 4 + b;
+        for (int b = 0; b < TR / 16; ++b) {
+            const int r = row0 + tx + 16 * b;
             if (r < p.R) layer_elem(p, slot, qp, ri, r, acc[a][b]);
         }
     }
 }
 
+// max over the 16 threads of a half warp that share ty (NaN kept)
+__device__ __forceinline__ float half_warp_max(float v) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v = nmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Residual products (FP32 backend).  Phase 1: [P; A] x over the x columns of
 // the check operand; phase 2: A^T lam_std over its multiplier columns.
+template <int TS, int TR>
 __global__ void __launch_bounds__(256) batch_check_fp32_kernel(BatchParams p, const float* __restrict__ Wc, int phase) {
-    const int tile = blockIdx.y;
-    if (tile >= p.counters[CNT_TILES]) return;
+    int tile, slot0;
+    if (!fp32_slots<TS>(p, tile, slot0)) return;
     const int ri = p.tile_rho[tile];
-    const int slot0 = tile * kSlotTile, row0 = blockIdx.x * 64;
+    const int row0 = blockIdx.x * TR;
     const int rows = phase == 1 ? p.n + p.m : p.n;
-    float acc[8][4];
+    float acc[TS / 16][TR / 16];
     if (phase == 1)
-        fp32_tile(p.CK32, Wc, p.ldkc, 0, p.n64, rows, slot0, row0, acc);
+        fp32_tile<TS, TR>(p.CK32, Wc, p.ldkc, 0, p.n64, rows, slot0, row0, acc);
     else
-        fp32_tile(p.CK32, Wc, p.ldkc, p.n64, p.ldkc, rows, slot0, row0, acc);
+        fp32_tile<TS, TR>(p.CK32, Wc, p.ldkc, p.n64, p.ldkc, rows, slot0, row0, acc);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        const int slot = slot0 + ty * 8 + a;
-        const int qp = p.perm[slot];
-        if (qp < 0) continue;
+    for (int a = 0; a < TS / 16; ++a) {
+        const int slot = slot0 + ty + 16 * a;
+        const int qp = p.perm[slot];     // the same in the 16 threads of a half warp
         float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f;
+        if (qp >= 0) {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int r = row0 + tx * 4 + b;
-            if (r >= rows) continue;
-            if (phase == 1) check1_elem(p, slot, qp, ri, r, acc[a][b], r0, r1, r2, r3);
-            else check2_elem(p, qp, r, acc[a][b], r0, r1);
+            for (int b = 0; b < TR / 16; ++b) {
+                const int r = row0 + tx + 16 * b;
+                if (r >= rows) continue;
+                if (phase == 1) check1_elem(p, slot, qp, ri, r, acc[a][b], r0, r1, r2, r3);
+                else check2_elem(p, qp, r, acc[a][b], r0, r1);
+            }
         }
+        r0 = half_warp_max(r0);
+        r1 = half_warp_max(r1);
+        r2 = half_warp_max(r2);
+        r3 = half_warp_max(r3);
+        if (qp < 0 || tx != 0) continue;
         if (phase == 1) {
             red_slot(p.RED, qp, RW_RP, r0);
             red_slot(p.RED, qp, RW_AX, r1);
@@ -215,6 +278,40 @@ __global__ void __launch_bounds__(256) batch_check_fp32_kernel(BatchParams p, co
             red_slot(p.RED, qp, RW_ATL, r1);
         }
     }
+}
+
+// Launch helpers: the full-width tile (128 slots x 64 rows) while more than
+// two slot tiles are active, else 32 x 32 sub-tiles, which skip the empty
+// slots of the last tile of a bank group and give the convergence tail more
+// CTAs.
+template <int TS, int TR>
+int launch_layer32(relu_qp_t h, const BatchParams& q, const W32Ptrs& wp, int tiles_max) {
+    auto k = batch_layer_fp32_kernel<TS, TR>;
+    RQ_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, F32Tile<TS, TR>::BYTES));
+    k<<<dim3(ceil_div(h->R, TR), tiles_max * (kSlotTile / TS)), 256, F32Tile<TS, TR>::BYTES, h->stream>>>(q, wp);
+    RQ_CUDA(h, cudaGetLastError());
+    return RELU_QP_OK;
+}
+
+int layer32(relu_qp_t h, const BatchParams& q, const W32Ptrs& wp, int tiles_max, int active) {
+    if (ceil_div(active, kSlotTile) <= 2) return launch_layer32<32, 32>(h, q, wp, tiles_max);
+    return launch_layer32<128, 64>(h, q, wp, tiles_max);
+}
+
+template <int TS, int TR>
+int launch_check32(relu_qp_t h, const BatchParams& q, const float* Wc, int tiles_max, int phase) {
+    auto k = batch_check_fp32_kernel<TS, TR>;
+    RQ_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, F32Tile<TS, TR>::BYTES));
+    const int rows = phase == 1 ? h->n + h->m : h->n;
+    k<<<dim3(ceil_div(rows, TR), tiles_max * (kSlotTile / TS)), 256, F32Tile<TS, TR>::BYTES, h->stream>>>(q, Wc,
+                                                                                                         phase);
+    RQ_CUDA(h, cudaGetLastError());
+    return RELU_QP_OK;
+}
+
+int check32(relu_qp_t h, const BatchParams& q, const float* Wc, int tiles_max, int active, int phase) {
+    if (ceil_div(active, kSlotTile) <= 2) return launch_check32<32, 32>(h, q, Wc, tiles_max, phase);
+    return launch_check32<128, 64>(h, q, Wc, tiles_max, phase);
 }
 
 struct DecideArgs {
@@ -230,67 +327,85 @@ struct DecideArgs {
     int *done_list, *done_count;
 };
 
-// Stop test and penalty rule per QP (one warp per QP).
-__global__ void batch_decide_kernel(BatchParams p, DecideArgs d) {
-    const int qp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (qp >= d.B || d.status[qp] != QP_ACTIVE) return;
+// Stop test and penalty rule per QP (one 128-thread block per QP: thread 0
+// decides, the block copies the outputs of a finished QP or rebases lam' on a
+// bank switch).
+constexpr int kDecideThreads = 128;
+
+__global__ void __launch_bounds__(kDecideThreads) batch_decide_kernel(BatchParams p, DecideArgs d) {
+    const int qp = blockIdx.x;
+    if (qp >= d.B) return;
+    __shared__ int s_act, s_nri;    // s_act: -1 not active, 0 continue, 1 finished, 2 bank switch
     unsigned* red = p.RED + (size_t)qp * RW_WORDS;
-    const double rp = __uint_as_float(red[RW_RP]), rd = __uint_as_float(red[RW_RD]);
-    const double nax = __uint_as_float(red[RW_AX]), nz = __uint_as_float(red[RW_Z]);
-    const double npx = __uint_as_float(red[RW_PX]), natl = __uint_as_float(red[RW_ATL]);
-    const double qn = p.QN[qp];
-    const int ri = d.rho_idx[qp];
-    const int it_qp = d.serve_len > 0 ? d.iters[qp] + d.serve_len : d.it;
-    const bool final_qp = d.serve_len > 0 ? it_qp >= d.max_iter : d.final_iter != 0;
-    const bool numerical = !(isfinite(rp) && isfinite(rd) && isfinite(npx) && isfinite(natl));
-    const double eps_p = d.eps_abs + d.eps_rel * fmax(nax, nz);
-    const double eps_d = d.eps_abs + d.eps_rel * fmax(fmax(npx, natl), qn);
-    const bool converged = !numerical && rp <= eps_p && rd <= eps_d;
-    if (converged || numerical || final_qp) {
-        for (int k = lane; k < p.n; k += 32) d.XO[(size_t)qp * p.n + k] = p.Y[(size_t)qp * p.ldn + k];
-        for (int i = lane; i < p.m; i += 32) {
+    if (threadIdx.x == 0) {
+        int act = -1, nri = 0;
+        if (d.status[qp] == QP_ACTIVE) {
+            const double rp = __uint_as_float(red[RW_RP]), rd = __uint_as_float(red[RW_RD]);
+            const double nax = __uint_as_float(red[RW_AX]), nz = __uint_as_float(red[RW_Z]);
+            const double npx = __uint_as_float(red[RW_PX]), natl = __uint_as_float(red[RW_ATL]);
+            const double qn = p.QN[qp];
+            const int ri = d.rho_idx[qp];
+            const int it_qp = d.serve_len > 0 ? d.iters[qp] + d.serve_len : d.it;
+            const bool final_qp = d.serve_len > 0 ? it_qp >= d.max_iter : d.final_iter != 0;
+            const bool numerical = !(isfinite(rp) && isfinite(rd) && isfinite(npx) && isfinite(natl));
+            const double eps_p = d.eps_abs + d.eps_rel * fmax(nax, nz);
+            const double eps_d = d.eps_abs + d.eps_rel * fmax(fmax(npx, natl), qn);
+            const bool converged = !numerical && rp <= eps_p && rd <= eps_d;
+            act = 0;
+            nri = ri;
+            if (converged || numerical || final_qp) {
+                act = 1;
+                d.status[qp] = numerical ? RELU_QP_NUMERICAL : (converged ? RELU_QP_SOLVED : RELU_QP_MAX_ITER);
+                d.iters[qp] = it_qp;
+                d.rpo[qp] = (float)rp;
+                d.rdo[qp] = (float)rd;
+                if (d.done_list) d.done_list[atomicAdd(d.done_count, 1)] = qp;
+            } else {
+                if (d.adaptive) {
+                    const double num = rp * fmax(fmax(npx, natl), fmax(qn, 1e-4));
+                    const double den = rd * fmax(fmax(nax, nz), 1e-4);
+                    if (num > 0.0 && den > 0.0) {
+                        const double est = p.rhod[ri] * sqrt(num / den);
+                        if (isfinite(est) && est > 0.0) {
+                            const double le = log(est);
+                            double best = 1e300;
+                            for (int k = 0; k < p.nr; ++k) {
+                                const double dd = fabs(le - log(p.rhod[k]));
+                                if (dd < best) { best = dd; nri = k; }
+                            }
+                        }
+                    }
+                    if (nri != ri) {
+                        act = 2;
+                        d.rho_idx[qp] = nri;
+                        d.nsw[qp] += 1;
+                    }
+                }
+                if (d.serve_len > 0) d.iters[qp] = it_qp;
+            }
+        }
+        s_act = act;
+        s_nri = nri;
+    }
+    __syncthreads();
+    const int act = s_act;
+    if (act < 0) return;
+    if (act == 1) {
+        for (int k = threadIdx.x; k < p.n; k += kDecideThreads) d.XO[(size_t)qp * p.n + k] = p.Y[(size_t)qp * p.ldn + k];
+        for (int i = threadIdx.x; i < p.m; i += kDecideThreads) {
             d.ZO[(size_t)qp * p.m + i] = p.Z[(size_t)qp * p.ldm + i];
             d.LO[(size_t)qp * p.m + i] = p.LSTD[(size_t)qp * p.ldm + i];
         }
-        if (lane == 0) {
-            d.status[qp] = numerical ? RELU_QP_NUMERICAL : (converged ? RELU_QP_SOLVED : RELU_QP_MAX_ITER);
-            d.iters[qp] = it_qp;
-            d.rpo[qp] = (float)rp;
-            d.rdo[qp] = (float)rd;
-            if (d.done_list) d.done_list[atomicAdd(d.done_count, 1)] = qp;
-        }
-    } else if (d.adaptive) {
-        const double num = rp * fmax(fmax(npx, natl), fmax(qn, 1e-4));
-        const double den = rd * fmax(fmax(nax, nz), 1e-4);
-        int nri = ri;
-        if (num > 0.0 && den > 0.0) {
-            const double est = p.rhod[ri] * sqrt(num / den);
-            if (isfinite(est) && est > 0.0) {
-                const double le = log(est);
-                double best = 1e300;
-                for (int k = 0; k < p.nr; ++k) {
-                    const double dd = fabs(le - log(p.rhod[k]));
-                    if (dd < best) { best = dd; nri = k; }
-                }
-            }
-        }
-        if (nri != ri) {
-            // rebase lam' so that the next layer is standard ADMM with the new rho
-            for (int i = lane; i < p.m; i += 32) {
-                const size_t o = (size_t)qp * p.ldm + i;
-                const float rho_i = (float)(p.rhod[nri] * (double)p.rs[i]);
-                p.LAM[o] = p.LSTD[o] - rho_i * (p.AY[o] - p.Z[o]);
-            }
-            if (lane == 0) {
-                d.rho_idx[qp] = nri;
-                d.nsw[qp] += 1;
-            }
+    } else if (act == 2) {
+        // rebase lam' so that the next layer is standard ADMM with the new rho
+        const int nri = s_nri;
+        for (int i = threadIdx.x; i < p.m; i += kDecideThreads) {
+            const size_t o = (size_t)qp * p.ldm + i;
+            const float rho_i = (float)(p.rhod[nri] * (double)p.rs[i]);
+            p.LAM[o] = p.LSTD[o] - rho_i * (p.AY[o] - p.Z[o]);
         }
     }
-    if (d.serve_len > 0 && !(converged || numerical || final_qp) && lane == 0) d.iters[qp] = it_qp;
-    __syncwarp();
-    if (lane < RW_WORDS) red[lane] = 0u;
+    if (threadIdx.x < RW_WORDS) red[threadIdx.x] = 0u;
 }
 
 // Regroup the active QPs by bank index: slots [base_g, base_g + count_g) hold
@@ -347,34 +462,44 @@ __global__ void __launch_bounds__(1024) batch_assign_kernel(int B, int slots, in
 }
 
 // Operand of the first layer of a chunk: s = [x; 2 rho z - lam'] per slot, in
-// FP32 or as a 3-way BF16 split; padding slots get zeros.
+// FP32 or as a 3-way BF16 split; padding slots get zeros.  One thread per 4
+// consecutive columns of a slot.
 __global__ void batch_fill_kernel(BatchParams p, const int* __restrict__ rho_idx, float* S32, __nv_bfloat16* T,
                                   size_t part) {
-    const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int q4 = p.ldk >> 2;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = (int)(e / q4);
+    const int k0 = (int)(e % q4) * 4;
     if (slot >= p.counters[CNT_TILES] * kSlotTile) return;
     const int qp = p.perm[slot];
     const int ri = qp >= 0 ? rho_idx[qp] : 0;
-    for (int k = lane; k < p.ldk; k += 32) {
-        float v = 0.f;
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int k = k0 + t;
+        v[t] = 0.f;
         if (qp >= 0) {
             if (k < p.n) {
-                v = p.Y[(size_t)qp * p.ldn + k];
+                v[t] = p.Y[(size_t)qp * p.ldn + k];
             } else if (k < p.R) {
                 const int i = k - p.n;
                 const size_t o = (size_t)qp * p.ldm + i;
-                v = 2.f * (p.rho[ri] * p.rs[i]) * p.Z[o] - p.LAM[o];
+                v[t] = 2.f * (p.rho[ri] * p.rs[i]) * p.Z[o] - p.LAM[o];
             }
         }
-        const size_t o = (size_t)slot * p.ldk + k;
-        if (S32) {
-            S32[o] = v;
-        } else {
-            __nv_bfloat16 a, b, c;
-            split3(v, a, b, c);
-            T[o] = a;
-            T[o + part] = b;
-            T[o + 2 * part] = c;
+    }
+    const size_t o = (size_t)slot * p.ldk + k0;
+    if (S32) {
+        st4(S32 + o, v);
+    } else {
+        __nv_bfloat16 a[4], b[4], c[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) split3(v[t], a[t], b[t], c[t]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            T[o + t] = a[t];
+            T[o + t + part] = b[t];
+            T[o + t + 2 * part] = c[t];
         }
     }
 }
@@ -552,10 +677,13 @@ __global__ void tune_perm_kernel(int slots, int cap, int active_tiles, int* perm
     }
 }
 
-// Choose the BN (rows per tile) of the tcgen05 layer for every number of
-// active slot tiles, and of the check kernels on the full capacity, by timing
-// them (state values do not matter here; every buffer they touch is
-// re-initialised by the next solve).
+// Choose the K split and the BN (rows per tile) of the tcgen05 refined layer
+// for every number of active slot tiles, and the BN of the check kernels on
+// the full capacity, by timing them (state values do not matter here; every
+// buffer they touch is re-initialised by the next solve).  The split is one
+// per handle, so that a QP's arithmetic never depends on its batch: the
+// split whose best widths give the smallest summed time over the measured
+// tile counts wins.  RELU_QP_TUNE_LOG=1 prints the measurements to stderr.
 int tc_tune(relu_qp_t h) {
     BatchWork& w = h->bw;
     BatchParams p = base_params(h);
@@ -566,35 +694,59 @@ int tc_tune(relu_qp_t h) {
     p.Dlo = OP + 3 * opart;
     p.CK = static_cast<__nv_bfloat16*>(w.CK);
     const int tiles = w.slots / kSlotTile;
-    int widths[16];
-    const int nw = tc_layer_widths(h, widths, 16);
+    const char* log_env = std::getenv("RELU_QP_TUNE_LOG");
+    const bool log = log_env && log_env[0] == '1';
     // measured tile counts: every count up to 8, then every 4th up to 32, then every 16th
     std::vector<int> counts;
     for (int t = 1; t <= tiles; ++t)
         if (t <= 8 || (t <= 32 && t % 4 == 0) || t % 16 == 0 || t == tiles) counts.push_back(t);
-    std::vector<int> table(tiles + 1, 128);
-    int best_full = 128;
-    for (int t : counts) {
-        tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, t, w.perm, w.tile_rho,
-                                                                         w.counters);
-        RQ_CUDA(h, cudaGetLastError());
-        float best = 1e30f;
-        int best_bn = 128;
-        for (int i = 0; i < nw; ++i) {
-            const int bn = widths[i];
-            RQ_TRY(tc_set_tiles(h, bn, 128));
-            RQ_TRY(tc_layer(h, p, 0, tiles, t));
-            RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-            for (int rep = 0; rep < 3; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, t));
-            RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
-            RQ_CUDA(h, cudaEventSynchronize(h->ev1));
-            float ms = 0.f;
-            RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-            if (ms < best) { best = ms; best_bn = bn; }
+    int splits[4];
+    const int nsplit = tc_splits(h, splits, 4);
+    double best_total = 1e300;
+    int best_ks = tc_split(h), best_full = 128;
+    std::vector<int> best_table;
+    for (int si = 0; si < nsplit; ++si) {
+        const int ks = splits[si];
+        if (ks == 1 && nsplit > 1) continue;   // a split always wins when the problem allows one
+        RQ_TRY(tc_set_split(h, ks));
+        int widths[16];
+        const int nw = tc_layer_widths(h, widths, 16);
+        std::vector<int> table(tiles + 1, widths[0]);
+        double total = 0.0;
+        int full_bn = widths[0];
+        for (int t : counts) {
+            tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, t, w.perm, w.tile_rho,
+                                                                             w.counters);
+            RQ_CUDA(h, cudaGetLastError());
+            float best = 1e30f;
+            int best_bn = widths[0];
+            for (int i = 0; i < nw; ++i) {
+                const int bn = widths[i];
+                RQ_TRY(tc_set_tiles(h, bn, 128));
+                RQ_TRY(tc_layer(h, p, 0, tiles, t));
+                RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+                RQ_TRY(tc_layer(h, p, 0, tiles, t));
+                for (int rep = 1; rep < 4; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, t, true));
+                RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+                RQ_CUDA(h, cudaEventSynchronize(h->ev1));
+                float ms = 0.f;
+                RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+                if (log) std::fprintf(stderr, "relu_qp tune: n=%d m=%d ks=%d tiles=%d bn=%d us=%.2f\n", h->n, h->m,
+                                      ks, t, bn, 1e3f * ms / 4);
+                if (ms < best) { best = ms; best_bn = bn; }
+            }
+            for (int u = t; u <= tiles; ++u) table[u] = best_bn;   // until the next measured count
+            total += best;
+            full_bn = best_bn;
         }
-        for (int u = t; u <= tiles; ++u) table[u] = best_bn;   // until the next measured count
-        best_full = best_bn;
+        if (total < best_total) {
+            best_total = total;
+            best_ks = ks;
+            best_table = table;
+            best_full = full_bn;
+        }
     }
+    RQ_TRY(tc_set_split(h, best_ks));
     tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, tiles, w.perm, w.tile_rho,
                                                                      w.counters);
     RQ_CUDA(h, cudaGetLastError());
@@ -619,7 +771,12 @@ int tc_tune(relu_qp_t h) {
         if (ms < bestc) { bestc = ms; best_cbn = bn; }
     }
     RQ_TRY(tc_set_tiles(h, best_bn, best_cbn));
-    RQ_TRY(tc_set_tiles_for(h, table));
+    RQ_TRY(tc_set_tiles_for(h, best_table));
+    if (log) {
+        std::fprintf(stderr, "relu_qp tune: chose ks=%d, widths by active tiles:", best_ks);
+        for (int t = 1; t <= tiles; ++t) std::fprintf(stderr, " %d", best_table[t]);
+        std::fprintf(stderr, "\n");
+    }
     if (tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "tensor-core kernel wait passed its deadline while tuning");
     RQ_CUDA(h, cudaMemsetAsync(w.RED, 0, sizeof(unsigned) * (size_t)w.cap * RW_WORDS, h->stream));
     RQ_CUDA(h, cudaMemsetAsync(w.counters, 0, sizeof(int) * CNT_WORDS, h->stream));
@@ -740,7 +897,7 @@ int regroup_slots(relu_qp_t h, const BatchParams& p, int nqp, bool assign) {
         ++h->launches;
     }
     const bool split_operand = bf16 && w.rebase_tc;
-    batch_fill_kernel<<<ceil_div(w.slots * 32, 256), 256, 0, h->stream>>>(
+    batch_fill_kernel<<<(int)((size_t)w.slots * (w.ldk / 4) / 256 + 1), 256, 0, h->stream>>>(
         p, w.rho_idx, split_operand ? nullptr : w.S32, split_operand ? OP + 4 * opart : nullptr, opart);
     RQ_CUDA(h, cudaGetLastError());
     ++h->launches;
@@ -759,6 +916,9 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
     __nv_bfloat16* OP = static_cast<__nv_bfloat16*>(w.OPND);
     W32Ptrs wp{};
     for (int r = 0; r < h->nr; ++r) wp.w[r] = h->be[r].Wt;
+    // profiling: one event pair around the refined layers of the chunk (events
+    // between them would break the programmatic overlap of consecutive layers)
+    const bool timed = h->prof_on && bf16 && len > 1 && prof_used + 2 <= h->prof_ev.size();
     for (int j = 0; j < len; ++j) {
         BatchParams q = p;
         q.flags = 0;
@@ -774,24 +934,22 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
                 // nearest); the tensor core's truncating accumulation of the full
                 // operand would set the fixed point's accuracy instead
                 q.Sin = w.S32;
-                dim3 grid(ceil_div(R, 64), tiles_max);
-                batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
-                RQ_CUDA(h, cudaGetLastError());
+                RQ_TRY(layer32(h, q, wp, tiles_max, active));
                 ++h->launches;
             } else {
                 // operand set read by this layer: 4..6 = s (3-way), else pair ((j-1)&1)
-                const bool timed = h->prof_on && j > 0 && prof_used + 2 <= h->prof_ev.size();
-                if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+                if (timed && j == 1) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
                 RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max,
-                                ceil_div(active, kSlotTile) + h->nr - 1));
+                                ceil_div(active, kSlotTile) + h->nr - 1, j > 0));
                 ++h->launches;
                 if (j > 0) {
                     ++h->layer_launches;
                     // three BF16 products of the (n+m) x (n+m) factored layer per active QP
                     h->layer_flops += 2.0 * 3.0 * (double)R * (double)R * (double)active;
                 }
-                if (timed) {
+                if (timed && j == len - 1) {
                     RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                    h->prof_span_launches.push_back(len - 1);
                     prof_used += 2;
                 }
             }
@@ -799,16 +957,15 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
             q.Sin = w.S32 + (size_t)(j & 1) * opart;
             q.Sout = w.S32 + (size_t)((j + 1) & 1) * opart;
             q.CK32 = w.CK32;
-            dim3 grid(ceil_div(R, 64), tiles_max);
-            const bool timed = h->prof_on && prof_used + 2 <= h->prof_ev.size();
-            if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
-            batch_layer_fp32_kernel<<<grid, 256, 0, h->stream>>>(q, wp);
-            RQ_CUDA(h, cudaGetLastError());
+            const bool timed32 = h->prof_on && prof_used + 2 <= h->prof_ev.size();
+            if (timed32) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+            RQ_TRY(layer32(h, q, wp, tiles_max, active));
             ++h->launches;
             ++h->layer_launches;
             h->layer_flops += 2.0 * (double)R * (double)R * (double)active;   // one FP32 product per QP
-            if (timed) {
+            if (timed32) {
                 RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                h->prof_span_launches.push_back(1);
                 prof_used += 2;
             }
         }
@@ -817,9 +974,8 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
 }
 
 // Residual products of a check: [P; A] x, then A^T lam_std (Eqs. primal, dual).
-int run_check(relu_qp_t h, const BatchParams& p) {
+int run_check(relu_qp_t h, const BatchParams& p, int active) {
     BatchWork& w = h->bw;
-    const int n = h->n, m = h->m;
     const int tiles_max = w.slots / kSlotTile;
     BatchParams q = p;
     if (w.prec == RELU_QP_PREC_BF16X3 && w.check_tc) {
@@ -828,10 +984,8 @@ int run_check(relu_qp_t h, const BatchParams& p) {
         RQ_TRY(tc_check(h, q, 2, tiles_max));
     } else {
         q.CK32 = w.CK32;
-        batch_check_fp32_kernel<<<dim3(ceil_div(n + m, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 1);
-        RQ_CUDA(h, cudaGetLastError());
-        batch_check_fp32_kernel<<<dim3(ceil_div(n, 64), tiles_max), 256, 0, h->stream>>>(q, w.Wc32, 2);
-        RQ_CUDA(h, cudaGetLastError());
+        RQ_TRY(check32(h, q, w.Wc32, tiles_max, active, 1));
+        RQ_TRY(check32(h, q, w.Wc32, tiles_max, active, 2));
     }
     h->launches += 2;
     return RELU_QP_OK;
@@ -856,6 +1010,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     const int tiles_max = w.slots / kSlotTile;
     // ---- start state ----
     const int rho0 = nearest_rho(h, h->opts.rho0);
+    h->prof_span_launches.clear();
     int* rw_dev = nullptr;
     if (rw) {
         RQ_CUDA(h, cudaMemcpyAsync(w.iters, rw, sizeof(int) * B, cudaMemcpyDefault, h->stream));
@@ -886,10 +1041,10 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         RQ_TRY(run_layers(h, p, len, check, active, prof_used));
         it += len;
         if (check) {
-            RQ_TRY(run_check(h, p));
+            RQ_TRY(run_check(h, p, active));
             DecideArgs d{B, it, last_chunk ? 1 : 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO,
                          w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, 0, max_iter, nullptr, nullptr};
-            batch_decide_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(p, d);
+            batch_decide_kernel<<<B, kDecideThreads, 0, h->stream>>>(p, d);
             RQ_CUDA(h, cudaGetLastError());
             ++h->launches;
         }
@@ -911,8 +1066,9 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         float ms = 0.f;
         RQ_CUDA(h, cudaEventElapsedTime(&ms, h->prof_ev[e], h->prof_ev[e + 1]));
         h->layer_ms += ms;
-        ++h->layer_timed;
+        h->layer_timed += h->prof_span_launches[e / 2];
     }
+    h->prof_span_launches.clear();
     // ---- outputs ----
     RQ_CUDA(h, cudaMemcpyAsync(Xo, w.XO, sizeof(float) * B * n, cudaMemcpyDefault, h->stream));
     if (Zo && m > 0) RQ_CUDA(h, cudaMemcpyAsync(Zo, w.ZO, sizeof(float) * B * m, cudaMemcpyDefault, h->stream));
@@ -1199,13 +1355,14 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
     // ---- one chunk ----
     const int ci = h->opts.check_interval;
     size_t prof_used = 0;
+    h->prof_span_launches.clear();    // the server does not read the layer events
     RQ_TRY(regroup_slots(h, p, w.cap, true));
     RQ_TRY(run_layers(h, p, ci, true, f.active, prof_used));
-    RQ_TRY(run_check(h, p));
+    RQ_TRY(run_check(h, p, f.active));
     RQ_SCUDA(s, cudaMemsetAsync(f.d.cnt, 0, sizeof(int), f.stream));
     DecideArgs dd{w.cap, 0, 0, h->opts.adaptive_rho, s->eps_abs, s->eps_rel, w.XO, w.ZO, w.LO,
                   w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, ci, s->max_iter, f.d.done, f.d.cnt};
-    batch_decide_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(p, dd);
+    batch_decide_kernel<<<w.cap, kDecideThreads, 0, f.stream>>>(p, dd);
     RQ_SCUDA(s, cudaGetLastError());
     serve_gather_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(
         p, f.d.done, f.d.cnt, f.d.client_of, w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, w.XO, f.d.Wx, f.d.Wl,

@@ -351,12 +351,17 @@ __device__ __forceinline__ void check2_elem(const BatchParams& p, int qp, int j,
 
 // --- entry points of the tcgen05 backend (batch_tc.cu) ---------------------
 int tc_prepare(relu_qp_t h);                     // BF16 splits of every W_rho and of [P | A^T]
-int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles);
+// operand_set < 0: accurate (3-way) layer; pdl: programmatic dependent launch on the
+// previous kernel of the stream (refined layers only)
+int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles, bool pdl = false);
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phase 1: [P; A] x, 2: A^T lam
 void tc_release(relu_qp_t h);
 int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);           // one refined width for every batch size
 int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles);  // [t] = width for t active slot tiles
 int tc_layer_widths(relu_qp_t h, int* out, int cap);                    // the refined widths available
+int tc_splits(relu_qp_t h, int* out, int cap);   // K splits of the refined layer the problem allows
+int tc_set_split(relu_qp_t h, int ks);           // select one (resets the width table)
+int tc_split(relu_qp_t h);
 int tc_error(relu_qp_t h);    // device error word of the backend (0 = none); clears it
 
 }  // namespace rq

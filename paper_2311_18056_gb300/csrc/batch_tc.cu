@@ -109,6 +109,16 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, u
     }
 }
 
+// Programmatic dependent launch: let the next kernel of the stream start its
+// set-up, and wait until the previous kernel's results are visible (a no-op
+// for a kernel launched without the programmatic-serialisation attribute).
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -217,8 +227,9 @@ struct TcSmem {
     static constexpr int kB = NB * BN * 128;
     static constexpr int kStage = kA + kB;
     static constexpr int kXpose = 8 * 32 * 17 * 4;      // epilogue transpose buffers (8 warps)
-    // partner's partial sums [128 slots][BN / 2 columns], 16-byte chunks swizzled by slot
-    static constexpr int kRecv = KS == 2 ? kSlotTile * (BN / 2) * 4 : 0;
+    // the partners' partial sums of this CTA's columns: KS - 1 buffers of [128 slots][BN / KS
+    // columns], 16-byte chunks swizzled by slot
+    static constexpr int kRecv = KS > 1 ? (KS - 1) * kSlotTile * (BN / KS) * 4 : 0;
     static constexpr int kBytes = STAGES * kStage + kXpose + kRecv + 1024 /* align */ + 256 /* barriers */;
 };
 
@@ -227,24 +238,39 @@ struct TcSmem {
 // values they carry stay in registers whatever the epilogue's register
 // pressure is; both return false when a wait passed its deadline
 // ---------------------------------------------------------------------------
-// bar0: full barriers [0, S), empty barriers [S, 2S); stage s at sbase + s * kStage
+// bar0: full barriers [0, S), empty barriers [S, 2S); stage s at sbase + s * kStage.
+// The weight tiles (B) never change between launches, so the tiles of the first
+// stages are requested before griddep_wait, i.e. while the previous kernel of
+// the stream may still run; the operand tiles (A), which that kernel writes,
+// only after it.
 template <int NA, int NB, int BN, int STAGES, int KSTAGE, int KA>
 __device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sbase, uint32_t bar0,
                                      int nkb, int koff, int a0, int a1, int a2, int b0, int b1, int b2,
                                      int& issued) {
     const int arow[3] = {a0, a1, a2}, brow[3] = {b0, b1, b2};
+    const int pre = nkb < STAGES ? nkb : STAGES;   // stages start empty
+    for (int kb = 0; kb < pre; ++kb) {
+        const uint32_t full = bar0 + 8 * kb;
+        mbar_expect_tx(full, KSTAGE);
+        const uint32_t st = sbase + kb * KSTAGE;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, kb * kBK + koff, brow[b], full);
+    }
+    griddep_wait();
     for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % STAGES;
         const uint32_t ph = (kb / STAGES) & 1;
-        if (!mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) return false;
         const uint32_t full = bar0 + 8 * s;
-        mbar_expect_tx(full, KSTAGE);
         const uint32_t st = sbase + s * KSTAGE;
         const int k0 = kb * kBK + koff;
+        if (kb >= pre) {
+            if (!mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) return false;
+            mbar_expect_tx(full, KSTAGE);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
+        }
 #pragma unroll
         for (int a = 0; a < NA; ++a) tma_load_2d(st + a * kTileBytesA, tmA, k0, arow[a], full);
-#pragma unroll
-        for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
         issued = kb + 1;
     }
     return true;
@@ -285,19 +311,23 @@ __device__ __noinline__ bool issue_mmas(uint32_t sbase, uint32_t bar0, uint32_t 
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-// float offset of (slot, col) in the receive buffer of OWN columns: the
-// 16-byte chunk index is XORed with slot % 8, so the 32 rows a warp writes or
-// reads at one column hit distinct banks (OWN is a multiple of 32)
+// float offset of (slot, col) in a receive buffer of OWN columns: the 16-byte
+// chunk index is XORed with the low bits of the slot, so the rows a warp
+// writes or reads at one column spread over the banks (OWN is 16 or a
+// multiple of 32)
 template <int OWN>
 __device__ __forceinline__ int recv_off(int slot, int col) {
-    return slot * OWN + ((((col >> 2) ^ (slot & 7))) << 2) + (col & 3);
+    constexpr int SW = OWN / 4 >= 8 ? 7 : OWN / 4 - 1;
+    return slot * OWN + ((((col >> 2) ^ (slot & SW))) << 2) + (col & 3);
 }
 
-// KS = 2 (refined layers): the CTA pair of a cluster splits the k-blocks in
-// two halves; after its main loop each CTA sends the partial sums of the
-// partner's half of the columns into the partner's shared memory and
-// finalises its own half.  The sum of the two halves is the same whatever
-// the batch size, so a QP's arithmetic does not depend on its batch.
+// KS = 2 or 4 (refined layers): the KS CTAs of a cluster split the k-blocks
+// into KS fixed ranges; after its main loop each CTA sends every partner the
+// partial sums of that partner's BN / KS columns (into the partner's shared
+// memory) and finalises its own columns, adding the KS partial sums in rank
+// order.  The ranges and the order depend only on the problem (never on the
+// batch size or the tile width), so a QP's arithmetic does not depend on its
+// batch.
 template <int MODE, int BN, int STAGES, int KS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchParams p,
@@ -308,29 +338,29 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     constexpr int ACC = 2;   // significance accumulators of BN columns each
     constexpr int TCOLS = tmem_cols(ACC * BN);
     constexpr int OWN = BN / KS;        // columns this CTA finalises
-    constexpr int PER = OWN / 2;        // columns per epilogue warp
-    static_assert(KS == 1 || KS == 2, "K split of 1 or 2");
+    constexpr int HALVES = OWN >= 32 ? 2 : 1;   // epilogue warps per TMEM lane quadrant
+    constexpr int PER = OWN / HALVES;   // columns per epilogue warp
+    static_assert(KS == 1 || KS == 2 || KS == 4, "K split of 1, 2 or 4");
     static_assert(PER % 16 == 0, "the epilogue works on 16-column pieces");
     using L = TcSmem<NA, NB, BN, STAGES, KS>;
 
     const int tile = blockIdx.y;
     if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA (and the cluster)
     const int slot0 = tile * kSlotTile;
-    const int rank = KS == 2 ? (int)cluster_rank() : 0;
+    const int rank = KS > 1 ? (int)cluster_rank() : 0;
     const int row0 = (blockIdx.x / KS) * BN;
     const int ri = p.tile_rho[tile];
     // k-blocks of this CTA: [kb_begin, kb_begin + kb_count)
-    const int kb_half = (g.num_kb + 1) / 2;
-    const int kb_begin = KS == 2 && rank == 1 ? kb_half : 0;
-    const int kb_count = KS == 2 ? (rank == 0 ? kb_half : g.num_kb - kb_half) : g.num_kb;
+    const int kb_begin = rank * g.num_kb / KS;
+    const int kb_count = (rank + 1) * g.num_kb / KS - kb_begin;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float* xpose = reinterpret_cast<float*>(smem + STAGES * L::kStage);
     float* recv = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
-    // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready, bars[2S+1] partner's
-    // partial sums received (KS = 2); then the TMEM address
+    // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready, bars[2S+1] partners'
+    // partial sums received (KS > 1); then the TMEM address
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
     __shared__ int s_fail;
 
@@ -341,7 +371,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_init(smem_u32(&bars[STAGES + s]), 1);
         }
         mbar_init(smem_u32(&bars[2 * STAGES]), 1);
-        mbar_init(smem_u32(&bars[2 * STAGES + 1]), 8);   // one arrival per epilogue warp of the partner
+        // one arrival per epilogue warp of every partner
+        mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * HALVES);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -354,13 +385,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     fence_before();
     __syncthreads();
     fence_after();
-    // the partner's barriers are initialised before anything is sent to it
-    if (KS == 2) cluster_sync();
+    // the partners' barriers are initialised before anything is sent to them
+    if (KS > 1) cluster_sync();
     const uint32_t tmem = *tmem_holder;
+    // the next kernel of the stream may be scheduled once every CTA got here
+    griddep_launch();
 
     if (warp == 0) {
         // ------------------------- TMA producer -------------------------
         if (lane == 0) {
+            prefetch_map(&tmA);
+            prefetch_map(&tmB);
             int arow[3] = {0, 0, 0}, brow[3] = {0, 0, 0};
 #pragma unroll
             for (int a = 0; a < NA; ++a) arow[a] = g.a_row[a] + slot0;
@@ -393,8 +428,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             }
         }
         __syncwarp();
-    } else {
+    } else if (HALVES == 2 || warp < 6) {
         // ------------------------- epilogue -------------------------
+        // the previous kernel's writes (the carried r, the state) are read and the
+        // operand it read is overwritten: wait for it
+        griddep_wait();
         const int q = warp & 3;                         // TMEM lane quadrant of this warp
         const int half = (warp - 2) >> 2;               // which half of this CTA's columns
         const int slot = slot0 + q * 32 + lane;
@@ -440,27 +478,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (ready) ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
         ready = __all_sync(0xffffffffu, ready);
         if (ready) fence_after();
-        if (KS == 2) {
-            // send the partner's columns of this warp's TMEM lanes: row (q * 32 + lane)
-            // of the partner's receive buffer, columns half * PER ...
-            const int pc0 = (1 - rank) * OWN + half * PER;
-            const uint32_t dst = mapa(smem_u32(recv), (uint32_t)(1 - rank));
+        if (KS > 1) {
+            // send every partner its columns of this warp's TMEM lanes: row (q * 32 + lane)
+            // of buffer j of the partner's receive area (j = this CTA's index among the
+            // partner's senders), columns half * PER ...
             const int srow = q * 32 + lane;
-            if (ready) {
+            for (int pk = 0; pk < KS; ++pk) {
+                if (pk == rank) continue;
+                const int j = rank < pk ? rank : rank - 1;
+                const int pc0 = pk * OWN + half * PER;
+                const uint32_t dst = mapa(smem_u32(recv + j * kSlotTile * OWN), (uint32_t)pk);
+                if (ready) {
 #pragma unroll
-                for (int c = 0; c < PER; c += 16) {
-                    float v[16], w[16];
-                    tmem_ld16(tl + pc0 + c, v);
-                    tmem_ld16(tl + BN + pc0 + c, w);
+                    for (int c = 0; c < PER; c += 16) {
+                        float v[16], w[16];
+                        tmem_ld16(tl + pc0 + c, v);
+                        tmem_ld16(tl + BN + pc0 + c, w);
 #pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, half * PER + c + j), v[j] + w[j],
-                                    v[j + 1] + w[j + 1], v[j + 2] + w[j + 2], v[j + 3] + w[j + 3]);
+                        for (int t = 0; t < 16; t += 4)
+                            st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, half * PER + c + t), v[t] + w[t],
+                                        v[t + 1] + w[t + 1], v[t + 2] + w[t + 2], v[t + 3] + w[t + 3]);
+                    }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(mapa(smem_u32(&bars[2 * STAGES + 1]), (uint32_t)pk));
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(mapa(smem_u32(&bars[2 * STAGES + 1]), (uint32_t)(1 - rank)));
-            // the partner's partial sums of this CTA's columns
+            // the partners' partial sums of this CTA's columns
             bool got = true;
             if (lane == 0) got = mbar_wait_cluster(smem_u32(&bars[2 * STAGES + 1]), 0, 64);
             got = __shfl_sync(0xffffffffu, got, 0);
@@ -487,16 +530,32 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 tmem_ld16(tl + BN + c0, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
-                if (KS == 2) {
+                if (KS > 1) {
+                    // partial sums of ranks 0 .. KS-1 added in rank order
+                    float tot[16];
 #pragma unroll
-                    for (int t = 0; t < 16; t += 4) {
-                        const float4 o =
-                            *reinterpret_cast<const float4*>(recv + recv_off<OWN>(q * 32 + lane, c0 - own0 + t));
-                        v[t] += o.x;
-                        v[t + 1] += o.y;
-                        v[t + 2] += o.z;
-                        v[t + 3] += o.w;
+                    for (int k = 0; k < KS; ++k) {
+                        float part[16];
+                        if (k == rank) {
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) part[t] = v[t];
+                        } else {
+                            const float* rb = recv + (k < rank ? k : k - 1) * kSlotTile * OWN;
+#pragma unroll
+                            for (int t = 0; t < 16; t += 4) {
+                                const float4 o =
+                                    *reinterpret_cast<const float4*>(rb + recv_off<OWN>(q * 32 + lane, c0 - own0 + t));
+                                part[t] = o.x;
+                                part[t + 1] = o.y;
+                                part[t + 2] = o.z;
+                                part[t + 3] = o.w;
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) tot[t] = k == 0 ? part[t] : tot[t] + part[t];
                     }
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) v[t] = tot[t];
                 }
                 if (whole) {
 #pragma unroll
@@ -550,8 +609,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     fence_before();
     __syncthreads();
-    // neither CTA of a pair leaves while the other may still address its shared memory
-    if (KS == 2) cluster_sync();
+    // no CTA of a cluster leaves while another may still address its shared memory
+    if (KS > 1) cluster_sync();
     if (warp == 1) {
         fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
@@ -579,7 +638,7 @@ struct TcState {
     EncodeTiledFn encode = nullptr;
     int bn_layer = 128, bn_check = 128;
     std::vector<int> bn_by_tiles;        // refined-layer width per number of active slot tiles
-    int ks = 1;                          // K split of the refined layer (fixed per handle)
+    int ks = 1;                          // K split of the refined layer (fixed per handle by the tuner)
     int* err = nullptr;                  // = counters + CNT_ERR
     // encoded maps, keyed by box rows
     CUtensorMap opnd_map, ck_map;
@@ -607,59 +666,73 @@ constexpr int stages_for() {
     return s > 4 ? 4 : s;
 }
 
+// pdl: launch with programmatic stream serialisation, so that this kernel's
+// set-up and first weight loads overlap the end of the previous kernel in the
+// stream (the kernel waits for that kernel's results before it touches them)
 template <int MODE, int BN, int KS>
 int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
-              int tiles) {
+              int tiles, bool pdl) {
     constexpr int S = stages_for<MODE, BN, KS>();
     static_assert(S >= 2, "not enough shared memory for two stages");
     using L = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, S, KS>;
     auto kern = tc_gemm_kernel<MODE, BN, S, KS>;
     RQ_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
     const dim3 grid(KS * ceil_div(g.rows, BN), tiles);
-    if (KS == 1) {
-        kern<<<grid, kThreadsTC, L::kBytes, h->stream>>>(a, b, p, g);
-    } else {
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = grid;
-        cfg.blockDim = dim3(kThreadsTC);
-        cfg.dynamicSmemBytes = L::kBytes;
-        cfg.stream = h->stream;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = KS;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        RQ_CUDA(h, cudaLaunchKernelEx(&cfg, kern, a, b, p, g));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreadsTC);
+    cfg.dynamicSmemBytes = L::kBytes;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    if (KS > 1) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = KS;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
     }
-    RQ_CUDA(h, cudaGetLastError());
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    RQ_CUDA(h, cudaLaunchKernelEx(&cfg, kern, a, b, p, g));
     return RELU_QP_OK;
 }
 
-// Refined layer: with a K split of 2 (every problem with at least two
-// k-blocks) the widths are 64, 128 and 192 (each epilogue warp finalises
-// BN / 4 columns; BN = 256 would not leave room for the receive buffer);
-// without, any width of kLayerBN (BN / 2 columns per warp).
+// Refined layer widths by K split: KS = 4 takes 64 and 128 (each CTA
+// finalises 16 or 32 columns; wider tiles leave no room for the three receive
+// buffers), KS = 2 takes 64, 128 and 192 (BN = 256 would not leave room for
+// the receive buffer), KS = 1 any width of kLayerBN (BN / 2 columns per warp).
 int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
-                     const CUtensorMap& a, int tiles) {
+                     const CUtensorMap& a, int tiles, bool pdl) {
     constexpr int M = MODE_LAYER_REFINED;
+    if (ks == 4) {
+        switch (bn) {
+            case 64: return launch_tc<M, 64, 4>(h, a, wmaps[1], p, g, tiles, pdl);
+            case 128: return launch_tc<M, 128, 4>(h, a, wmaps[3], p, g, tiles, pdl);
+            default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
+        }
+    }
     if (ks == 2) {
         switch (bn) {
-            case 64: return launch_tc<M, 64, 2>(h, a, wmaps[1], p, g, tiles);
-            case 128: return launch_tc<M, 128, 2>(h, a, wmaps[3], p, g, tiles);
-            case 192: return launch_tc<M, 192, 2>(h, a, wmaps[5], p, g, tiles);
+            case 64: return launch_tc<M, 64, 2>(h, a, wmaps[1], p, g, tiles, pdl);
+            case 128: return launch_tc<M, 128, 2>(h, a, wmaps[3], p, g, tiles, pdl);
+            case 192: return launch_tc<M, 192, 2>(h, a, wmaps[5], p, g, tiles, pdl);
             default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
         }
     }
     switch (bn) {
-        case 32: return launch_tc<M, 32, 1>(h, a, wmaps[0], p, g, tiles);
-        case 64: return launch_tc<M, 64, 1>(h, a, wmaps[1], p, g, tiles);
-        case 96: return launch_tc<M, 96, 1>(h, a, wmaps[2], p, g, tiles);
-        case 128: return launch_tc<M, 128, 1>(h, a, wmaps[3], p, g, tiles);
-        case 160: return launch_tc<M, 160, 1>(h, a, wmaps[4], p, g, tiles);
-        case 192: return launch_tc<M, 192, 1>(h, a, wmaps[5], p, g, tiles);
-        case 256: return launch_tc<M, 256, 1>(h, a, wmaps[6], p, g, tiles);
+        case 32: return launch_tc<M, 32, 1>(h, a, wmaps[0], p, g, tiles, pdl);
+        case 64: return launch_tc<M, 64, 1>(h, a, wmaps[1], p, g, tiles, pdl);
+        case 96: return launch_tc<M, 96, 1>(h, a, wmaps[2], p, g, tiles, pdl);
+        case 128: return launch_tc<M, 128, 1>(h, a, wmaps[3], p, g, tiles, pdl);
+        case 160: return launch_tc<M, 160, 1>(h, a, wmaps[4], p, g, tiles, pdl);
+        case 192: return launch_tc<M, 192, 1>(h, a, wmaps[5], p, g, tiles, pdl);
+        case 256: return launch_tc<M, 256, 1>(h, a, wmaps[6], p, g, tiles, pdl);
         default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
     }
 }
@@ -668,8 +741,8 @@ int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, cons
 template <int MODE>
 int dispatch_3part(relu_qp_t h, int bn, const CUtensorMap& b64, const CUtensorMap& b128, const BatchParams& p,
                    const TcArgs& g, const CUtensorMap& a, int tiles) {
-    if (bn <= 64) return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles);
-    return launch_tc<MODE, 128, 1>(h, a, b128, p, g, tiles);
+    if (bn <= 64) return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles, false);
+    return launch_tc<MODE, 128, 1>(h, a, b128, p, g, tiles, false);
 }
 
 }  // namespace
@@ -686,7 +759,8 @@ int tc_prepare(relu_qp_t h) {
         return fail(h, RELU_QP_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
     st->encode = reinterpret_cast<EncodeTiledFn>(fn);
     st->err = w.counters + CNT_ERR;
-    // the K split is a property of the problem (never of the batch size)
+    // the K split is a property of the problem (never of the batch size); tc_tune
+    // may switch it between the splits the problem allows before the first solve
     st->ks = w.ldk / kBK >= 2 ? 2 : 1;
     RQ_TRY(encode_2d(h, st, &st->opnd_map, w.OPND, 7ull * w.slots, w.ldk, kSlotTile));
     RQ_TRY(encode_2d(h, st, &st->ck_map, w.CK, 3ull * w.slots, w.ldkc, kSlotTile));
@@ -703,8 +777,29 @@ void tc_release(relu_qp_t h) {
 }
 
 bool width_ok(const TcState* st, int bn) {
+    if (st->ks == 4) return bn == 64 || bn == 128;
     return st->ks == 2 ? (bn == 64 || bn == 128 || bn == 192) : bn_index(bn) >= 0;
 }
+
+// K splits the problem allows: every rank of a split needs at least two k-blocks
+int tc_splits(relu_qp_t h, int* out, int cap) {
+    const int nkb = h->bw.ldk / kBK;
+    int k = 0;
+    for (int ks : {1, 2, 4})
+        if ((ks == 1 || nkb >= 2 * ks) && k < cap) out[k++] = ks;
+    return k;
+}
+
+int tc_set_split(relu_qp_t h, int ks) {
+    TcState* st = static_cast<TcState*>(h->bw.tc);
+    if (ks != 1 && ks != 2 && ks != 4) return fail(h, RELU_QP_ERR_INVALID, "unsupported K split");
+    st->ks = ks;
+    st->bn_layer = ks == 1 ? 128 : 64;
+    st->bn_by_tiles.clear();
+    return RELU_QP_OK;
+}
+
+int tc_split(relu_qp_t h) { return static_cast<const TcState*>(h->bw.tc)->ks; }
 
 int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
@@ -731,7 +826,7 @@ int tc_layer_widths(relu_qp_t h, int* out, int cap) {
     return k;
 }
 
-int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles) {
+int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles, bool pdl) {
     BatchWork& w = h->bw;
     TcState* st = static_cast<TcState*>(w.tc);
     TcArgs g{};
@@ -751,7 +846,7 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int 
     }
     g.a_row[0] = (2 * operand_set) * w.slots;
     g.a_row[1] = (2 * operand_set + 1) * w.slots;
-    return dispatch_refined(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, tiles);
+    return dispatch_refined(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, tiles, pdl);
 }
 
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {

@@ -129,6 +129,7 @@ struct relu_qp_s {
     double layer_ms = 0.0, layer_flops = 0.0;
     int prof_on = 0;
     std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_span_launches;     // launches covered by each recorded event pair
     std::string err;
     std::vector<void*> allocs;               // every cudaMalloc of the handle
 };
