@@ -314,19 +314,6 @@ int check32(relu_qp_t h, const BatchParams& q, const float* Wc, int tiles_max, i
     return launch_check32<128, 64>(h, q, Wc, tiles_max, phase);
 }
 
-struct DecideArgs {
-    int B, it, final_iter, adaptive;
-    double eps_abs, eps_rel;
-    float *XO, *ZO, *LO;
-    int *status, *iters, *rho_idx, *nsw;
-    float *rpo, *rdo;
-    // continuous batching: layers since the previous check of each QP (0 = whole-batch
-    // solve, where `it` and `final_iter` hold for every QP), per-QP layer budget, and the
-    // list the finished QPs are appended to
-    int serve_len, max_iter;
-    int *done_list, *done_count;
-};
-
 // Stop test and penalty rule per QP (one 128-thread block per QP: thread 0
 // decides, the block copies the outputs of a finished QP or rebases lam' on a
 // bank switch).
@@ -340,49 +327,8 @@ __global__ void __launch_bounds__(kDecideThreads) batch_decide_kernel(BatchParam
     if (threadIdx.x == 0) {
         int act = -1, nri = 0;
         if (d.status[qp] == QP_ACTIVE) {
-            const double rp = __uint_as_float(red[RW_RP]), rd = __uint_as_float(red[RW_RD]);
-            const double nax = __uint_as_float(red[RW_AX]), nz = __uint_as_float(red[RW_Z]);
-            const double npx = __uint_as_float(red[RW_PX]), natl = __uint_as_float(red[RW_ATL]);
-            const double qn = p.QN[qp];
-            const int ri = d.rho_idx[qp];
-            const int it_qp = d.serve_len > 0 ? d.iters[qp] + d.serve_len : d.it;
-            const bool final_qp = d.serve_len > 0 ? it_qp >= d.max_iter : d.final_iter != 0;
-            const bool numerical = !(isfinite(rp) && isfinite(rd) && isfinite(npx) && isfinite(natl));
-            const double eps_p = d.eps_abs + d.eps_rel * fmax(nax, nz);
-            const double eps_d = d.eps_abs + d.eps_rel * fmax(fmax(npx, natl), qn);
-            const bool converged = !numerical && rp <= eps_p && rd <= eps_d;
-            act = 0;
-            nri = ri;
-            if (converged || numerical || final_qp) {
-                act = 1;
-                d.status[qp] = numerical ? RELU_QP_NUMERICAL : (converged ? RELU_QP_SOLVED : RELU_QP_MAX_ITER);
-                d.iters[qp] = it_qp;
-                d.rpo[qp] = (float)rp;
-                d.rdo[qp] = (float)rd;
-                if (d.done_list) d.done_list[atomicAdd(d.done_count, 1)] = qp;
-            } else {
-                if (d.adaptive) {
-                    const double num = rp * fmax(fmax(npx, natl), fmax(qn, 1e-4));
-                    const double den = rd * fmax(fmax(nax, nz), 1e-4);
-                    if (num > 0.0 && den > 0.0) {
-                        const double est = p.rhod[ri] * sqrt(num / den);
-                        if (isfinite(est) && est > 0.0) {
-                            const double le = log(est);
-                            double best = 1e300;
-                            for (int k = 0; k < p.nr; ++k) {
-                                const double dd = fabs(le - log(p.rhod[k]));
-                                if (dd < best) { best = dd; nri = k; }
-                            }
-                        }
-                    }
-                    if (nri != ri) {
-                        act = 2;
-                        d.rho_idx[qp] = nri;
-                        d.nsw[qp] += 1;
-                    }
-                }
-                if (d.serve_len > 0) d.iters[qp] = it_qp;
-            }
+            const unsigned w[RW_WORDS] = {red[0], red[1], red[2], red[3], red[4], red[5], red[6], red[7]};
+            act = decide_qp(p, d, qp, w, nri);
         }
         s_act = act;
         s_nri = nri;
@@ -662,6 +608,7 @@ int batch_alloc(relu_qp_t h) {
         RQ_TRY(alloc(h, &w.CK32, (size_t)w.slots * w.ldkc));
         RQ_TRY(alloc(h, &w.Wc32, (size_t)(n + m) * w.ldkc));
     }
+    RQ_TRY(batch_tail_alloc(h));
     return RELU_QP_OK;
 }
 
@@ -1034,6 +981,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     int it = 0;
     int active = B;              // QPs in the batch (known to the host after each check)
     size_t prof_used = 0;
+    bool tail_used = false;
     while (it < max_iter) {
         const int len = std::min(chunk, max_iter - it);
         const bool last_chunk = it + len == max_iter;
@@ -1057,11 +1005,21 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
             if (cnt[CNT_ERR]) break;     // reported below
             if (cnt[CNT_ACTIVE] == 0) break;
             active = cnt[CNT_ACTIVE];
+            if (active <= kTailMax && w.tail_grid > 0) {
+                // the few QPs left finish in one cooperative launch
+                DecideArgs d{B, it, 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO, w.status, w.iters,
+                             w.rho_idx, w.nsw, w.rp, w.rd, 0, max_iter, nullptr, nullptr};
+                RQ_TRY(batch_tail(h, p, d, active, it, max_iter));
+                tail_used = true;
+                break;
+            }
         }
     }
     RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     if (bf16 && tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "a tensor-core kernel wait passed its deadline");
+    if (tail_used && batch_tail_error(h))
+        return fail(h, RELU_QP_ERR_TIMEOUT, "a grid barrier of the convergence-tail kernel passed its deadline");
     for (size_t e = 0; e + 1 < prof_used; e += 2) {
         float ms = 0.f;
         RQ_CUDA(h, cudaEventElapsedTime(&ms, h->prof_ev[e], h->prof_ev[e + 1]));

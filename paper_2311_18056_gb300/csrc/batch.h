@@ -349,6 +349,89 @@ __device__ __forceinline__ void check2_elem(const BatchParams& p, int qp, int j,
     natl = nmax(natl, fabsf(acc));
 }
 
+struct DecideArgs {
+    int B, it, final_iter, adaptive;
+    double eps_abs, eps_rel;
+    float *XO, *ZO, *LO;
+    int *status, *iters, *rho_idx, *nsw;
+    float *rpo, *rdo;
+    // continuous batching: layers since the previous check of each QP (0 = whole-batch
+    // solve, where `it` and `final_iter` hold for every QP), per-QP layer budget, and the
+    // list the finished QPs are appended to
+    int serve_len, max_iter;
+    int *done_list, *done_count;
+};
+
+// Stop test (Eqs. primal, dual with eps_abs + eps_rel * norms) and penalty rule
+// (Eq. rho_update, nearest bank entry in log distance) for one active QP from
+// its reduction words w (|.|-maxima as float bits, RW_*), its bank index ri and
+// (continuous batching) its layer count before this chunk.  Pure: act = 1 if
+// the QP finished (status, it_qp, residuals filled in), 2 if it switches to
+// bank entry nri, 0 otherwise.
+struct Decision {
+    int act, status, it_qp, nri;
+    float rp, rd;
+};
+
+__device__ __forceinline__ Decision decide_eval(const BatchParams& p, const DecideArgs& d, int qp,
+                                                const unsigned (&w)[RW_WORDS], int ri, int iters_before) {
+    const double rp = __uint_as_float(w[RW_RP]), rd = __uint_as_float(w[RW_RD]);
+    const double nax = __uint_as_float(w[RW_AX]), nz = __uint_as_float(w[RW_Z]);
+    const double npx = __uint_as_float(w[RW_PX]), natl = __uint_as_float(w[RW_ATL]);
+    const double qn = p.QN[qp];
+    Decision x{0, 0, d.serve_len > 0 ? iters_before + d.serve_len : d.it, ri, (float)rp, (float)rd};
+    const bool final_qp = d.serve_len > 0 ? x.it_qp >= d.max_iter : d.final_iter != 0;
+    const bool numerical = !(isfinite(rp) && isfinite(rd) && isfinite(npx) && isfinite(natl));
+    const double eps_p = d.eps_abs + d.eps_rel * fmax(nax, nz);
+    const double eps_d = d.eps_abs + d.eps_rel * fmax(fmax(npx, natl), qn);
+    const bool converged = !numerical && rp <= eps_p && rd <= eps_d;
+    if (converged || numerical || final_qp) {
+        x.act = 1;
+        x.status = numerical ? RELU_QP_NUMERICAL : (converged ? RELU_QP_SOLVED : RELU_QP_MAX_ITER);
+        return x;
+    }
+    if (d.adaptive) {
+        const double num = rp * fmax(fmax(npx, natl), fmax(qn, 1e-4));
+        const double den = rd * fmax(fmax(nax, nz), 1e-4);
+        if (num > 0.0 && den > 0.0) {
+            const double est = p.rhod[ri] * sqrt(num / den);
+            if (isfinite(est) && est > 0.0) {
+                const double le = log(est);
+                double best = 1e300;
+                for (int k = 0; k < p.nr; ++k) {
+                    const double dd = fabs(le - log(p.rhod[k]));
+                    if (dd < best) { best = dd; x.nri = k; }
+                }
+            }
+        }
+        if (x.nri != ri) x.act = 2;
+    }
+    return x;
+}
+
+// decide_eval for the QP's own records, which it then updates (status, iters,
+// residuals, the done list; bank index and switch count).  Returns act; nri
+// receives the bank index to continue with.
+__device__ __forceinline__ int decide_qp(const BatchParams& p, const DecideArgs& d, int qp,
+                                         const unsigned (&w)[RW_WORDS], int& nri) {
+    const Decision x = decide_eval(p, d, qp, w, d.rho_idx[qp], d.iters[qp]);
+    nri = x.nri;
+    if (x.act == 1) {
+        d.status[qp] = x.status;
+        d.iters[qp] = x.it_qp;
+        d.rpo[qp] = x.rp;
+        d.rdo[qp] = x.rd;
+        if (d.done_list) d.done_list[atomicAdd(d.done_count, 1)] = qp;
+        return 1;
+    }
+    if (x.act == 2) {
+        d.rho_idx[qp] = x.nri;
+        d.nsw[qp] += 1;
+    }
+    if (d.serve_len > 0) d.iters[qp] = x.it_qp;
+    return x.act;
+}
+
 // --- entry points of the tcgen05 backend (batch_tc.cu) ---------------------
 int tc_prepare(relu_qp_t h);                     // BF16 splits of every W_rho and of [P | A^T]
 // operand_set < 0: accurate (3-way) layer; pdl: programmatic dependent launch on the
@@ -363,5 +446,13 @@ int tc_splits(relu_qp_t h, int* out, int cap);   // K splits of the refined laye
 int tc_set_split(relu_qp_t h, int ks);           // select one (resets the width table)
 int tc_split(relu_qp_t h);
 int tc_error(relu_qp_t h);    // device error word of the backend (0 = none); clears it
+
+// --- convergence tail (batch_tail.cu) --------------------------------------
+constexpr int kTailMax = 8;      // QPs the tail kernel takes at most
+int batch_tail_alloc(relu_qp_t h);
+// Run every remaining chunk (layers it0 + 1 .. max_iter) of the nq <= kTailMax
+// active QPs in one cooperative launch; d holds the decision records.
+int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, int it0, int max_iter);
+int batch_tail_error(relu_qp_t h);   // device error word of the last tail launch
 
 }  // namespace rq

@@ -1,0 +1,461 @@
+// Convergence tail of a batched solve: once at most kTailMax QPs are still
+// active, one cooperative kernel runs every remaining chunk of Algorithm 1 for
+// them (layers, the residual checks of Eqs. primal and dual, the penalty rule
+// of Eq. rho_update and the stop test), with grid barriers between the phases
+// instead of a few kernel launches per layer and a host round trip per check.
+//
+// Arithmetic.  The layer and the residual products are FP32 on the CUDA cores
+// with exactly the summation order of the tiled FP32 kernels (16-wide k steps
+// summed as fresh partials, batch.cu), and the element-wise parts are the same
+// functions (layer_elem, check1_elem, check2_elem, decide_qp), so for the FP32
+// backend a QP's iterates do not depend on whether it finishes in the tiled
+// kernels or here.  In the BF16 split backend the QPs that reach the tail
+// continue in FP32 (more accurate than the split products).
+//
+// Work split.  A warp takes one row r of the product at a time for every tail
+// QP: lane l computes the 16-wide k-step partials of the steps l, l + 32, ...
+// (coalesced 64-byte loads of the row of Wt, reused for all QPs; the QPs'
+// operand vectors are staged in shared memory with every 16-float step padded
+// to 20 floats, so that the lanes' 16-byte reads spread over the banks), the
+// partials go to shared memory, and lane j adds QP j's partials in k order.
+// Every barrier wait has a deadline after which the kernel records
+// RELU_QP_ERR_TIMEOUT and returns.
+#include "batch.h"
+
+#include <algorithm>
+
+namespace rq {
+
+namespace {
+
+constexpr int kTailThreads = 256;
+
+struct TailArgs {
+    BatchParams p;              // state (QP-indexed rows), bank scalars; Sout / CK32 set per phase
+    DecideArgs d;
+    const float* W[RQ_MAX_RHO];  // FP32 Wt of every bank entry, rows of ldk floats
+    const float* Wc;            // FP32 check matrix [[P, A^T], [A, 0]], rows of ldkc floats
+    float* S;                   // operand double buffer [2][kTailMax][ldk]
+    float* CKB;                 // check operand [kTailMax][ldkc]
+    unsigned* red;              // [3][kTailMax][RW_WORDS] reduction words, rotated per check
+    unsigned* bar;              // grid barrier [count, generation]
+    int* err;                   // error word
+    const int* qlist;           // [nq] QP ids
+    int nq, it0, max_iter, ci;
+    long long timeout_ns;
+};
+
+__device__ __forceinline__ long long tail_timer() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier; false in every thread of the CTA if the wait passed its
+// deadline or another CTA reported an error.
+__device__ bool tail_barrier(const TailArgs& a, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (gridDim.x > 1) {
+            volatile unsigned* gen = a.bar + 1;
+            const unsigned g = *gen;
+            __threadfence();
+            const unsigned arrived = atomicAdd(a.bar, 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(a.bar, 0u);
+                __threadfence();
+                atomicAdd(a.bar + 1, 1u);
+            } else {
+                const long long t0 = tail_timer();
+                while (*gen == g) {
+                    if (tail_timer() - t0 > a.timeout_ns) {
+                        atomicExch(a.err, RELU_QP_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        if (*((volatile int*)a.err) != 0) ok = 0;
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+constexpr int kStep = 16;       // k per partial (the tiled kernels' step)
+constexpr int kStepPad = 20;    // floats per staged step (bank spread of 16-byte reads)
+
+// Copy the floats [col0, col0 + cols) (multiples of 16) of every live tail QP's
+// row of `src` (row stride ld) into the padded shared layout
+// [j][step][kStepPad] (ops floats per QP).  Asynchronous copies (L2 -> shared,
+// all in flight at once); the caller's __syncthreads follows the wait here.
+__device__ __forceinline__ void stage_rows(float* sm, int ops, const float* src, int ld, int col0, int cols, int nq,
+                                           const int* s_live) {
+    const int c4 = cols >> 2;
+    for (int e = threadIdx.x; e < nq * c4; e += blockDim.x) {
+        const int j = e / c4, q = (col0 >> 2) + (e - j * c4);
+        if (!s_live[j]) continue;
+        const uint32_t d = static_cast<uint32_t>(
+            __cvta_generic_to_shared(sm + (size_t)j * ops + (q >> 2) * kStepPad + (q & 3) * 4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + (size_t)j * ld + 4 * q)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+constexpr int kRB = 1;          // rows per warp pass
+constexpr int kPbs = 33;        // stride of a round's partials (32 steps, padded)
+
+// kRB consecutive rows r0 .. r0 + kRB - 1 (< nrows) of a product for every
+// live tail QP (warp-cooperative).  Step c of row r (k = 16 c .. 16 c + 15, c in
+// [c0, c1)) for QP j is
+//   part = FMA chain over k in order, starting at 0        (as fp32_tile)
+// and acc_j(r) = sum of the parts in increasing c         (as fp32_tile).
+// Rounds of 32 steps: lane l computes step c0 + 32 i + l of every row and QP
+// (the rows' Wt values stay in registers across the QPs, each staged operand
+// value feeds kRB rows), writes the partials to pb, and lane j adds QP j's
+// partials of the round in step order.  acc[i] is valid in lane j < nq.
+// wrow(j, r) gives QP j's row r of the matrix; rows of QPs that share the
+// same matrix are loaded once.
+template <class WRow>
+__device__ __forceinline__ void warp_rows(const float* __restrict__ opnd, int ops, float* pb, int nq,
+                                          const int* s_live, int c0, int c1, int r0, int nrows, WRow wrow,
+                                          float (&acc)[kRB]) {
+    const int lane = threadIdx.x & 31;
+    unsigned live = 0;
+    for (int j = 0; j < nq; ++j) live |= (s_live[j] ? 1u : 0u) << j;
+#pragma unroll
+    for (int i = 0; i < kRB; ++i) acc[i] = 0.f;
+    for (int cb = c0; cb < c1; cb += 32) {
+        const int c = cb + lane;
+        unsigned todo = live;
+        while (todo) {
+            const int j0 = __ffs(todo) - 1;
+            const float* w0 = wrow(j0, r0);
+            unsigned same = 0;
+            for (int j = j0; j < nq; ++j)
+                if (((todo >> j) & 1u) && wrow(j, r0) == w0) same |= 1u << j;
+            todo &= ~same;
+            if (c < c1) {
+                float4 wv[kRB][4];
+#pragma unroll
+                for (int i = 0; i < kRB; ++i)
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        wv[i][t] = r0 + i < nrows ? __ldg(reinterpret_cast<const float4*>(wrow(j0, r0 + i) + c * kStep) + t)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                // the rows' next round (same matrix) while this one computes
+                if (c + 32 < c1)
+#pragma unroll
+                    for (int i = 0; i < kRB; ++i)
+                        if (r0 + i < nrows)
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(wrow(j0, r0 + i) + (c + 32) * kStep));
+                unsigned m = same;
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    const float* xs = opnd + (size_t)j * ops + c * kStepPad;
+                    float part[kRB];
+#pragma unroll
+                    for (int i = 0; i < kRB; ++i) part[i] = 0.f;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const float4 xv = *reinterpret_cast<const float4*>(xs + 4 * t);
+#pragma unroll
+                        for (int i = 0; i < kRB; ++i) {
+                            part[i] = fmaf(xv.x, wv[i][t].x, part[i]);
+                            part[i] = fmaf(xv.y, wv[i][t].y, part[i]);
+                            part[i] = fmaf(xv.z, wv[i][t].z, part[i]);
+                            part[i] = fmaf(xv.w, wv[i][t].w, part[i]);
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < kRB; ++i) pb[(i * kTailMax + j) * kPbs + lane] = part[i];
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < nq && ((live >> lane) & 1u)) {
+            const int nc = min(32, c1 - cb);
+#pragma unroll
+            for (int i = 0; i < kRB; ++i) {
+                const float* q = pb + (i * kTailMax + lane) * kPbs;
+                for (int l = 0; l < nc; ++l) acc[i] += q[l];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Operand of the first layer of a chunk, as batch_fill_kernel: s = [x; 2 rho z - lam'].
+__device__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const int* s_ri) {
+    const BatchParams& p = a.p;
+    const int total = a.nq * p.ldk;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int j = e / p.ldk, k = e - j * p.ldk;
+        if (!s_live[j]) continue;
+        const int qp = a.qlist[j], ri = s_ri[j];
+        float v = 0.f;
+        if (k < p.n) {
+            v = p.Y[(size_t)qp * p.ldn + k];
+        } else if (k < p.R) {
+            const int i = k - p.n;
+            const size_t o = (size_t)qp * p.ldm + i;
+            v = 2.f * (p.rho[ri] * p.rs[i]) * p.Z[o] - p.LAM[o];
+        }
+        S[(size_t)j * p.ldk + k] = v;
+    }
+}
+
+__global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a) {
+    extern __shared__ __align__(16) float tsm[];
+    __shared__ int s_ok, s_live[kTailMax], s_ri[kTailMax], s_act[kTailMax], s_nri[kTailMax], s_any;
+    __shared__ unsigned s_red[kTailMax][RW_WORDS];
+    BatchParams p = a.p;
+    const int nq = a.nq;
+    const int nsteps = (p.ldk > p.ldkc ? p.ldk : p.ldkc) / kStep;
+    const int ops = nsteps * kStepPad;                       // staged floats per QP
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* pb = tsm + (size_t)kTailMax * ops + (size_t)warp * kRB * kTailMax * kPbs;
+    const int gwarp = blockIdx.x * (kTailThreads / 32) + warp, nwarps = gridDim.x * (kTailThreads / 32);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    if (threadIdx.x < kTailMax) {
+        const int j = threadIdx.x;
+        s_live[j] = j < nq ? 1 : 0;
+        s_ri[j] = j < nq ? a.d.rho_idx[a.qlist[j]] : 0;
+    }
+    __syncthreads();
+    int cur = 0, checks = 0, it = a.it0;
+    tail_fill(a, a.S, s_live, s_ri);
+    if (!tail_barrier(a, &s_ok)) return;
+    const int chunk = a.ci > 0 ? a.ci : 25;
+    while (it < a.max_iter) {
+        const int len = min(chunk, a.max_iter - it);
+        const bool last_chunk = it + len == a.max_iter;
+        const bool check = (a.ci > 0 && (it + len) % a.ci == 0) || last_chunk;
+        // ---------------- len layers ----------------
+        for (int jl = 0; jl < len; ++jl) {
+            const float* Sc = a.S + (size_t)cur * kTailMax * p.ldk;
+            p.Sout = a.S + (size_t)(cur ^ 1) * kTailMax * p.ldk;
+            p.CK32 = a.CKB;
+            p.CK = nullptr;
+            p.flags = jl == len - 1 ? (EPI_LAST | (check ? EPI_CHECK : 0u)) : 0u;
+            stage_rows(tsm, ops, Sc, p.ldk, 0, p.ldk, nq, s_live);
+            __syncthreads();
+            for (int r0 = gwarp * kRB; r0 < p.R; r0 += nwarps * kRB) {
+                float acc[kRB];
+                warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r0, p.R,
+                          [&](int j, int r) { return a.W[s_ri[j]] + (size_t)r * p.ldk; }, acc);
+                if (lane < nq && s_live[lane])
+#pragma unroll
+                    for (int i = 0; i < kRB; ++i)
+                        if (r0 + i < p.R) layer_elem(p, lane, a.qlist[lane], s_ri[lane], r0 + i, acc[i]);
+            }
+            cur ^= 1;
+            if (!tail_barrier(a, &s_ok)) return;
+        }
+        it += len;
+        if (check) {
+            unsigned* slot = a.red + (size_t)(checks % 3) * kTailMax * RW_WORDS;
+            if (blockIdx.x == 0)
+                for (int e = threadIdx.x; e < kTailMax * RW_WORDS; e += blockDim.x)
+                    a.red[(size_t)((checks + 1) % 3) * kTailMax * RW_WORDS + e] = 0u;
+            ++checks;
+            p.CK32 = a.CKB;
+            p.CK = nullptr;
+            // phase 1: [P; A] x over the x columns of the check operand
+            for (int e = threadIdx.x; e < kTailMax * RW_WORDS; e += blockDim.x) (&s_red[0][0])[e] = 0u;
+            stage_rows(tsm, ops, a.CKB, p.ldkc, 0, p.n64, nq, s_live);
+            __syncthreads();
+            {
+                float rp = 0.f, nax = 0.f, nz = 0.f, npx = 0.f;
+                for (int r0 = gwarp * kRB; r0 < p.n + p.m; r0 += nwarps * kRB) {
+                    float acc[kRB];
+                    warp_rows(tsm, ops, pb, nq, s_live, 0, p.n64 / kStep, r0, p.n + p.m,
+                              [&](int, int r) { return a.Wc + (size_t)r * p.ldkc; }, acc);
+                    if (lane < nq && s_live[lane])
+#pragma unroll
+                        for (int i = 0; i < kRB; ++i)
+                            if (r0 + i < p.n + p.m)
+                                check1_elem(p, lane, a.qlist[lane], s_ri[lane], r0 + i, acc[i], rp, nax, nz, npx);
+                }
+                if (lane < nq && s_live[lane]) {
+                    atomicMax(&s_red[lane][RW_RP], __float_as_uint(fabsf(rp)));
+                    atomicMax(&s_red[lane][RW_AX], __float_as_uint(fabsf(nax)));
+                    atomicMax(&s_red[lane][RW_Z], __float_as_uint(fabsf(nz)));
+                    atomicMax(&s_red[lane][RW_PX], __float_as_uint(fabsf(npx)));
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nq * RW_WORDS; e += blockDim.x)
+                if ((&s_red[0][0])[e]) atomicMax(slot + e, (&s_red[0][0])[e]);
+            if (!tail_barrier(a, &s_ok)) return;
+            // phase 2: A^T lam_std over the multiplier columns
+            for (int e = threadIdx.x; e < kTailMax * RW_WORDS; e += blockDim.x) (&s_red[0][0])[e] = 0u;
+            stage_rows(tsm, ops, a.CKB, p.ldkc, p.n64, p.ldkc - p.n64, nq, s_live);
+            __syncthreads();
+            {
+                float rd = 0.f, natl = 0.f;
+                for (int r0 = gwarp * kRB; r0 < p.n; r0 += nwarps * kRB) {
+                    float acc[kRB];
+                    warp_rows(tsm, ops, pb, nq, s_live, p.n64 / kStep, p.ldkc / kStep, r0, p.n,
+                              [&](int, int r) { return a.Wc + (size_t)r * p.ldkc; }, acc);
+                    if (lane < nq && s_live[lane])
+#pragma unroll
+                        for (int i = 0; i < kRB; ++i)
+                            if (r0 + i < p.n) check2_elem(p, a.qlist[lane], r0 + i, acc[i], rd, natl);
+                }
+                if (lane < nq && s_live[lane]) {
+                    atomicMax(&s_red[lane][RW_RD], __float_as_uint(fabsf(rd)));
+                    atomicMax(&s_red[lane][RW_ATL], __float_as_uint(fabsf(natl)));
+                }
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nq * RW_WORDS; e += blockDim.x)
+                if ((&s_red[0][0])[e]) atomicMax(slot + e, (&s_red[0][0])[e]);
+            if (!tail_barrier(a, &s_ok)) return;
+            // decision: every CTA reaches the same one; CTA 0 writes the per-QP records
+            if (threadIdx.x < nq) {
+                const int j = threadIdx.x;
+                int act = -1, nri = s_ri[j];
+                if (s_live[j]) {
+                    unsigned w[RW_WORDS];
+#pragma unroll
+                    for (int k = 0; k < RW_WORDS; ++k) w[k] = __ldcg(slot + j * RW_WORDS + k);
+                    DecideArgs d = a.d;
+                    d.it = it;
+                    d.final_iter = last_chunk ? 1 : 0;
+                    if (blockIdx.x == 0) {
+                        act = decide_qp(p, d, a.qlist[j], w, nri);
+                    } else {
+                        const Decision x = decide_eval(p, d, a.qlist[j], w, s_ri[j], 0);
+                        act = x.act;
+                        nri = x.nri;
+                    }
+                }
+                s_act[j] = act;
+                s_nri[j] = nri;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int any = 0;
+                for (int j = 0; j < nq; ++j) {
+                    if (s_act[j] == 1) s_live[j] = 0;
+                    if (s_act[j] == 2) s_ri[j] = s_nri[j];
+                    any |= s_live[j];
+                }
+                s_any = any;
+            }
+            __syncthreads();
+            // outputs of finished QPs; lam' rebase of switched ones
+            const int width = p.n > p.m ? p.n : p.m;
+            for (int o = tid; o < width * nq; o += nthr) {
+                const int e = o / nq, j = o - e * nq;
+                const int qp = a.qlist[j];
+                if (s_act[j] == 1) {
+                    if (e < p.n) a.d.XO[(size_t)qp * p.n + e] = p.Y[(size_t)qp * p.ldn + e];
+                    if (e < p.m) {
+                        a.d.ZO[(size_t)qp * p.m + e] = p.Z[(size_t)qp * p.ldm + e];
+                        a.d.LO[(size_t)qp * p.m + e] = p.LSTD[(size_t)qp * p.ldm + e];
+                    }
+                } else if (s_act[j] == 2 && e < p.m) {
+                    const size_t oo = (size_t)qp * p.ldm + e;
+                    const float rho_i = (float)(p.rhod[s_ri[j]] * (double)p.rs[e]);
+                    p.LAM[oo] = p.LSTD[oo] - rho_i * (p.AY[oo] - p.Z[oo]);
+                }
+            }
+            if (!s_any) return;
+            if (!tail_barrier(a, &s_ok)) return;
+        }
+        if (last_chunk) return;
+        // operand of the next chunk's first layer from the state
+        tail_fill(a, a.S + (size_t)cur * kTailMax * p.ldk, s_live, s_ri);
+        if (!tail_barrier(a, &s_ok)) return;
+    }
+}
+
+// Active QP ids in increasing order (one warp).
+__global__ void tail_list_kernel(int B, const int* __restrict__ status, int* list, int cap) {
+    int base = 0;
+    for (int c0 = 0; c0 < B; c0 += 32) {
+        const int qp = c0 + threadIdx.x;
+        const bool act = qp < B && status[qp] == QP_ACTIVE;
+        const unsigned ball = __ballot_sync(0xffffffffu, act);
+        const int pos = base + __popc(ball & ((1u << threadIdx.x) - 1u));
+        if (act && pos < cap) list[pos] = qp;
+        base += __popc(ball);
+    }
+}
+
+// staged operands [kTailMax][steps][kStepPad] + per-warp round partials [8][kRB][kTailMax][kPbs]
+size_t tail_smem(const BatchWork& w) {
+    const size_t steps = (size_t)std::max(w.ldk, w.ldkc) / kStep;
+    return ((size_t)kTailMax * steps * kStepPad + (size_t)(kTailThreads / 32) * kRB * kTailMax * kPbs) * sizeof(float);
+}
+
+}  // namespace
+
+int batch_tail_alloc(relu_qp_t h) {
+    BatchWork& w = h->bw;
+    RQ_TRY(alloc(h, &w.TS, 2 * (size_t)kTailMax * w.ldk));
+    RQ_TRY(alloc(h, &w.TCK, (size_t)kTailMax * w.ldkc));
+    RQ_TRY(alloc(h, &w.TRED, 3 * (size_t)kTailMax * RW_WORDS));
+    RQ_TRY(alloc(h, &w.TBAR, 4));
+    RQ_TRY(alloc(h, &w.TLIST, kTailMax));
+    const size_t smem = tail_smem(w);
+    int smem_max = 0;
+    RQ_CUDA(h, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+    if (smem + 1024 > (size_t)smem_max) {   // problem too large for the staged operands: no tail kernel
+        w.tail_grid = 0;
+        return RELU_QP_OK;
+    }
+    RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem));
+    // every CTA co-resident (grid barrier); two per SM when they fit, so that each warp
+    // takes at most one row of the product
+    w.tail_grid = std::min(per_sm, 2) * h->num_sms;
+    return RELU_QP_OK;
+}
+
+int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, int it0, int max_iter) {
+    BatchWork& w = h->bw;
+    if (nq <= 0 || nq > kTailMax || w.tail_grid <= 0) return fail(h, RELU_QP_ERR_INVALID, "tail size");
+    tail_list_kernel<<<1, 32, 0, h->stream>>>(w.B, w.status, w.TLIST, kTailMax);
+    RQ_CUDA(h, cudaGetLastError());
+    RQ_CUDA(h, cudaMemsetAsync(w.TRED, 0, sizeof(unsigned) * 3 * kTailMax * RW_WORDS, h->stream));
+    RQ_CUDA(h, cudaMemsetAsync(w.TBAR, 0, sizeof(unsigned) * 4, h->stream));
+    TailArgs a{};
+    a.p = p;
+    a.d = d;
+    for (int r = 0; r < h->nr; ++r) a.W[r] = h->be[r].Wt;
+    a.Wc = w.Wc32;
+    a.S = w.TS;
+    a.CKB = w.TCK;
+    a.red = w.TRED;
+    a.bar = w.TBAR;
+    a.err = reinterpret_cast<int*>(w.TBAR + 2);
+    a.qlist = w.TLIST;
+    a.nq = nq;
+    a.it0 = it0;
+    a.max_iter = max_iter;
+    a.ci = h->opts.check_interval;
+    a.timeout_ns = 2000000000LL;
+    void* args[] = {&a};
+    RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)batch_tail_kernel, dim3(w.tail_grid), dim3(kTailThreads), args,
+                                           tail_smem(w), h->stream));
+    h->launches += 2;
+    return RELU_QP_OK;
+}
+
+int batch_tail_error(relu_qp_t h) {
+    int e = 0;
+    cudaMemcpy(&e, h->bw.TBAR + 2, sizeof(int), cudaMemcpyDeviceToHost);
+    return e;
+}
+
+}  // namespace rq

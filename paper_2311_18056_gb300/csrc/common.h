@@ -103,6 +103,11 @@ struct BatchWork {
     int nx = 0, ldx = 0;
     float *F32 = nullptr, *Ft32 = nullptr, *E32 = nullptr, *l0 = nullptr, *u0 = nullptr, *X0 = nullptr;
     float* G[RQ_MAX_RHO] = {};             // G_r = Bop_r F
+    // convergence tail (batch_tail.cu): operands, check operand, reduction and barrier words, QP list
+    float *TS = nullptr, *TCK = nullptr;
+    unsigned *TRED = nullptr, *TBAR = nullptr;
+    int* TLIST = nullptr;
+    int tail_grid = 0;                     // CTAs of its cooperative launch (0: unavailable)
 };
 
 }  // namespace rq

@@ -148,7 +148,12 @@ def test_converged_humanoid_sampled(rq, prec):
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
 def test_alone_equals_in_batch(rq, prec):
-    """Batch invariance of full solves (checks, rho switches, regrouping)."""
+    """Batch invariance of full solves (checks, rho switches, regrouping, the
+    convergence tail).  FP32: the same layers and the same iterates to rounding
+    (the tail kernel repeats the tiled kernels' arithmetic).  BF16 split: a QP
+    alone reaches the FP32 tail kernel after its first check, inside the batch
+    only once at most 8 QPs are left, so the two solves agree to the stated
+    tolerance of converged solutions: both solved, x within 1e-3 of each other."""
     pq, X0, Q, L, U = mpc_batch("family0", 300)
     s = rq.ReluQP(pq.P, pq.A, L[0], U[0], q=Q[0], sigma=SIGMA, rho_bank=BANK, max_batch=300, precision=prec)
     s.update_batch(Q, L, U)
@@ -156,8 +161,12 @@ def test_alone_equals_in_batch(rq, prec):
     for b in [0, 150, 299]:
         s.update_batch(Q[b:b + 1], L[b:b + 1], U[b:b + 1])
         one = s.solve_batch(eps_abs=1e-3)
-        assert one["iters"][0] == full["iters"][b]
-        assert np.max(np.abs(one["x"][0] - full["x"][b])) <= 1e-6 * (1 + np.max(np.abs(one["x"][0])))
+        if prec == 0:
+            assert one["iters"][0] == full["iters"][b]
+            assert np.max(np.abs(one["x"][0] - full["x"][b])) <= 1e-6 * (1 + np.max(np.abs(one["x"][0])))
+        else:
+            assert one["status"][0] == full["status"][b] == rq.SOLVED
+            assert np.max(np.abs(one["x"][0] - full["x"][b])) <= 1e-3
     s.close()
 
 
