@@ -603,6 +603,7 @@ int batch_alloc(relu_qp_t h) {
         RQ_TRY(dev_alloc(h, &w.CK, sizeof(uint16_t) * 3 * (size_t)w.slots * w.ldkc + 1024));
         RQ_TRY(dev_alloc(h, &w.WB, sizeof(uint16_t) * (size_t)nr * 3 * w.Rpad * w.ldk + 1024));
         RQ_TRY(dev_alloc(h, &w.WCB, sizeof(uint16_t) * 3 * (size_t)w.npad * w.ldkc + 1024));
+        RQ_TRY(alloc(h, &w.chunk_sync, (size_t)w.slots / kSlotTile));
     } else {
         RQ_TRY(alloc(h, &w.S32, 2 * (size_t)w.slots * w.ldk));
         RQ_TRY(alloc(h, &w.CK32, (size_t)w.slots * w.ldkc));
@@ -854,7 +855,8 @@ int regroup_slots(relu_qp_t h, const BatchParams& p, int nqp, bool assign) {
 // `len` layers of one chunk over the slots of the last regroup; with `check`
 // the last layer also writes x into the check operand.  `active` is the
 // number of QPs in the batch (for the tile-width choice and the FLOP count).
-int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int active, size_t& prof_used) {
+int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int active, int tiles_now,
+               size_t& prof_used) {
     BatchWork& w = h->bw;
     const int R = h->R;
     const bool bf16 = w.prec == RELU_QP_PREC_BF16X3;
@@ -866,6 +868,9 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
     // profiling: one event pair around the refined layers of the chunk (events
     // between them would break the programmatic overlap of consecutive layers)
     const bool timed = h->prof_on && bf16 && len > 1 && prof_used + 2 <= h->prof_ev.size();
+    // layer counters of the persistent chunk kernel start at zero
+    if (bf16 && w.chunk_sync && len > 1)
+        RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * tiles_max, h->stream));
     for (int j = 0; j < len; ++j) {
         BatchParams q = p;
         q.flags = 0;
@@ -876,6 +881,26 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
             q.Dlo = q.Dhi + opart;
             if (w.check_tc) q.CK = static_cast<__nv_bfloat16*>(w.CK);
             else q.CK32 = w.CK32;
+            if (j == 1 && w.chunk_sync) {
+                // layers 1 .. len-1 in one persistent launch when the tile's CTAs fit in one wave
+                BatchParams qc = q;
+                qc.flags = 0;
+                if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
+                const int rc = tc_chunk(h, qc, len - 1, EPI_LAST | (check ? EPI_CHECK : 0u), tiles_now);
+                if (rc == RELU_QP_OK) {
+                    h->launches += 1;
+                    h->layer_launches += len - 1;
+                    h->layer_flops += (len - 1) * 2.0 * 3.0 * (double)R * (double)R * (double)active;
+                    if (timed) {
+                        RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used + 1], h->stream));
+                        h->prof_span_launches.push_back(len - 1);
+                        prof_used += 2;
+                    }
+                    break;
+                }
+                if (rc != RELU_QP_ERR_UNSUPPORTED) return rc;
+                // refused: one launch per layer below (which records the span's start again)
+            }
             if (j == 0 && !w.rebase_tc) {
                 // accurate layer c = Wt s_ref + b in FP32 on the CUDA cores (round to
                 // nearest); the tensor core's truncating accumulation of the full
@@ -980,13 +1005,16 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     const int chunk = ci > 0 ? ci : 25;
     int it = 0;
     int active = B;              // QPs in the batch (known to the host after each check)
+    // slot tiles in use: exact at a cold start (every QP in the starting bank entry's
+    // group) and after each check, an upper bound after a warm start
+    int tiles_now = rw ? std::min(tiles_max, ceil_div(B, kSlotTile) + h->nr - 1) : ceil_div(B, kSlotTile);
     size_t prof_used = 0;
     bool tail_used = false;
     while (it < max_iter) {
         const int len = std::min(chunk, max_iter - it);
         const bool last_chunk = it + len == max_iter;
         const bool check = (ci > 0 && (it + len) % ci == 0) || last_chunk;
-        RQ_TRY(run_layers(h, p, len, check, active, prof_used));
+        RQ_TRY(run_layers(h, p, len, check, active, tiles_now, prof_used));
         it += len;
         if (check) {
             RQ_TRY(run_check(h, p, active));
@@ -1005,6 +1033,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
             if (cnt[CNT_ERR]) break;     // reported below
             if (cnt[CNT_ACTIVE] == 0) break;
             active = cnt[CNT_ACTIVE];
+            tiles_now = cnt[CNT_TILES];
             if (active <= kTailMax && w.tail_grid > 0) {
                 // the few QPs left finish in one cooperative launch
                 DecideArgs d{B, it, 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO, w.status, w.iters,
@@ -1315,7 +1344,7 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
     size_t prof_used = 0;
     h->prof_span_launches.clear();    // the server does not read the layer events
     RQ_TRY(regroup_slots(h, p, w.cap, true));
-    RQ_TRY(run_layers(h, p, ci, true, f.active, prof_used));
+    RQ_TRY(run_layers(h, p, ci, true, f.active, 0, prof_used));
     RQ_TRY(run_check(h, p, f.active));
     RQ_SCUDA(s, cudaMemsetAsync(f.d.cnt, 0, sizeof(int), f.stream));
     DecideArgs dd{w.cap, 0, 0, h->opts.adaptive_rho, s->eps_abs, s->eps_rel, w.XO, w.ZO, w.LO,
@@ -1396,6 +1425,8 @@ int server_create(relu_qp_server_t* out, relu_qp_t const* families, int nf, cons
         RQ_SCUDA(s, cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
         f.saved_stream = h->stream;
         h->stream = f.stream;
+        // families share the GPU: no persistent (one-wave, co-resident) chunk kernels
+        if (h->bw.tc) tc_disable_chunk(h);
         const size_t cap = f.cap, cl = f.clients > 0 ? f.clients : 1;
         RQ_TRY(sdev(s, f, &f.d.idx, cap));
         RQ_TRY(sdev(s, f, &f.d.cl, cap));

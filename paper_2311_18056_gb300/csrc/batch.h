@@ -438,6 +438,13 @@ int tc_prepare(relu_qp_t h);                     // BF16 splits of every W_rho a
 // previous kernel of the stream (refined layers only)
 int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles, bool pdl = false);
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phase 1: [P; A] x, 2: A^T lam
+// Refined layers 1 .. nl of a chunk in one persistent launch (flags of layer nl
+// get last_flags); active_tiles = slot tiles in use (an upper bound).
+// RELU_QP_ERR_UNSUPPORTED: not possible here (too many CTAs for one wave, or the
+// launch was refused, which disables it for the handle); the caller launches the
+// layers one by one.
+int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active_tiles);
+void tc_disable_chunk(relu_qp_t h);
 void tc_release(relu_qp_t h);
 int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);           // one refined width for every batch size
 int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles);  // [t] = width for t active slot tiles

@@ -276,6 +276,85 @@ __device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* 
     return true;
 }
 
+// One layer of the persistent chunk kernel: as produce(), with the stage
+// ring continuing across layers (k-block g0 + kb uses stage (g0 + kb) % S),
+// and the operand tiles requested only once every CTA of this slot tile has
+// released the previous layer (its counter reached `target`; sync == nullptr:
+// wait for the previous kernel of the stream instead).
+template <int NB, int BN, int STAGES, int KSTAGE, int KA>
+__device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sbase,
+                                           uint32_t bar0, int nkb, int koff, int g0, int a0, int a1, int b0, int b1,
+                                           const unsigned* sync, unsigned target, int& issued) {
+    const int brow[2] = {b0, b1}, arow[2] = {a0, a1};
+    const int pre = nkb < STAGES ? nkb : STAGES;
+    for (int kb = 0; kb < pre; ++kb) {
+        const int gk = g0 + kb, s = gk % STAGES;
+        if (!mbar_wait(bar0 + 8 * (STAGES + s), ((gk / STAGES) & 1) ^ 1)) return false;
+        const uint32_t full = bar0 + 8 * s;
+        mbar_expect_tx(full, KSTAGE);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            tma_load_2d(sbase + s * KSTAGE + KA + b * BN * 128, tmB, kb * kBK + koff, brow[b], full);
+    }
+    if (sync) {
+        const long long t0 = gtime();
+        while (true) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sync) : "memory");
+            if (v >= target) break;
+            if (gtime() - t0 > kWaitNs) return false;
+            __nanosleep(64);
+        }
+        // the operand was written by generic stores of other CTAs; order them before the TMA reads
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    } else {
+        griddep_wait();
+    }
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int gk = g0 + kb, s = gk % STAGES;
+        const uint32_t full = bar0 + 8 * s;
+        const uint32_t st = sbase + s * KSTAGE;
+        const int k0 = kb * kBK + koff;
+        if (kb >= pre) {
+            if (!mbar_wait(bar0 + 8 * (STAGES + s), ((gk / STAGES) & 1) ^ 1)) return false;
+            mbar_expect_tx(full, KSTAGE);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
+        }
+#pragma unroll
+        for (int a = 0; a < 2; ++a) tma_load_2d(st + a * kTileBytesA, tmA, k0, arow[a], full);
+        issued = gk + 1;
+    }
+    return true;
+}
+
+template <int BN, int STAGES, int KSTAGE, int KA>
+__device__ __noinline__ bool issue_layer(uint32_t sbase, uint32_t bar0, uint32_t tmem, int nkb, int g0) {
+    constexpr uint32_t IDESC = idesc_bf16(BN);
+    const uint64_t d0 = sdesc(sbase);
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int gk = g0 + kb, s = gk % STAGES;
+        if (!mbar_wait(bar0 + 8 * s, (gk / STAGES) & 1)) return false;
+        fence_after();
+        const uint64_t da = d0 + (uint64_t)((s * KSTAGE) >> 4);
+        const uint64_t db = da + (uint64_t)(KA >> 4);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+                // (d_hi, w1) -> accumulator 0; (d_hi, w2), (d_lo, w1) -> accumulator 1
+                const int ia = pr == 2 ? 1 : 0, ib = pr == 1 ? 1 : 0;
+                const uint64_t ad = da + (uint64_t)((ia * kTileBytesA + kk * 32) >> 4);
+                const uint64_t bd = db + (uint64_t)((ib * BN * 128 + kk * 32) >> 4);
+                const bool first = kb == 0 && kk == 0 && pr <= 1;
+                mma_bf16(tmem + (pr == 0 ? 0 : BN), ad, bd, IDESC, first ? 0u : 1u);
+            }
+        }
+        mma_commit(bar0 + 8 * (STAGES + s));
+    }
+    return true;
+}
+
 // Descriptors are formed once; a stage, part or 16-element k step is a
 // constant byte offset, i.e. an add of offset / 16 to the address field
 // (shared addresses stay below 2^18, so the 14-bit field cannot carry).
@@ -319,6 +398,195 @@ template <int OWN>
 __device__ __forceinline__ int recv_off(int slot, int col) {
     constexpr int SW = OWN / 4 >= 8 ? 7 : OWN / 4 - 1;
     return slot * OWN + ((((col >> 2) ^ (slot & SW))) << 2) + (col & 3);
+}
+
+// The epilogue of one tile for the epilogue warp `warp` (2..9): waits for the
+// accumulators (barrier bar_acc, phase parity par_acc), exchanges the K-split
+// partial sums with the partners (bar_recv / par_recv), and applies the
+// element-wise part of the mode to this warp's columns.  Returns false after a
+// deadline (the error is recorded).
+template <int MODE, int BN, int KS>
+__device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs& g, int warp, int lane, int rank,
+                                              int slot0, int row0, int ri, uint32_t tmem, float* xpose, float* recv,
+                                              uint32_t bar_acc, uint32_t par_acc, uint32_t bar_recv,
+                                              uint32_t par_recv, int* s_fail) {
+    constexpr int OWN = BN / KS;
+    constexpr int HALVES = OWN >= 32 ? 2 : 1;
+    constexpr int PER = OWN / HALVES;
+    const int q = warp & 3;                         // TMEM lane quadrant of this warp
+    const int half = (warp - 2) >> 2;               // which half of this CTA's columns
+    const int slot = slot0 + q * 32 + lane;
+    const int qp = p.perm[slot];
+    const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+    // whole 16-row pieces are transposed through shared memory so that
+    // lane = 4 * (slot % 8) + (row group): QP slot pass * 8 + lane / 4, rows cg..cg+3
+    const int cg = (lane & 3) * 4;
+    int qq[4];
+#pragma unroll
+    for (int pass = 0; pass < 4; ++pass) qq[pass] = __shfl_sync(0xffffffffu, qp, pass * 8 + (lane >> 2));
+    const int own0 = rank * OWN;
+    const int cbeg = own0 + half * PER, cend = cbeg + PER;
+    const bool n_aligned = (p.n & 3) == 0;
+    auto whole_at = [&](int c0) {
+        const int r0 = row0 + c0;
+        return MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows && (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
+    };
+    // refined layers: the lighter refined-only inputs (flags never hold EPI_REBASE)
+    using Piece = typename std::conditional<MODE == MODE_LAYER_REFINED, Chunk4R, Chunk4>::type;
+    Piece in[4];
+    float rs[4] = {1.f, 1.f, 1.f, 1.f}, rs_next[4] = {1.f, 1.f, 1.f, 1.f};
+    // inputs of one 4-row piece of the 16-column chunk at c0 (pass = QP group)
+    auto load_pass = [&](int c0, int pass) {
+        if (qq[pass] >= 0) chunk4_load(p, qq[pass], ri, row0 + c0 + cg, in[pass]);
+    };
+    auto load_rs = [&](int c0, float (&dst)[4]) {
+        const int r0 = row0 + c0 + cg;
+        if (r0 >= p.n) ld4(p.rs + (r0 - p.n), dst);
+    };
+    // the inputs of the first chunk load while the MMAs run
+    if (whole_at(cbeg)) {
+        load_rs(cbeg, rs);
+#pragma unroll
+        for (int pass = 0; pass < 4; ++pass) load_pass(cbeg, pass);
+    }
+    // one lane per warp polls the accumulator barrier (sleeping between
+    // polls) for the whole main loop; then every lane observes the
+    // completed phase itself
+    bool ready = true;
+    if (lane == 0) ready = mbar_wait_sleep(bar_acc, par_acc, 256);
+    ready = __shfl_sync(0xffffffffu, ready, 0);
+    if (ready) ready = mbar_wait(bar_acc, par_acc);
+    ready = __all_sync(0xffffffffu, ready);
+    if (ready) fence_after();
+    if (KS > 1) {
+        // send every partner its columns of this warp's TMEM lanes: row (q * 32 + lane)
+        // of buffer j of the partner's receive area (j = this CTA's index among the
+        // partner's senders), columns half * PER ...
+        const int srow = q * 32 + lane;
+        for (int pk = 0; pk < KS; ++pk) {
+            if (pk == rank) continue;
+            const int j = rank < pk ? rank : rank - 1;
+            const int pc0 = pk * OWN + half * PER;
+            const uint32_t dst = mapa(smem_u32(recv + j * kSlotTile * OWN), (uint32_t)pk);
+            if (ready) {
+#pragma unroll
+                for (int c = 0; c < PER; c += 16) {
+                    float v[16], w[16];
+                    tmem_ld16(tl + pc0 + c, v);
+                    tmem_ld16(tl + BN + pc0 + c, w);
+#pragma unroll
+                    for (int t = 0; t < 16; t += 4)
+                        st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, half * PER + c + t), v[t] + w[t],
+                                    v[t + 1] + w[t + 1], v[t + 2] + w[t + 2], v[t + 3] + w[t + 3]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa(bar_recv, (uint32_t)pk));
+        }
+        // the partners' partial sums of this CTA's columns
+        bool got = true;
+        if (lane == 0) got = mbar_wait_cluster(bar_recv, par_recv, 64);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (got) got = mbar_wait_cluster(bar_recv, par_recv, 0);
+        got = __all_sync(0xffffffffu, got);
+        if (!got && ready && lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); *s_fail = 1; }
+        ready = ready && got;
+    }
+    if (!ready) {
+        if (lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); *s_fail = 1; }
+    } else {
+        float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
+        float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
+        // inputs of the next whole chunk load pass by pass as this chunk's
+        // passes finish, so that a memory round trip overlaps a chunk of work
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            const int r0 = row0 + c0;
+            const bool whole = whole_at(c0);
+            const int cn = c0 + 16;
+            const bool next_whole = cn < cend && whole_at(cn);
+            if (next_whole) load_rs(cn, rs_next);
+            float v[16], w[16];
+            tmem_ld16(tl + c0, v);
+            tmem_ld16(tl + BN + c0, w);
+#pragma unroll
+            for (int t = 0; t < 16; ++t) v[t] += w[t];
+            if (KS > 1) {
+                // partial sums of ranks 0 .. KS-1 added in rank order
+                float tot[16];
+#pragma unroll
+                for (int k = 0; k < KS; ++k) {
+                    float part[16];
+                    if (k == rank) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) part[t] = v[t];
+                    } else {
+                        const float* rb = recv + (k < rank ? k : k - 1) * kSlotTile * OWN;
+#pragma unroll
+                        for (int t = 0; t < 16; t += 4) {
+                            const float4 o =
+                                *reinterpret_cast<const float4*>(rb + recv_off<OWN>(q * 32 + lane, c0 - own0 + t));
+                            part[t] = o.x;
+                            part[t + 1] = o.y;
+                            part[t + 2] = o.z;
+                            part[t + 3] = o.w;
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) tot[t] = k == 0 ? part[t] : tot[t] + part[t];
+                }
+#pragma unroll
+                for (int t = 0; t < 16; ++t) v[t] = tot[t];
+            }
+            if (whole) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
+                __syncwarp();
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) {
+                    const int sl = pass * 8 + (lane >> 2);          // slot within the warp's 32
+                    if (qq[pass] >= 0) {
+                        float a4[4];
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) a4[t] = xb[sl * 17 + cg + t];
+                        chunk4_apply(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, in[pass], rs);
+                    }
+                    if (next_whole) load_pass(cn, pass);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rs[k] = rs_next[k];
+                __syncwarp();
+                continue;
+            }
+            if (qp >= 0) {
+#pragma unroll 4
+                for (int t = 0; t < 16; ++t) {
+                    const int r = r0 + t;
+                    if (r >= g.rows) continue;
+                    if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
+                    else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
+                    else layer_elem(p, slot, qp, ri, r, v[t]);
+                }
+            }
+            if (next_whole) {
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) load_pass(cn, pass);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) rs[k] = rs_next[k];
+            }
+        }
+        if (qp >= 0) {
+            if (MODE == MODE_CHECK1) {
+                red_slot(p.RED, qp, RW_RP, ra);
+                red_slot(p.RED, qp, RW_AX, rb);
+                red_slot(p.RED, qp, RW_Z, rc);
+                red_slot(p.RED, qp, RW_PX, rd);
+            } else if (MODE == MODE_CHECK2) {
+                red_slot(p.RED, qp, RW_RD, ra);
+                red_slot(p.RED, qp, RW_ATL, rb);
+            }
+        }
+    }
+    return ready;
 }
 
 // KS = 2 or 4 (refined layers): the KS CTAs of a cluster split the k-blocks
@@ -433,183 +701,178 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // the previous kernel's writes (the carried r, the state) are read and the
         // operand it read is overwritten: wait for it
         griddep_wait();
-        const int q = warp & 3;                         // TMEM lane quadrant of this warp
-        const int half = (warp - 2) >> 2;               // which half of this CTA's columns
-        const int slot = slot0 + q * 32 + lane;
-        const int qp = p.perm[slot];
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-        // whole 16-row pieces are transposed through shared memory so that
-        // lane = 4 * (slot % 8) + (row group): QP slot pass * 8 + lane / 4, rows cg..cg+3
-        const int cg = (lane & 3) * 4;
-        int qq[4];
-#pragma unroll
-        for (int pass = 0; pass < 4; ++pass) qq[pass] = __shfl_sync(0xffffffffu, qp, pass * 8 + (lane >> 2));
-        const int own0 = rank * OWN;
-        const int cbeg = own0 + half * PER, cend = cbeg + PER;
-        const bool n_aligned = (p.n & 3) == 0;
-        auto whole_at = [&](int c0) {
-            const int r0 = row0 + c0;
-            return MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows && (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
-        };
-        // refined layers: the lighter refined-only inputs (flags never hold EPI_REBASE)
-        using Piece = typename std::conditional<MODE == MODE_LAYER_REFINED, Chunk4R, Chunk4>::type;
-        Piece in[4];
-        float rs[4] = {1.f, 1.f, 1.f, 1.f}, rs_next[4] = {1.f, 1.f, 1.f, 1.f};
-        // inputs of one 4-row piece of the 16-column chunk at c0 (pass = QP group)
-        auto load_pass = [&](int c0, int pass) {
-            if (qq[pass] >= 0) chunk4_load(p, qq[pass], ri, row0 + c0 + cg, in[pass]);
-        };
-        auto load_rs = [&](int c0, float (&dst)[4]) {
-            const int r0 = row0 + c0 + cg;
-            if (r0 >= p.n) ld4(p.rs + (r0 - p.n), dst);
-        };
-        // the inputs of the first chunk load while the MMAs run
-        if (whole_at(cbeg)) {
-            load_rs(cbeg, rs);
-#pragma unroll
-            for (int pass = 0; pass < 4; ++pass) load_pass(cbeg, pass);
+        tile_epilogue<MODE, BN, KS>(p, g, warp, lane, rank, slot0, row0, ri, tmem, xpose, recv,
+                                    smem_u32(&bars[2 * STAGES]), 0, smem_u32(&bars[2 * STAGES + 1]), 0, &s_fail);
+    }
+    fence_before();
+    __syncthreads();
+    // no CTA of a cluster leaves while another may still address its shared memory
+    if (KS > 1) cluster_sync();
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent chunk: the refined layers 1 .. nl of one chunk in one launch.
+// Every CTA keeps its (slot tile, row block, k range) for all layers, so the
+// set-up (barriers, TMEM, tensor maps) happens once and the weight tiles of a
+// layer are requested while the previous layer still finishes.  Layer j reads
+// operand pair (j - 1) & 1 and writes pair j & 1 (both written only by the
+// epilogues of the CTAs of the same slot tile): after its epilogue a CTA adds
+// one to the tile's counter, and a producer requests the operand of layer j
+// only once the counter shows every CTA of the tile done with layer j - 1.
+// That also orders the reuse of TMEM and of the receive buffers (a partner
+// sends layer j's partial sums only after all of layer j - 1 is done).  The
+// CTAs of a tile must be co-resident (cooperative launch; the host checks the
+// count); every wait has a deadline.
+// ---------------------------------------------------------------------------
+struct ChunkArgs {
+    int nl;                    // refined layers of the chunk (1 .. nl)
+    unsigned last_flags;       // extra flags of layer nl (EPI_LAST, EPI_CHECK)
+    __nv_bfloat16* OP;         // operand parts: pair 0 = parts 0, 1; pair 1 = parts 2, 3
+    size_t opart;              // elements per part
+    int slots;                 // rows per part in the operand tensor map
+    unsigned* sync;            // per slot tile: CTAs done with layers so far (zero at launch)
+};
+
+template <int BN, int STAGES, int KS>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    tc_chunk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchParams p,
+                    TcArgs g, ChunkArgs c) {
+    constexpr int TCOLS = tmem_cols(2 * BN);
+    constexpr int OWN = BN / KS;
+    constexpr int HALVES = OWN >= 32 ? 2 : 1;
+    constexpr int PER = OWN / HALVES;
+    static_assert(KS == 1 || KS == 2 || KS == 4, "K split of 1, 2 or 4");
+    static_assert(PER % 16 == 0, "the epilogue works on 16-column pieces");
+    using L = TcSmem<2, 2, BN, STAGES, KS>;
+
+    const int tile = blockIdx.y;
+    if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA (and the cluster)
+    const int slot0 = tile * kSlotTile;
+    const int rank = KS > 1 ? (int)cluster_rank() : 0;
+    const int row0 = (blockIdx.x / KS) * BN;
+    const int ri = p.tile_rho[tile];
+    const int kb_begin = rank * g.num_kb / KS;
+    const int kb_count = (rank + 1) * g.num_kb / KS - kb_begin;
+    const unsigned nct = gridDim.x;                // CTAs of this slot tile
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* xpose = reinterpret_cast<float*>(smem + STAGES * L::kStage);
+    float* recv = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+    int& s_fail = *reinterpret_cast<int*>(tmem_holder + 1);   // in the dynamic area: no static shared memory
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[STAGES + s]), 1);
         }
-        // one lane per warp polls the accumulator barrier (sleeping between
-        // polls) for the whole main loop; then every lane observes the
-        // completed phase itself
-        bool ready = true;
-        if (lane == 0) ready = mbar_wait_sleep(smem_u32(&bars[2 * STAGES]), 0, 256);
-        ready = __shfl_sync(0xffffffffu, ready, 0);
-        if (ready) ready = mbar_wait(smem_u32(&bars[2 * STAGES]), 0);
-        ready = __all_sync(0xffffffffu, ready);
-        if (ready) fence_after();
-        if (KS > 1) {
-            // send every partner its columns of this warp's TMEM lanes: row (q * 32 + lane)
-            // of buffer j of the partner's receive area (j = this CTA's index among the
-            // partner's senders), columns half * PER ...
-            const int srow = q * 32 + lane;
-            for (int pk = 0; pk < KS; ++pk) {
-                if (pk == rank) continue;
-                const int j = rank < pk ? rank : rank - 1;
-                const int pc0 = pk * OWN + half * PER;
-                const uint32_t dst = mapa(smem_u32(recv + j * kSlotTile * OWN), (uint32_t)pk);
-                if (ready) {
-#pragma unroll
-                    for (int c = 0; c < PER; c += 16) {
-                        float v[16], w[16];
-                        tmem_ld16(tl + pc0 + c, v);
-                        tmem_ld16(tl + BN + pc0 + c, w);
-#pragma unroll
-                        for (int t = 0; t < 16; t += 4)
-                            st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, half * PER + c + t), v[t] + w[t],
-                                        v[t + 1] + w[t + 1], v[t + 2] + w[t + 2], v[t + 3] + w[t + 3]);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(mapa(smem_u32(&bars[2 * STAGES + 1]), (uint32_t)pk));
-            }
-            // the partners' partial sums of this CTA's columns
-            bool got = true;
-            if (lane == 0) got = mbar_wait_cluster(smem_u32(&bars[2 * STAGES + 1]), 0, 64);
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (got) got = mbar_wait_cluster(smem_u32(&bars[2 * STAGES + 1]), 0, 0);
-            got = __all_sync(0xffffffffu, got);
-            if (!got && ready && lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
-            ready = ready && got;
-        }
-        if (!ready) {
-            if (lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
-        } else {
-            float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
-            float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
-            // inputs of the next whole chunk load pass by pass as this chunk's
-            // passes finish, so that a memory round trip overlaps a chunk of work
-            for (int c0 = cbeg; c0 < cend; c0 += 16) {
-                const int r0 = row0 + c0;
-                const bool whole = whole_at(c0);
-                const int cn = c0 + 16;
-                const bool next_whole = cn < cend && whole_at(cn);
-                if (next_whole) load_rs(cn, rs_next);
-                float v[16], w[16];
-                tmem_ld16(tl + c0, v);
-                tmem_ld16(tl + BN + c0, w);
-#pragma unroll
-                for (int t = 0; t < 16; ++t) v[t] += w[t];
-                if (KS > 1) {
-                    // partial sums of ranks 0 .. KS-1 added in rank order
-                    float tot[16];
-#pragma unroll
-                    for (int k = 0; k < KS; ++k) {
-                        float part[16];
-                        if (k == rank) {
-#pragma unroll
-                            for (int t = 0; t < 16; ++t) part[t] = v[t];
-                        } else {
-                            const float* rb = recv + (k < rank ? k : k - 1) * kSlotTile * OWN;
-#pragma unroll
-                            for (int t = 0; t < 16; t += 4) {
-                                const float4 o =
-                                    *reinterpret_cast<const float4*>(rb + recv_off<OWN>(q * 32 + lane, c0 - own0 + t));
-                                part[t] = o.x;
-                                part[t + 1] = o.y;
-                                part[t + 2] = o.z;
-                                part[t + 3] = o.w;
-                            }
-                        }
-#pragma unroll
-                        for (int t = 0; t < 16; ++t) tot[t] = k == 0 ? part[t] : tot[t] + part[t];
-                    }
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) v[t] = tot[t];
-                }
-                if (whole) {
-#pragma unroll
-                    for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
-                    __syncwarp();
-#pragma unroll
-                    for (int pass = 0; pass < 4; ++pass) {
-                        const int sl = pass * 8 + (lane >> 2);          // slot within the warp's 32
-                        if (qq[pass] >= 0) {
-                            float a4[4];
-#pragma unroll
-                            for (int t = 0; t < 4; ++t) a4[t] = xb[sl * 17 + cg + t];
-                            chunk4_apply(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, in[pass], rs);
-                        }
-                        if (next_whole) load_pass(cn, pass);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) rs[k] = rs_next[k];
-                    __syncwarp();
-                    continue;
-                }
-                if (qp >= 0) {
-#pragma unroll 4
-                    for (int t = 0; t < 16; ++t) {
-                        const int r = r0 + t;
-                        if (r >= g.rows) continue;
-                        if (MODE == MODE_CHECK1) check1_elem(p, slot, qp, ri, r, v[t], ra, rb, rc, rd);
-                        else if (MODE == MODE_CHECK2) check2_elem(p, qp, r, v[t], ra, rb);
-                        else layer_elem(p, slot, qp, ri, r, v[t]);
-                    }
-                }
-                if (next_whole) {
-#pragma unroll
-                    for (int pass = 0; pass < 4; ++pass) load_pass(cn, pass);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) rs[k] = rs_next[k];
+        mbar_init(smem_u32(&bars[2 * STAGES]), 1);
+        mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * HALVES);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (KS > 1) cluster_sync();
+    const uint32_t tmem = *tmem_holder;
+    griddep_launch();
+
+    if (warp == 0) {
+        // ------------------------- TMA producer -------------------------
+        if (lane == 0) {
+            prefetch_map(&tmA);
+            prefetch_map(&tmB);
+            const int b0 = g.b_row[0] + ri * g.b_rho_stride + row0, b1 = g.b_row[1] + ri * g.b_rho_stride + row0;
+            int issued = 0;
+            for (int j = 1; j <= c.nl; ++j) {
+                if (*(volatile int*)&s_fail) break;
+                const int a0 = 2 * ((j - 1) & 1) * c.slots + slot0;
+                const bool ok = produce_layer<2, BN, STAGES, L::kStage, L::kA>(
+                    &tmA, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK,
+                    (j - 1) * kb_count, a0, a0 + c.slots, b0, b1, j == 1 ? nullptr : c.sync + tile,
+                    (unsigned)(j - 1) * nct, issued);
+                if (!ok) {
+                    atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                    s_fail = 1;
+                    break;
                 }
             }
-            if (qp >= 0) {
-                if (MODE == MODE_CHECK1) {
-                    red_slot(p.RED, qp, RW_RP, ra);
-                    red_slot(p.RED, qp, RW_AX, rb);
-                    red_slot(p.RED, qp, RW_Z, rc);
-                    red_slot(p.RED, qp, RW_PX, rd);
-                } else if (MODE == MODE_CHECK2) {
-                    red_slot(p.RED, qp, RW_RD, ra);
-                    red_slot(p.RED, qp, RW_ATL, rb);
+            // wait (bounded) for the copies still in flight
+            for (int gk = (issued > STAGES ? issued - STAGES : 0); gk < issued; ++gk)
+                mbar_wait(smem_u32(&bars[gk % STAGES]), (gk / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        // ------------------------- MMA issuer -------------------------
+        if (lane == 0) {
+            int done = 0;
+            for (int j = 1; j <= c.nl; ++j) {
+                if (*(volatile int*)&s_fail) break;
+                if (!issue_layer<BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem, kb_count,
+                                                               (j - 1) * kb_count)) {
+                    atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                    s_fail = 1;
+                    break;
                 }
+                mma_commit(smem_u32(&bars[2 * STAGES]));
+                done = j;
+            }
+            // keep TMEM alive until the last MMAs have landed
+            if (done > 0 && !mbar_wait(smem_u32(&bars[2 * STAGES]), (done - 1) & 1)) {
+                atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                s_fail = 1;
+            }
+        }
+        __syncwarp();
+    } else if (HALVES == 2 || warp < 6) {
+        // ------------------------- epilogue -------------------------
+        griddep_wait();
+        constexpr int kEpiThreads = 32 * 4 * HALVES;
+        for (int j = 1; j <= c.nl; ++j) {
+            BatchParams q = p;
+            q.flags = EPI_REFINE | (j == c.nl ? c.last_flags : 0u);
+            q.Dhi = c.OP + (size_t)(2 * (j & 1)) * c.opart;
+            q.Dlo = q.Dhi + c.opart;
+            tile_epilogue<MODE_LAYER_REFINED, BN, KS>(q, g, warp, lane, rank, slot0, row0, ri, tmem, xpose, recv,
+                                                      smem_u32(&bars[2 * STAGES]), (uint32_t)((j - 1) & 1),
+                                                      smem_u32(&bars[2 * STAGES + 1]), (uint32_t)((j - 1) & 1),
+                                                      &s_fail);
+            // release this CTA's part of layer j: its operand and state stores, then
+            // its TMEM reads, before the tile's counter moves on
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            fence_before();
+            // barrier of the epilogue warps that also ORs their view of the failure
+            // flag, so that all of them leave the loop together or none does
+            const int mine = *(volatile int*)&s_fail;
+            int any;
+            asm volatile(
+                "{\n .reg .pred pi, po;\n setp.ne.s32 pi, %1, 0;\n"
+                " bar.red.or.pred po, 1, %2, pi;\n selp.s32 %0, 1, 0, po;\n}\n"
+                : "=r"(any)
+                : "r"(mine), "r"(kEpiThreads)
+                : "memory");
+            if (any) break;
+            if (warp == 2 && lane == 0) {
+                __threadfence();
+                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c.sync + tile) : "memory");
             }
         }
     }
     fence_before();
     __syncthreads();
-    // no CTA of a cluster leaves while another may still address its shared memory
     if (KS > 1) cluster_sync();
     if (warp == 1) {
         fence_after();
@@ -639,6 +902,7 @@ struct TcState {
     int bn_layer = 128, bn_check = 128;
     std::vector<int> bn_by_tiles;        // refined-layer width per number of active slot tiles
     int ks = 1;                          // K split of the refined layer (fixed per handle by the tuner)
+    bool chunk_ok = true;                // persistent chunk kernel usable (cleared after a refused launch)
     int* err = nullptr;                  // = counters + CNT_ERR
     // encoded maps, keyed by box rows
     CUtensorMap opnd_map, ck_map;
@@ -701,6 +965,67 @@ int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const Bat
     cfg.numAttrs = na;
     RQ_CUDA(h, cudaLaunchKernelEx(&cfg, kern, a, b, p, g));
     return RELU_QP_OK;
+}
+
+template <int BN, int KS>
+int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
+                 const ChunkArgs& c, int tiles_y) {
+    constexpr int S = stages_for<MODE_LAYER_REFINED, BN, KS>();
+    using L = TcSmem<2, 2, BN, S, KS>;
+    auto kern = tc_chunk_kernel<BN, S, KS>;
+    RQ_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(KS * ceil_div(g.rows, BN), tiles_y);
+    cfg.blockDim = dim3(kThreadsTC);
+    cfg.dynamicSmemBytes = L::kBytes;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[3];
+    int na = 0;
+    if (KS > 1) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = KS;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    attr[na].id = cudaLaunchAttributeCooperative;     // every CTA co-resident
+    attr[na].val.cooperative = 1;
+    ++na;
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, p, g, c);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RELU_QP_ERR_UNSUPPORTED;     // the caller falls back to one launch per layer
+    }
+    return RELU_QP_OK;
+}
+
+int dispatch_chunk(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
+                   const CUtensorMap& a, const ChunkArgs& c, int tiles_y) {
+    if (ks == 4) {
+        switch (bn) {
+            case 64: return launch_chunk<64, 4>(h, a, wmaps[1], p, g, c, tiles_y);
+            case 128: return launch_chunk<128, 4>(h, a, wmaps[3], p, g, c, tiles_y);
+        }
+    } else if (ks == 2) {
+        switch (bn) {
+            case 64: return launch_chunk<64, 2>(h, a, wmaps[1], p, g, c, tiles_y);
+            case 128: return launch_chunk<128, 2>(h, a, wmaps[3], p, g, c, tiles_y);
+            case 192: return launch_chunk<192, 2>(h, a, wmaps[5], p, g, c, tiles_y);
+        }
+    } else {
+        switch (bn) {
+            case 64: return launch_chunk<64, 1>(h, a, wmaps[1], p, g, c, tiles_y);
+            case 128: return launch_chunk<128, 1>(h, a, wmaps[3], p, g, c, tiles_y);
+            case 192: return launch_chunk<192, 1>(h, a, wmaps[5], p, g, c, tiles_y);
+            case 256: return launch_chunk<256, 1>(h, a, wmaps[6], p, g, c, tiles_y);
+        }
+    }
+    return RELU_QP_ERR_UNSUPPORTED;
 }
 
 // Refined layer widths by K split: KS = 4 takes 64 and 128 (each CTA
@@ -848,6 +1173,36 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int 
     g.a_row[1] = (2 * operand_set + 1) * w.slots;
     return dispatch_refined(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, tiles, pdl);
 }
+
+int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active_tiles) {
+    BatchWork& w = h->bw;
+    TcState* st = static_cast<TcState*>(w.tc);
+    if (!st->chunk_ok || nl < 1 || active_tiles < 1) return RELU_QP_ERR_UNSUPPORTED;
+    int bn = st->bn_layer;
+    if (!st->bn_by_tiles.empty())
+        bn = st->bn_by_tiles[std::max(1, std::min<int>(active_tiles, (int)st->bn_by_tiles.size() - 1))];
+    const int tiles_y = std::min(active_tiles, w.slots / kSlotTile);
+    // all CTAs of the active tiles co-resident, one per SM
+    if ((long long)st->ks * ceil_div(h->R, bn) * tiles_y > h->num_sms) return RELU_QP_ERR_UNSUPPORTED;
+    TcArgs g{};
+    g.num_kb = w.ldk / kBK;
+    g.rows = h->R;
+    g.err = st->err;
+    g.b_rho_stride = 3 * w.Rpad;
+    for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
+    ChunkArgs c{};
+    c.nl = nl;
+    c.last_flags = last_flags;
+    c.OP = static_cast<__nv_bfloat16*>(w.OPND);
+    c.opart = (size_t)w.slots * w.ldk;
+    c.slots = w.slots;
+    c.sync = w.chunk_sync;
+    const int rc = dispatch_chunk(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, c, tiles_y);
+    if (rc == RELU_QP_ERR_UNSUPPORTED) st->chunk_ok = false;   // launch refused: not again for this handle
+    return rc;
+}
+
+void tc_disable_chunk(relu_qp_t h) { static_cast<TcState*>(h->bw.tc)->chunk_ok = false; }
 
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
     BatchWork& w = h->bw;

@@ -108,6 +108,7 @@ struct BatchWork {
     unsigned *TRED = nullptr, *TBAR = nullptr;
     int* TLIST = nullptr;
     int tail_grid = 0;                     // CTAs of its cooperative launch (0: unavailable)
+    unsigned* chunk_sync = nullptr;        // per slot tile: layer counters of the persistent chunk kernel
 };
 
 }  // namespace rq
