@@ -1046,7 +1046,11 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     }
     RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (bf16 && tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "a tensor-core kernel wait passed its deadline");
+    if (bf16) {
+        const int e = tc_error(h);
+        if (e == RELU_QP_ERR_TIMEOUT) return fail(h, e, "a tensor-core kernel wait passed its deadline");
+        if (e) return fail(h, RELU_QP_ERR_CUDA, "a tensor-core kernel found a launch shape it cannot run");
+    }
     if (tail_used && batch_tail_error(h))
         return fail(h, RELU_QP_ERR_TIMEOUT, "a grid barrier of the convergence-tail kernel passed its deadline");
     for (size_t e = 0; e + 1 < prof_used; e += 2) {

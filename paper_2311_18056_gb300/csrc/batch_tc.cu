@@ -174,6 +174,12 @@ __device__ __forceinline__ uint32_t cluster_rank() {
     return r;
 }
 
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
 // shared::cluster address of the variable at shared::cta address `addr` in CTA `rank`
 __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
     uint32_t r;
@@ -614,6 +620,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
     const int tile = blockIdx.y;
     if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA (and the cluster)
+    // the partial-sum exchange addresses KS CTAs of a cluster: refuse any other launch shape
+    if (KS > 1 && cluster_size() != (uint32_t)KS) {
+        if (threadIdx.x == 0) atomicExch(g.err, RELU_QP_ERR_CUDA);
+        return;
+    }
     const int slot0 = tile * kSlotTile;
     const int rank = KS > 1 ? (int)cluster_rank() : 0;
     const int row0 = (blockIdx.x / KS) * BN;
@@ -686,11 +697,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         if (lane == 0) {
             const bool ok = issue_mmas<NPROD, BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
                                                                            kb_count);
-            if (ok) {
-                mma_commit(smem_u32(&bars[2 * STAGES]));
-                // keep TMEM alive until the MMAs have landed
-                if (!mbar_wait(smem_u32(&bars[2 * STAGES]), 0)) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); s_fail = 1; }
-            } else {
+            // (also after a failure: MMAs already issued must land before TMEM is freed)
+            mma_commit(smem_u32(&bars[2 * STAGES]));
+            // keep TMEM alive until the MMAs have landed
+            if (!mbar_wait(smem_u32(&bars[2 * STAGES]), 0) || !ok) {
                 atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
                 s_fail = 1;
             }
@@ -725,8 +735,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // only once the counter shows every CTA of the tile done with layer j - 1.
 // That also orders the reuse of TMEM and of the receive buffers (a partner
 // sends layer j's partial sums only after all of layer j - 1 is done).  The
-// CTAs of a tile must be co-resident (cooperative launch; the host checks the
-// count); every wait has a deadline.
+// CTAs of a tile must be co-resident: the host launches it only when the grid
+// is at most one CTA per SM and nothing else of the handle runs beside it;
+// every wait has a deadline.
 // ---------------------------------------------------------------------------
 struct ChunkArgs {
     int nl;                    // refined layers of the chunk (1 .. nl)
@@ -751,6 +762,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 
     const int tile = blockIdx.y;
     if (tile >= p.counters[CNT_TILES]) return;     // uniform over the CTA (and the cluster)
+    if (KS > 1 && cluster_size() != (uint32_t)KS) {
+        if (threadIdx.x == 0) atomicExch(g.err, RELU_QP_ERR_CUDA);
+        return;
+    }
     const int slot0 = tile * kSlotTile;
     const int rank = KS > 1 ? (int)cluster_rank() : 0;
     const int row0 = (blockIdx.x / KS) * BN;
@@ -818,20 +833,22 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
         if (lane == 0) {
-            int done = 0;
+            int commits = 0;
             for (int j = 1; j <= c.nl; ++j) {
                 if (*(volatile int*)&s_fail) break;
-                if (!issue_layer<BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem, kb_count,
-                                                               (j - 1) * kb_count)) {
+                const bool ok = issue_layer<BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
+                                                                        kb_count, (j - 1) * kb_count);
+                // committed also after a failure, so that the MMAs already issued are waited for
+                mma_commit(smem_u32(&bars[2 * STAGES]));
+                ++commits;
+                if (!ok) {
                     atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
                     s_fail = 1;
                     break;
                 }
-                mma_commit(smem_u32(&bars[2 * STAGES]));
-                done = j;
             }
             // keep TMEM alive until the last MMAs have landed
-            if (done > 0 && !mbar_wait(smem_u32(&bars[2 * STAGES]), (done - 1) & 1)) {
+            if (commits > 0 && !mbar_wait(smem_u32(&bars[2 * STAGES]), (commits - 1) & 1)) {
                 atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
                 s_fail = 1;
             }
@@ -979,7 +996,7 @@ int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const 
     cfg.blockDim = dim3(kThreadsTC);
     cfg.dynamicSmemBytes = L::kBytes;
     cfg.stream = h->stream;
-    cudaLaunchAttribute attr[3];
+    cudaLaunchAttribute attr[2];
     int na = 0;
     if (KS > 1) {
         attr[na].id = cudaLaunchAttributeClusterDimension;
@@ -988,9 +1005,6 @@ int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const 
         attr[na].val.clusterDim.z = 1;
         ++na;
     }
-    attr[na].id = cudaLaunchAttributeCooperative;     // every CTA co-resident
-    attr[na].val.cooperative = 1;
-    ++na;
     attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[na].val.programmaticStreamSerializationAllowed = 1;
     ++na;
