@@ -170,9 +170,10 @@ def kernel_source_hash():
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the refined tensor-core layer from the committed
-    ncu summary, if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "tc_layer_refined_batched_n800.md")
+    """DRAM bytes per refined layer and the QP slots that layer covered, from the
+    committed ncu summary of the persistent chunk kernel, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "tc_chunk_refined_batched_n800.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -183,7 +184,7 @@ def profiled_traffic():
     if vals.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"]), float(vals["algorithmic_flops_per_launch"].split()[0])
+        return float(vals["dram_bytes_per_layer"]), float(vals["qp_slots_per_layer"])
     except (KeyError, ValueError):
         return None
 
@@ -344,23 +345,27 @@ def run_ours(args):
     e2e = {"value": solves / t_e2e, "unit": UNIT, "h2d_bytes_per_step": B * pq.nx * 4,
            "d2h_bytes_per_step": B * (pq.n + 2 * pq.m) * 4 + B * 40}
 
-    # ---- roofline of the dominant kernel (tensor-core refined layer) ----
+    # ---- roofline of the dominant kernel: the tensor-core refined layer (one unit =
+    # one layer over the active QPs; the persistent chunk kernel runs 24 per launch) ----
     peak_sus, peak_burst, peak_kind = measured_peaks()
     roof = None
     if prof["layer_timed"] > 0 and prof["layer_ms"] > 0:
-        flops_per_launch = prof["layer_flops"] / max(prof["layer_launches"], 1)
+        flops_per_layer = prof["layer_flops"] / max(prof["layer_launches"], 1)
         achieved = prof["layer_flops"] / (prof["layer_ms"] / 1e3) / 1e12
+        qps_per_layer = flops_per_layer / (2.0 * 3.0 * (pq.n + pq.m) ** 2)
         tr = profiled_traffic()
-        # the capture is a full-batch launch; scale its bytes to the average launch by the work it does
-        traffic = None if tr is None else tr[0] * flops_per_launch / tr[1]
+        # the capture covered a known number of QP slots: scale its bytes to the average layer's QPs
+        traffic = None if tr is None else tr[0] * qps_per_layer / tr[1]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
                 "frac": achieved / peak_sus, "traffic": traffic,
-                "traffic_basis": "ncu dram bytes of a full-batch launch (profiles/tc_layer_refined_batched_n800.md)"
-                                 " scaled by the average launch's QPs",
-                "kernel": "tc_gemm_kernel refined layer (3 BF16 products, FP32 accumulate in TMEM)",
+                "traffic_basis": "ncu DRAM bytes per layer of a chunk-kernel launch "
+                                 "(profiles/tc_chunk_refined_batched_n800.md), scaled by QPs",
+                "kernel": "refined tensor-core layer (tc_chunk_kernel / tc_gemm_kernel): 3 BF16 products, "
+                          "FP32 accumulate in TMEM, epilogue fused",
+                "unit_of_work": "one refined layer over the active QPs",
                 "peak_kind": f"bf16 sustained, {peak_kind}",
-                "launches_timed": prof["layer_timed"], "avg_launch_us": 1e3 * prof["layer_ms"] / prof["layer_timed"],
-                "flops_per_launch": flops_per_launch}
+                "layers_timed": prof["layer_timed"], "avg_layer_us": 1e3 * prof["layer_ms"] / prof["layer_timed"],
+                "flops_per_layer": flops_per_layer, "avg_qps_per_layer": qps_per_layer}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": float(step_ms.mean()), "higher_is_better": True, "scaling": "weak",
