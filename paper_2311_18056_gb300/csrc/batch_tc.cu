@@ -75,6 +75,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t done;
     asm volatile(
@@ -236,7 +240,10 @@ struct TcSmem {
     // the partners' partial sums of this CTA's columns: KS - 1 buffers of [128 slots][BN / KS
     // columns], 16-byte chunks swizzled by slot
     static constexpr int kRecv = KS > 1 ? (KS - 1) * kSlotTile * (BN / KS) * 4 : 0;
-    static constexpr int kBytes = STAGES * kStage + kXpose + kRecv + 1024 /* align */ + 256 /* barriers */;
+    // 3-part modes: FP32 running sums of the drained accumulators, per epilogue warp
+    // [32 lanes][BN / 2 + 1] (padded rows)
+    static constexpr int kDrain = NA == 3 ? 8 * 32 * (BN / 2 + 1) * 4 : 0;
+    static constexpr int kBytes = STAGES * kStage + kXpose + kRecv + kDrain + 1024 /* align */ + 256 /* barriers */;
 };
 
 // ---------------------------------------------------------------------------
@@ -393,6 +400,45 @@ __device__ __noinline__ bool issue_mmas(uint32_t sbase, uint32_t bar0, uint32_t 
     return true;
 }
 
+// 3-part modes (accurate layer, residual products): the products of k-block kb
+// go into a fresh accumulator pair in TMEM buffer kb & 1 (columns
+// [2 BN (kb & 1), 2 BN (kb & 1) + 2 BN)), committed to kready[kb & 1]; the
+// epilogue warps add every k-block's pair into FP32 running sums (round to
+// nearest) and release the buffer through drained[kb & 1].  The tensor core's
+// truncating accumulation then spans the 4 MMA steps of one k-block instead of
+// the whole dot product.
+template <int BN, int STAGES, int KSTAGE, int KA>
+__device__ __noinline__ bool issue_mmas_drain(uint32_t sbase, uint32_t bar0, uint32_t tmem, int nkb, uint32_t kready0,
+                                              uint32_t drained0) {
+    constexpr uint32_t IDESC = idesc_bf16(BN);
+    const uint64_t d0 = sdesc(sbase);
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        const int b = kb & 1;
+        if (!mbar_wait(bar0 + 8 * s, (kb / STAGES) & 1)) return false;
+        if (kb >= 2 && !mbar_wait(drained0 + 8 * b, ((kb >> 1) - 1) & 1)) return false;
+        fence_after();
+        const uint64_t da = d0 + (uint64_t)((s * KSTAGE) >> 4);
+        const uint64_t db = da + (uint64_t)(KA >> 4);
+        const uint32_t tb = tmem + (uint32_t)(2 * BN * b);
+#pragma unroll
+        for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+            for (int pr = 0; pr < 6; ++pr) {
+                const int ia = pr == 0 ? 0 : pr == 1 ? 0 : pr == 2 ? 1 : pr == 3 ? 0 : pr == 4 ? 1 : 2;
+                const int ib = pr == 0 ? 0 : pr == 1 ? 1 : pr == 2 ? 0 : pr == 3 ? 2 : pr == 4 ? 1 : 0;
+                const uint64_t ad = da + (uint64_t)((ia * kTileBytesA + kk * 32) >> 4);
+                const uint64_t bd = db + (uint64_t)((ib * BN * 128 + kk * 32) >> 4);
+                const bool first = kk == 0 && pr <= 1;   // fresh pair for every k-block
+                mma_bf16(tb + (pr == 0 ? 0 : BN), ad, bd, IDESC, first ? 0u : 1u);
+            }
+        }
+        mma_commit(bar0 + 8 * (STAGES + s));
+        mma_commit(kready0 + 8 * b);
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
@@ -415,10 +461,13 @@ template <int MODE, int BN, int KS>
 __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs& g, int warp, int lane, int rank,
                                               int slot0, int row0, int ri, uint32_t tmem, float* xpose, float* recv,
                                               uint32_t bar_acc, uint32_t par_acc, uint32_t bar_recv,
-                                              uint32_t par_recv, int* s_fail) {
+                                              uint32_t par_recv, int* s_fail, float* drain = nullptr, int nkb = 0,
+                                              uint32_t kready0 = 0, uint32_t drained0 = 0) {
     constexpr int OWN = BN / KS;
     constexpr int HALVES = OWN >= 32 ? 2 : 1;
     constexpr int PER = OWN / HALVES;
+    constexpr bool DRAIN = MODE != MODE_LAYER_REFINED;
+    static_assert(!DRAIN || KS == 1, "drained modes run without a K split");
     const int q = warp & 3;                         // TMEM lane quadrant of this warp
     const int half = (warp - 2) >> 2;               // which half of this CTA's columns
     const int slot = slot0 + q * 32 + lane;
@@ -459,11 +508,40 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
     // polls) for the whole main loop; then every lane observes the
     // completed phase itself
     bool ready = true;
-    if (lane == 0) ready = mbar_wait_sleep(bar_acc, par_acc, 256);
-    ready = __shfl_sync(0xffffffffu, ready, 0);
-    if (ready) ready = mbar_wait(bar_acc, par_acc);
-    ready = __all_sync(0xffffffffu, ready);
-    if (ready) fence_after();
+    // this warp's running sums [lane][PER] (drained modes)
+    float* dsum = DRAIN ? drain + (warp - 2) * 32 * (PER + 1) + lane * (PER + 1) : nullptr;
+    if (DRAIN) {
+#pragma unroll
+        for (int c = 0; c < PER; ++c) dsum[c] = 0.f;
+        for (int kb = 0; kb < nkb && ready; ++kb) {
+            const int b = kb & 1;
+            const uint32_t par = (kb >> 1) & 1;
+            if (lane == 0) ready = mbar_wait_sleep(kready0 + 8 * b, par, 64);
+            ready = __shfl_sync(0xffffffffu, ready, 0);
+            if (ready) ready = mbar_wait(kready0 + 8 * b, par);
+            ready = __all_sync(0xffffffffu, ready);
+            if (!ready) break;
+            fence_after();
+            const uint32_t tb = tl + (uint32_t)(2 * BN * b);
+#pragma unroll
+            for (int c = 0; c < PER; c += 16) {
+                float v[16], w[16];
+                tmem_ld16(tb + cbeg + c, v);
+                tmem_ld16(tb + BN + cbeg + c, w);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) dsum[c + t] += v[t] + w[t];
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(drained0 + 8 * b);
+        }
+    } else {
+        if (lane == 0) ready = mbar_wait_sleep(bar_acc, par_acc, 256);
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (ready) ready = mbar_wait(bar_acc, par_acc);
+        ready = __all_sync(0xffffffffu, ready);
+        if (ready) fence_after();
+    }
     if (KS > 1) {
         // send every partner its columns of this warp's TMEM lanes: row (q * 32 + lane)
         // of buffer j of the partner's receive area (j = this CTA's index among the
@@ -511,11 +589,17 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
             const int cn = c0 + 16;
             const bool next_whole = cn < cend && whole_at(cn);
             if (next_whole) load_rs(cn, rs_next);
-            float v[16], w[16];
-            tmem_ld16(tl + c0, v);
-            tmem_ld16(tl + BN + c0, w);
+            float v[16];
+            if (DRAIN) {
 #pragma unroll
-            for (int t = 0; t < 16; ++t) v[t] += w[t];
+                for (int t = 0; t < 16; ++t) v[t] = dsum[c0 - cbeg + t];
+            } else {
+                float w[16];
+                tmem_ld16(tl + c0, v);
+                tmem_ld16(tl + BN + c0, w);
+#pragma unroll
+                for (int t = 0; t < 16; ++t) v[t] += w[t];
+            }
             if (KS > 1) {
                 // partial sums of ranks 0 .. KS-1 added in rank order
                 float tot[16];
@@ -610,7 +694,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     constexpr int NB = NA;
     constexpr int NPROD = NA == 2 ? 3 : 6;
     constexpr int ACC = 2;   // significance accumulators of BN columns each
-    constexpr int TCOLS = tmem_cols(ACC * BN);
+    constexpr bool DRAIN = MODE != MODE_LAYER_REFINED;
+    constexpr int TCOLS = tmem_cols((DRAIN ? 2 : 1) * ACC * BN);   // drained modes: two buffers
     constexpr int OWN = BN / KS;        // columns this CTA finalises
     constexpr int HALVES = OWN >= 32 ? 2 : 1;   // epilogue warps per TMEM lane quadrant
     constexpr int PER = OWN / HALVES;   // columns per epilogue warp
@@ -637,10 +722,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float* xpose = reinterpret_cast<float*>(smem + STAGES * L::kStage);
     float* recv = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
+    float* drain = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv + L::kDrain);
     // bars[0..S) full, bars[S..2S) empty, bars[2S] accumulator ready, bars[2S+1] partners'
-    // partial sums received (KS > 1); then the TMEM address
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+    // partial sums received (KS > 1), bars[2S+2..2S+3] k-block buffer ready, bars[2S+4..2S+5]
+    // buffer drained (3-part modes); then the TMEM address
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -652,6 +739,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mbar_init(smem_u32(&bars[2 * STAGES]), 1);
         // one arrival per epilogue warp of every partner
         mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * HALVES);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&bars[2 * STAGES + 2 + b]), 1);
+            mbar_init(smem_u32(&bars[2 * STAGES + 4 + b]), 4 * HALVES);   // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -695,8 +786,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
         if (lane == 0) {
-            const bool ok = issue_mmas<NPROD, BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
-                                                                           kb_count);
+            const bool ok =
+                DRAIN ? issue_mmas_drain<BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem, kb_count,
+                                                                      smem_u32(&bars[2 * STAGES + 2]),
+                                                                      smem_u32(&bars[2 * STAGES + 4]))
+                      : issue_mmas<NPROD, BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
+                                                                       kb_count);
             // (also after a failure: MMAs already issued must land before TMEM is freed)
             mma_commit(smem_u32(&bars[2 * STAGES]));
             // keep TMEM alive until the MMAs have landed
@@ -712,7 +807,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // operand it read is overwritten: wait for it
         griddep_wait();
         tile_epilogue<MODE, BN, KS>(p, g, warp, lane, rank, slot0, row0, ri, tmem, xpose, recv,
-                                    smem_u32(&bars[2 * STAGES]), 0, smem_u32(&bars[2 * STAGES + 1]), 0, &s_fail);
+                                    smem_u32(&bars[2 * STAGES]), 0, smem_u32(&bars[2 * STAGES + 1]), 0, &s_fail,
+                                    drain, kb_count, smem_u32(&bars[2 * STAGES + 2]), smem_u32(&bars[2 * STAGES + 4]));
     }
     fence_before();
     __syncthreads();
@@ -943,7 +1039,7 @@ template <int MODE, int BN, int KS>
 constexpr int stages_for() {
     using L1 = TcSmem<MODE == MODE_LAYER_REFINED ? 2 : 3, MODE == MODE_LAYER_REFINED ? 2 : 3, BN, 1, KS>;
     constexpr int budget = 227 * 1024 - 512;   // opt-in maximum less the static shared memory
-    constexpr int s = (budget - 1024 - 256 - L1::kXpose - L1::kRecv) / L1::kStage;
+    constexpr int s = (budget - 1024 - 256 - L1::kXpose - L1::kRecv - L1::kDrain) / L1::kStage;
     return s > 4 ? 4 : s;
 }
 
@@ -1080,8 +1176,11 @@ int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, cons
 template <int MODE>
 int dispatch_3part(relu_qp_t h, int bn, const CUtensorMap& b64, const CUtensorMap& b128, const BatchParams& p,
                    const TcArgs& g, const CUtensorMap& a, int tiles) {
-    if (bn <= 64) return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles, false);
-    return launch_tc<MODE, 128, 1>(h, a, b128, p, g, tiles, false);
+    // the drained accumulation keeps FP32 sums of BN / 2 columns per epilogue warp in
+    // shared memory: BN = 64 leaves room for two pipeline stages
+    (void)bn;
+    (void)b128;
+    return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles, false);
 }
 
 }  // namespace

@@ -76,11 +76,11 @@ struct SingleWork {
 // Workspace of batched solves (allocated when opts.max_batch > 0).
 struct BatchWork {
     int cap = 0, slots = 0, prec = 0, B = 0;
-    int rebase_tc = 0;   // BF16 form: 1 = accurate layer on the tensor cores (3-way split),
-                         // 0 = on the CUDA cores in FP32 (default; see batch.cu)
-    int check_tc = 0;    // BF16 form: 1 = residual products on the tensor cores (3-way split),
-                         // 0 = on the CUDA cores in FP32 (default: the tensor core's truncating
-                         // accumulation is too coarse for the stop test when |lam| ~ 1e3)
+    int rebase_tc = 1;   // BF16 form: 1 = accurate layer on the tensor cores (3-way split, every
+                         // k-block's products drained into FP32 sums; default), 0 = on the CUDA
+                         // cores in FP32
+    int check_tc = 1;    // BF16 form: 1 = residual products on the tensor cores (3-way split,
+                         // drained like the accurate layer; default), 0 = on the CUDA cores in FP32
     int ldn = 0, ldm = 0, ldR = 0, ldk = 0, n64 = 0, m64 = 0, ldkc = 0, Rpad = 0, npad = 0;
     // check matrix [[P, A^T], [A, 0]]: (n + m) rows (padded to npad), ldkc = n64 + m64 columns
     // per-QP state (QP-indexed rows)
