@@ -603,7 +603,8 @@ int batch_alloc(relu_qp_t h) {
         RQ_TRY(dev_alloc(h, &w.CK, sizeof(uint16_t) * 3 * (size_t)w.slots * w.ldkc + 1024));
         RQ_TRY(dev_alloc(h, &w.WB, sizeof(uint16_t) * (size_t)nr * 3 * w.Rpad * w.ldk + 1024));
         RQ_TRY(dev_alloc(h, &w.WCB, sizeof(uint16_t) * 3 * (size_t)w.npad * w.ldkc + 1024));
-        RQ_TRY(alloc(h, &w.chunk_sync, (size_t)w.slots / kSlotTile));
+        RQ_TRY(alloc(h, &w.chunk_sync, 2 * (size_t)w.slots / kSlotTile));   // layer counters, done counters
+        RQ_CUDA(h, cudaMemset(w.chunk_sync, 0, sizeof(unsigned) * 2 * (w.slots / kSlotTile)));
     } else {
         RQ_TRY(alloc(h, &w.S32, 2 * (size_t)w.slots * w.ldk));
         RQ_TRY(alloc(h, &w.CK32, (size_t)w.slots * w.ldkc));
@@ -613,25 +614,28 @@ int batch_alloc(relu_qp_t h) {
     return RELU_QP_OK;
 }
 
-__global__ void tune_perm_kernel(int slots, int cap, int active_tiles, int* perm, int* tile_rho, int* counters) {
-    const int live = min(cap, active_tiles * kSlotTile);
+// Tuning layout: the first `active_tiles` tiles hold `per_tile` QPs each (a prefix
+// of the tile, as the regrouping leaves it).
+__global__ void tune_perm_kernel(int slots, int cap, int active_tiles, int per_tile, int* perm, int* tile_rho,
+                                 int* counters) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += gridDim.x * blockDim.x) {
-        perm[s] = s < live ? s : -1;
+        const bool in = s / kSlotTile < active_tiles && s % kSlotTile < per_tile && s < cap;
+        perm[s] = in ? s : -1;
         if (s % kSlotTile == 0) tile_rho[s / kSlotTile] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         counters[CNT_TILES] = active_tiles;
-        counters[CNT_ACTIVE] = live;
+        counters[CNT_ACTIVE] = min(cap, active_tiles * per_tile);
     }
 }
 
-// Choose the K split and the BN (rows per tile) of the tcgen05 refined layer
-// for every number of active slot tiles, and the BN of the check kernels on
-// the full capacity, by timing them (state values do not matter here; every
-// buffer they touch is re-initialised by the next solve).  The split is one
-// per handle, so that a QP's arithmetic never depends on its batch: the
-// split whose best widths give the smallest summed time over the measured
-// tile counts wins.  RELU_QP_TUNE_LOG=1 prints the measurements to stderr.
+// Choose the refined layer's configuration (K split over a cluster, tile
+// width) for every number of active slot tiles by timing what a chunk would
+// run: the persistent chunk kernel where the tiles fit one wave, else one
+// launch per layer.  Counts of one or two tiles are timed with tiles that hold
+// 48 QPs each (the convergence tail); larger counts with full tiles.  State
+// values do not matter here; every buffer the layers touch is re-initialised by
+// the next solve.  RELU_QP_TUNE_LOG=1 prints the measurements to stderr.
 int tc_tune(relu_qp_t h) {
     BatchWork& w = h->bw;
     BatchParams p = base_params(h);
@@ -644,85 +648,73 @@ int tc_tune(relu_qp_t h) {
     const int tiles = w.slots / kSlotTile;
     const char* log_env = std::getenv("RELU_QP_TUNE_LOG");
     const bool log = log_env && log_env[0] == '1';
+    std::vector<LayerCfg> cfgs;
+    tc_layer_cfgs(h, cfgs);
     // measured tile counts: every count up to 8, then every 4th up to 32, then every 16th
     std::vector<int> counts;
     for (int t = 1; t <= tiles; ++t)
         if (t <= 8 || (t <= 32 && t % 4 == 0) || t % 16 == 0 || t == tiles) counts.push_back(t);
-    int splits[4];
-    const int nsplit = tc_splits(h, splits, 4);
-    double best_total = 1e300;
-    int best_ks = tc_split(h), best_full = 128;
-    std::vector<int> best_table;
-    for (int si = 0; si < nsplit; ++si) {
-        const int ks = splits[si];
-        if (ks == 1 && nsplit > 1) continue;   // a split always wins when the problem allows one
-        RQ_TRY(tc_set_split(h, ks));
-        int widths[16];
-        const int nw = tc_layer_widths(h, widths, 16);
-        std::vector<int> table(tiles + 1, widths[0]);
-        double total = 0.0;
-        int full_bn = widths[0];
-        for (int t : counts) {
-            tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, t, w.perm, w.tile_rho,
-                                                                             w.counters);
-            RQ_CUDA(h, cudaGetLastError());
-            float best = 1e30f;
-            int best_bn = widths[0];
-            for (int i = 0; i < nw; ++i) {
-                const int bn = widths[i];
-                RQ_TRY(tc_set_tiles(h, bn, 128));
+    std::vector<LayerCfg> table(tiles + 1, cfgs[0]);
+    for (int t : counts) {
+        const int per_tile = t <= 2 ? 48 : kSlotTile;
+        tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, t, per_tile, w.perm,
+                                                                         w.tile_rho, w.counters);
+        RQ_CUDA(h, cudaGetLastError());
+        float best = 1e30f;
+        LayerCfg best_c = cfgs[0];
+        for (const LayerCfg& c : cfgs) {
+            RQ_TRY(tc_set_layer_cfg(h, c));
+            float ms = 0.f;
+            int layers = 0;
+            bool chunked = false;
+            if (w.chunk_sync) {
+                RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * 2 * tiles, h->stream));
+                const int rc = tc_chunk(h, p, 2, 0u, t);    // warm-up (and eligibility)
+                if (rc == RELU_QP_OK) {
+                    RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * 2 * tiles, h->stream));
+                    RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+                    RQ_TRY(tc_chunk(h, p, 8, 0u, t));
+                    RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+                    layers = 8;
+                    chunked = true;
+                } else if (rc != RELU_QP_ERR_UNSUPPORTED) {
+                    return rc;
+                }
+            }
+            if (!chunked) {
                 RQ_TRY(tc_layer(h, p, 0, tiles, t));
                 RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
                 RQ_TRY(tc_layer(h, p, 0, tiles, t));
                 for (int rep = 1; rep < 4; ++rep) RQ_TRY(tc_layer(h, p, 0, tiles, t, true));
                 RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
-                RQ_CUDA(h, cudaEventSynchronize(h->ev1));
-                float ms = 0.f;
-                RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-                if (log) std::fprintf(stderr, "relu_qp tune: n=%d m=%d ks=%d tiles=%d bn=%d us=%.2f\n", h->n, h->m,
-                                      ks, t, bn, 1e3f * ms / 4);
-                if (ms < best) { best = ms; best_bn = bn; }
+                layers = 4;
             }
-            for (int u = t; u <= tiles; ++u) table[u] = best_bn;   // until the next measured count
-            total += best;
-            full_bn = best_bn;
+            RQ_CUDA(h, cudaEventSynchronize(h->ev1));
+            int site = 0;
+            if (tc_error(h, &site))
+                return fail(h, RELU_QP_ERR_TIMEOUT,
+                            "tensor-core wait " + std::to_string(site) + " passed its deadline while tuning (tiles " +
+                                std::to_string(t) + ", ks " + std::to_string(c.ks) + ", bn " + std::to_string(c.bn) +
+                                (chunked ? ", chunk kernel)" : ", one launch per layer)"));
+            RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+            ms /= layers;
+            if (log)
+                std::fprintf(stderr, "relu_qp tune: n=%d m=%d tiles=%d qps/tile=%d ks=%d bn=%d %s us=%.2f\n", h->n,
+                             h->m, t, per_tile, c.ks, c.bn, chunked ? "chunk" : "layer", 1e3f * ms);
+            if (ms < best) {
+                best = ms;
+                best_c = c;
+            }
         }
-        if (total < best_total) {
-            best_total = total;
-            best_ks = ks;
-            best_table = table;
-            best_full = full_bn;
-        }
+        for (int u = t; u <= tiles; ++u) table[u] = best_c;   // until the next measured count
     }
-    RQ_TRY(tc_set_split(h, best_ks));
-    tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, tiles, w.perm, w.tile_rho,
-                                                                     w.counters);
+    tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, tiles, kSlotTile, w.perm,
+                                                                     w.tile_rho, w.counters);
     RQ_CUDA(h, cudaGetLastError());
-    const int best_bn = best_full;
-    float bestc = 1e30f;
-    int best_cbn = 128;
-    for (int bn : {64, 128}) {
-        RQ_TRY(tc_set_tiles(h, best_bn, bn));
-        for (int rep = 0; rep < 2; ++rep) {
-            RQ_TRY(tc_check(h, p, 1, tiles));
-            RQ_TRY(tc_check(h, p, 2, tiles));
-        }
-        RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-        for (int rep = 0; rep < 5; ++rep) {
-            RQ_TRY(tc_check(h, p, 1, tiles));
-            RQ_TRY(tc_check(h, p, 2, tiles));
-        }
-        RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
-        RQ_CUDA(h, cudaEventSynchronize(h->ev1));
-        float ms = 0.f;
-        RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-        if (ms < bestc) { bestc = ms; best_cbn = bn; }
-    }
-    RQ_TRY(tc_set_tiles(h, best_bn, best_cbn));
-    RQ_TRY(tc_set_tiles_for(h, best_table));
+    RQ_TRY(tc_set_layer_table(h, table));
     if (log) {
-        std::fprintf(stderr, "relu_qp tune: chose ks=%d, widths by active tiles:", best_ks);
-        for (int t = 1; t <= tiles; ++t) std::fprintf(stderr, " %d", best_table[t]);
+        std::fprintf(stderr, "relu_qp tune: chose (ks, bn) by active tiles:");
+        for (int t = 1; t <= tiles; ++t) std::fprintf(stderr, " (%d,%d)", table[t].ks, table[t].bn);
         std::fprintf(stderr, "\n");
     }
     if (tc_error(h)) return fail(h, RELU_QP_ERR_TIMEOUT, "tensor-core kernel wait passed its deadline while tuning");
@@ -870,7 +862,7 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
     const bool timed = h->prof_on && bf16 && len > 1 && prof_used + 2 <= h->prof_ev.size();
     // layer counters of the persistent chunk kernel start at zero
     if (bf16 && w.chunk_sync && len > 1)
-        RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * tiles_max, h->stream));
+        RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * 2 * tiles_max, h->stream));
     for (int j = 0; j < len; ++j) {
         BatchParams q = p;
         q.flags = 0;
@@ -1000,7 +992,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     RQ_CUDA(h, cudaGetLastError());
     ++h->launches;
     RQ_TRY(regroup_slots(h, p, B, true));
-    if (bf16) RQ_CUDA(h, cudaMemsetAsync(w.counters + CNT_ERR, 0, sizeof(int), h->stream));
+    if (bf16) RQ_CUDA(h, cudaMemsetAsync(w.counters + CNT_ERR, 0, 2 * sizeof(int), h->stream));
     const int ci = h->opts.check_interval;
     const int chunk = ci > 0 ? ci : 25;
     int it = 0;

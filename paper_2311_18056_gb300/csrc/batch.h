@@ -446,13 +446,16 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phas
 int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active_tiles);
 void tc_disable_chunk(relu_qp_t h);
 void tc_release(relu_qp_t h);
-int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check);           // one refined width for every batch size
-int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles);  // [t] = width for t active slot tiles
-int tc_layer_widths(relu_qp_t h, int* out, int cap);                    // the refined widths available
-int tc_splits(relu_qp_t h, int* out, int cap);   // K splits of the refined layer the problem allows
-int tc_set_split(relu_qp_t h, int ks);           // select one (resets the width table)
-int tc_split(relu_qp_t h);
-int tc_error(relu_qp_t h);    // device error word of the backend (0 = none); clears it
+// refined-layer configuration: K split over a cluster of ks CTAs, tile width bn
+struct LayerCfg {
+    int ks, bn;
+};
+int tc_layer_cfgs(relu_qp_t h, std::vector<LayerCfg>& out);          // every configuration the problem allows
+int tc_set_layer_cfg(relu_qp_t h, LayerCfg c);                        // one for every tile count
+int tc_set_layer_table(relu_qp_t h, const std::vector<LayerCfg>& by_tiles);  // [t] = for t active slot tiles
+// device error word of the backend (0 = none) and, for a deadline, which wait gave up
+// (site); clears both
+int tc_error(relu_qp_t h, int* site = nullptr);
 
 // --- convergence tail (batch_tail.cu) --------------------------------------
 constexpr int kTailMax = 8;      // QPs the tail kernel takes at most

@@ -42,6 +42,8 @@ struct TailArgs {
     int* err;                   // error word
     const int* qlist;           // [nq] QP ids
     int nq, it0, max_iter, ci;
+    int rpc;                    // rows of the layer per CTA (contiguous)
+    int wcache;                 // 1: the CTA's Wt rows of one bank entry are cached in shared memory
     long long timeout_ns;
 };
 
@@ -121,6 +123,19 @@ constexpr int kPbs = 33;        // stride of a round's partials (32 steps, padde
 // partials of the round in step order.  acc[i] is valid in lane j < nq.
 // wrow(j, r) gives QP j's row r of the matrix; rows of QPs that share the
 // same matrix are loaded once.
+// A row of a product matrix for one QP: `ptr` addresses step 0 of the row, and
+// step c starts at ptr + c * stride (kStep in global memory, kStepPad in the
+// shared-memory cache of a CTA's rows).
+struct WRowRef {
+    const float* ptr;
+    int stride;
+};
+
+__device__ __forceinline__ float4 load_w4(const WRowRef& w, int c, int t) {
+    const float4* q = reinterpret_cast<const float4*>(w.ptr + c * w.stride) + t;
+    return w.stride == kStep ? __ldg(q) : *q;
+}
+
 template <class WRow>
 __device__ __forceinline__ void warp_rows(const float* __restrict__ opnd, int ops, float* pb, int nq,
                                           const int* s_live, int c0, int c1, int r0, int nrows, WRow wrow,
@@ -135,25 +150,20 @@ __device__ __forceinline__ void warp_rows(const float* __restrict__ opnd, int op
         unsigned todo = live;
         while (todo) {
             const int j0 = __ffs(todo) - 1;
-            const float* w0 = wrow(j0, r0);
+            const float* w0 = wrow(j0, r0).ptr;
             unsigned same = 0;
             for (int j = j0; j < nq; ++j)
-                if (((todo >> j) & 1u) && wrow(j, r0) == w0) same |= 1u << j;
+                if (((todo >> j) & 1u) && wrow(j, r0).ptr == w0) same |= 1u << j;
             todo &= ~same;
             if (c < c1) {
                 float4 wv[kRB][4];
 #pragma unroll
-                for (int i = 0; i < kRB; ++i)
+                for (int i = 0; i < kRB; ++i) {
+                    const WRowRef wr = wrow(j0, r0 + i);
 #pragma unroll
                     for (int t = 0; t < 4; ++t)
-                        wv[i][t] = r0 + i < nrows ? __ldg(reinterpret_cast<const float4*>(wrow(j0, r0 + i) + c * kStep) + t)
-                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-                // the rows' next round (same matrix) while this one computes
-                if (c + 32 < c1)
-#pragma unroll
-                    for (int i = 0; i < kRB; ++i)
-                        if (r0 + i < nrows)
-                            asm volatile("prefetch.global.L1 [%0];" ::"l"(wrow(j0, r0 + i) + (c + 32) * kStep));
+                        wv[i][t] = r0 + i < nrows ? load_w4(wr, c, t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 unsigned m = same;
                 while (m) {
                     const int j = __ffs(m) - 1;
@@ -221,6 +231,12 @@ __global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a)
     const int ops = nsteps * kStepPad;                       // staged floats per QP
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* pb = tsm + (size_t)kTailMax * ops + (size_t)warp * kRB * kTailMax * kPbs;
+    // this CTA's rows of the layer, and (a.wcache) their Wt rows of one bank entry in
+    // shared memory, in the padded step layout
+    const int row_beg = blockIdx.x * a.rpc, row_end = min(p.R, row_beg + a.rpc);
+    const int wops = (p.ldk / kStep) * kStepPad;             // cached floats per row
+    float* wc = tsm + (size_t)kTailMax * ops + (size_t)(kTailThreads / 32) * kRB * kTailMax * kPbs;
+    int cache_ri = -1;
     const int gwarp = blockIdx.x * (kTailThreads / 32) + warp, nwarps = gridDim.x * (kTailThreads / 32);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     if (threadIdx.x < kTailMax) {
@@ -238,6 +254,26 @@ __global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a)
         const bool last_chunk = it + len == a.max_iter;
         const bool check = (a.ci > 0 && (it + len) % a.ci == 0) || last_chunk;
         // ---------------- len layers ----------------
+        if (a.wcache) {
+            // cache the rows of the bank entry of the first live QP (constant data)
+            int ri0 = -1;
+            for (int j = 0; j < nq && ri0 < 0; ++j)
+                if (s_live[j]) ri0 = s_ri[j];
+            if (ri0 >= 0 && ri0 != cache_ri) {
+                const int c4 = p.ldk >> 2;
+                for (int e = threadIdx.x; e < (row_end - row_beg) * c4; e += blockDim.x) {
+                    const int rr = e / c4, q = e - rr * c4;
+                    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(
+                        wc + (size_t)rr * wops + (q >> 2) * kStepPad + (q & 3) * 4));
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                                 "l"(a.W[ri0] + (size_t)(row_beg + rr) * p.ldk + 4 * q)
+                                 : "memory");
+                }
+                asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+                __syncthreads();
+                cache_ri = ri0;
+            }
+        }
         for (int jl = 0; jl < len; ++jl) {
             const float* Sc = a.S + (size_t)cur * kTailMax * p.ldk;
             p.Sout = a.S + (size_t)(cur ^ 1) * kTailMax * p.ldk;
@@ -246,14 +282,18 @@ __global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a)
             p.flags = jl == len - 1 ? (EPI_LAST | (check ? EPI_CHECK : 0u)) : 0u;
             stage_rows(tsm, ops, Sc, p.ldk, 0, p.ldk, nq, s_live);
             __syncthreads();
-            for (int r0 = gwarp * kRB; r0 < p.R; r0 += nwarps * kRB) {
+            for (int r0 = row_beg + warp * kRB; r0 < row_end; r0 += (kTailThreads / 32) * kRB) {
                 float acc[kRB];
-                warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r0, p.R,
-                          [&](int j, int r) { return a.W[s_ri[j]] + (size_t)r * p.ldk; }, acc);
+                warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r0, row_end,
+                          [&](int j, int r) {
+                              return s_ri[j] == cache_ri ? WRowRef{wc + (size_t)(r - row_beg) * wops, kStepPad}
+                                                         : WRowRef{a.W[s_ri[j]] + (size_t)r * p.ldk, kStep};
+                          },
+                          acc);
                 if (lane < nq && s_live[lane])
 #pragma unroll
                     for (int i = 0; i < kRB; ++i)
-                        if (r0 + i < p.R) layer_elem(p, lane, a.qlist[lane], s_ri[lane], r0 + i, acc[i]);
+                        if (r0 + i < row_end) layer_elem(p, lane, a.qlist[lane], s_ri[lane], r0 + i, acc[i]);
             }
             cur ^= 1;
             if (!tail_barrier(a, &s_ok)) return;
@@ -276,7 +316,7 @@ __global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a)
                 for (int r0 = gwarp * kRB; r0 < p.n + p.m; r0 += nwarps * kRB) {
                     float acc[kRB];
                     warp_rows(tsm, ops, pb, nq, s_live, 0, p.n64 / kStep, r0, p.n + p.m,
-                              [&](int, int r) { return a.Wc + (size_t)r * p.ldkc; }, acc);
+                              [&](int, int r) { return WRowRef{a.Wc + (size_t)r * p.ldkc, kStep}; }, acc);
                     if (lane < nq && s_live[lane])
 #pragma unroll
                         for (int i = 0; i < kRB; ++i)
@@ -303,7 +343,7 @@ __global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a)
                 for (int r0 = gwarp * kRB; r0 < p.n; r0 += nwarps * kRB) {
                     float acc[kRB];
                     warp_rows(tsm, ops, pb, nq, s_live, p.n64 / kStep, p.ldkc / kStep, r0, p.n,
-                              [&](int, int r) { return a.Wc + (size_t)r * p.ldkc; }, acc);
+                              [&](int, int r) { return WRowRef{a.Wc + (size_t)r * p.ldkc, kStep}; }, acc);
                     if (lane < nq && s_live[lane])
 #pragma unroll
                         for (int i = 0; i < kRB; ++i)
@@ -392,9 +432,12 @@ __global__ void tail_list_kernel(int B, const int* __restrict__ status, int* lis
 }
 
 // staged operands [kTailMax][steps][kStepPad] + per-warp round partials [8][kRB][kTailMax][kPbs]
-size_t tail_smem(const BatchWork& w) {
+// (+ the cached Wt rows [rows][ldk steps][kStepPad])
+size_t tail_smem(const BatchWork& w, int cached_rows) {
     const size_t steps = (size_t)std::max(w.ldk, w.ldkc) / kStep;
-    return ((size_t)kTailMax * steps * kStepPad + (size_t)(kTailThreads / 32) * kRB * kTailMax * kPbs) * sizeof(float);
+    return ((size_t)kTailMax * steps * kStepPad + (size_t)(kTailThreads / 32) * kRB * kTailMax * kPbs +
+            (size_t)cached_rows * (w.ldk / kStep) * kStepPad) *
+           sizeof(float);
 }
 
 }  // namespace
@@ -406,19 +449,33 @@ int batch_tail_alloc(relu_qp_t h) {
     RQ_TRY(alloc(h, &w.TRED, 3 * (size_t)kTailMax * RW_WORDS));
     RQ_TRY(alloc(h, &w.TBAR, 4));
     RQ_TRY(alloc(h, &w.TLIST, kTailMax));
-    const size_t smem = tail_smem(w);
     int smem_max = 0;
     RQ_CUDA(h, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-    if (smem + 1024 > (size_t)smem_max) {   // problem too large for the staged operands: no tail kernel
-        w.tail_grid = 0;
-        return RELU_QP_OK;
-    }
-    RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    w.tail_grid = 0;
+    // one CTA per SM with the CTA's rows of Wt in shared memory when they fit, else two
+    // CTAs per SM reading Wt through L1 (every CTA co-resident: grid barrier)
+    const int rpc1 = ceil_div(h->R, h->num_sms);
+    const size_t smem1 = tail_smem(w, rpc1);
+    const size_t smem2 = tail_smem(w, 0);
     int per_sm = 0;
-    RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem));
-    // every CTA co-resident (grid barrier); two per SM when they fit, so that each warp
-    // takes at most one row of the product
+    if (smem1 + 1024 <= (size_t)smem_max) {
+        RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
+        RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem1));
+        if (per_sm >= 1) {
+            w.tail_grid = h->num_sms;
+            w.tail_rpc = rpc1;
+            w.tail_cache = 1;
+            w.tail_smem = smem1;
+            return RELU_QP_OK;
+        }
+    }
+    if (smem2 + 1024 > (size_t)smem_max) return RELU_QP_OK;   // problem too large: no tail kernel
+    RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+    RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem2));
     w.tail_grid = std::min(per_sm, 2) * h->num_sms;
+    w.tail_rpc = w.tail_grid > 0 ? ceil_div(h->R, w.tail_grid) : 0;
+    w.tail_cache = 0;
+    w.tail_smem = smem2;
     return RELU_QP_OK;
 }
 
@@ -444,10 +501,12 @@ int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, i
     a.it0 = it0;
     a.max_iter = max_iter;
     a.ci = h->opts.check_interval;
+    a.rpc = w.tail_rpc;
+    a.wcache = w.tail_cache;
     a.timeout_ns = 2000000000LL;
     void* args[] = {&a};
     RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)batch_tail_kernel, dim3(w.tail_grid), dim3(kTailThreads), args,
-                                           tail_smem(w), h->stream));
+                                           w.tail_smem, h->stream));
     h->launches += 2;
     return RELU_QP_OK;
 }

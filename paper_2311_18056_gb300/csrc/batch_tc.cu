@@ -57,6 +57,14 @@ struct TcArgs {
 // ---------------------------------------------------------------------------
 // PTX helpers
 // ---------------------------------------------------------------------------
+// a wait gave up: error word err[0], and err[1] = which wait (first one wins)
+enum WaitSite : int {
+    WS_PROD_EMPTY = 1, WS_PROD_SYNC, WS_MMA_FULL, WS_MMA_ACC, WS_EPI_ACC, WS_EPI_RECV, WS_DRAIN_READY, WS_DRAIN_FREE
+};
+__device__ __forceinline__ void wait_failed(int* err, int site) {
+    atomicCAS(err + 1, 0, site);
+    atomicExch(err, RELU_QP_ERR_TIMEOUT);
+}
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -256,15 +264,40 @@ struct TcSmem {
 // stages are requested before griddep_wait, i.e. while the previous kernel of
 // the stream may still run; the operand tiles (A), which that kernel writes,
 // only after it.
+// Operand tiles of the slot groups in use: the active QPs of a tile fill its
+// slots from the first one on, so the 32-slot groups with work are a prefix
+// (bit g of gmask); a full tile takes one 128-row box, a partial one a 32-row
+// box per group.  Rows of idle groups keep stale values; their MMA rows only
+// feed the outputs of empty slots, which the epilogue discards.
+template <int NA>
+__device__ __forceinline__ void load_operand(const CUtensorMap* tmA, const CUtensorMap* tmA32, uint32_t st, int k0,
+                                             const int (&arow)[3], unsigned gmask, uint32_t full) {
+    if (gmask == 0xFu) {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) tma_load_2d(st + a * kTileBytesA, tmA, k0, arow[a], full);
+    } else {
+#pragma unroll
+        for (int a = 0; a < NA; ++a)
+            for (int g = 0; g < 4; ++g)
+                if ((gmask >> g) & 1u) tma_load_2d(st + a * kTileBytesA + g * 4096, tmA32, k0, arow[a] + 32 * g, full);
+    }
+}
+
+template <int NA>
+__device__ __forceinline__ uint32_t operand_bytes(unsigned gmask) {
+    return (uint32_t)(NA * __popc(gmask) * 4096);
+}
+
 template <int NA, int NB, int BN, int STAGES, int KSTAGE, int KA>
-__device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sbase, uint32_t bar0,
-                                     int nkb, int koff, int a0, int a1, int a2, int b0, int b1, int b2,
-                                     int& issued) {
+__device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* tmA32, const CUtensorMap* tmB,
+                                     uint32_t sbase, uint32_t bar0, int nkb, int koff, int a0, int a1, int a2, int b0,
+                                     int b1, int b2, unsigned gmask, int& issued) {
     const int arow[3] = {a0, a1, a2}, brow[3] = {b0, b1, b2};
+    const uint32_t tx = (uint32_t)(KSTAGE - KA) + operand_bytes<NA>(gmask);
     const int pre = nkb < STAGES ? nkb : STAGES;   // stages start empty
     for (int kb = 0; kb < pre; ++kb) {
         const uint32_t full = bar0 + 8 * kb;
-        mbar_expect_tx(full, KSTAGE);
+        mbar_expect_tx(full, tx);
         const uint32_t st = sbase + kb * KSTAGE;
 #pragma unroll
         for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, kb * kBK + koff, brow[b], full);
@@ -278,12 +311,11 @@ __device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* 
         const int k0 = kb * kBK + koff;
         if (kb >= pre) {
             if (!mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) return false;
-            mbar_expect_tx(full, KSTAGE);
+            mbar_expect_tx(full, tx);
 #pragma unroll
             for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
         }
-#pragma unroll
-        for (int a = 0; a < NA; ++a) tma_load_2d(st + a * kTileBytesA, tmA, k0, arow[a], full);
+        load_operand<NA>(tmA, tmA32, st, k0, arow, gmask, full);
         issued = kb + 1;
     }
     return true;
@@ -295,16 +327,18 @@ __device__ __noinline__ bool produce(const CUtensorMap* tmA, const CUtensorMap* 
 // released the previous layer (its counter reached `target`; sync == nullptr:
 // wait for the previous kernel of the stream instead).
 template <int NB, int BN, int STAGES, int KSTAGE, int KA>
-__device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtensorMap* tmB, uint32_t sbase,
-                                           uint32_t bar0, int nkb, int koff, int g0, int a0, int a1, int b0, int b1,
-                                           const unsigned* sync, unsigned target, int& issued) {
-    const int brow[2] = {b0, b1}, arow[2] = {a0, a1};
+__device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtensorMap* tmA32, const CUtensorMap* tmB,
+                                           uint32_t sbase, uint32_t bar0, int nkb, int koff, int g0, int a0, int a1,
+                                           int b0, int b1, unsigned gmask, const unsigned* sync, unsigned target,
+                                           int& issued, bool& sync_failed) {
+    const int brow[2] = {b0, b1}, arow[3] = {a0, a1, 0};
+    const uint32_t tx = (uint32_t)(KSTAGE - KA) + operand_bytes<2>(gmask);
     const int pre = nkb < STAGES ? nkb : STAGES;
     for (int kb = 0; kb < pre; ++kb) {
         const int gk = g0 + kb, s = gk % STAGES;
         if (!mbar_wait(bar0 + 8 * (STAGES + s), ((gk / STAGES) & 1) ^ 1)) return false;
         const uint32_t full = bar0 + 8 * s;
-        mbar_expect_tx(full, KSTAGE);
+        mbar_expect_tx(full, tx);
 #pragma unroll
         for (int b = 0; b < NB; ++b)
             tma_load_2d(sbase + s * KSTAGE + KA + b * BN * 128, tmB, kb * kBK + koff, brow[b], full);
@@ -315,7 +349,10 @@ __device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtenso
             unsigned v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sync) : "memory");
             if (v >= target) break;
-            if (gtime() - t0 > kWaitNs) return false;
+            if (gtime() - t0 > kWaitNs) {
+                sync_failed = true;
+                return false;
+            }
             __nanosleep(64);
         }
         // the operand was written by generic stores of other CTAs; order them before the TMA reads
@@ -330,12 +367,11 @@ __device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtenso
         const int k0 = kb * kBK + koff;
         if (kb >= pre) {
             if (!mbar_wait(bar0 + 8 * (STAGES + s), ((gk / STAGES) & 1) ^ 1)) return false;
-            mbar_expect_tx(full, KSTAGE);
+            mbar_expect_tx(full, tx);
 #pragma unroll
             for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
         }
-#pragma unroll
-        for (int a = 0; a < 2; ++a) tma_load_2d(st + a * kTileBytesA, tmA, k0, arow[a], full);
+        load_operand<2>(tmA, tmA32, st, k0, arow, gmask, full);
         issued = gk + 1;
     }
     return true;
@@ -573,11 +609,11 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
         got = __shfl_sync(0xffffffffu, got, 0);
         if (got) got = mbar_wait_cluster(bar_recv, par_recv, 0);
         got = __all_sync(0xffffffffu, got);
-        if (!got && ready && lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); *s_fail = 1; }
+        if (!got && ready && lane == 0) { wait_failed(g.err, WS_EPI_RECV); *s_fail = 1; }
         ready = ready && got;
     }
     if (!ready) {
-        if (lane == 0) { atomicExch(g.err, RELU_QP_ERR_TIMEOUT); *s_fail = 1; }
+        if (lane == 0) { wait_failed(g.err, DRAIN ? WS_DRAIN_READY : WS_EPI_ACC); *s_fail = 1; }
     } else {
         float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
         float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
@@ -683,13 +719,13 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
 // into KS fixed ranges; after its main loop each CTA sends every partner the
 // partial sums of that partner's BN / KS columns (into the partner's shared
 // memory) and finalises its own columns, adding the KS partial sums in rank
-// order.  The ranges and the order depend only on the problem (never on the
-// batch size or the tile width), so a QP's arithmetic does not depend on its
-// batch.
+// order.  The ranges and the order depend only on the problem and KS; the tuner
+// picks KS per number of active slot tiles, so in the BF16 split form a QP's
+// rounding may depend on the size of its batch (within the form's tolerance).
 template <int MODE, int BN, int STAGES, int KS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchParams p,
-                   TcArgs g) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA32,
+                   const __grid_constant__ CUtensorMap tmB, BatchParams p, TcArgs g) {
     constexpr int NA = MODE == MODE_LAYER_REFINED ? 2 : 3;
     constexpr int NB = NA;
     constexpr int NPROD = NA == 2 ? 3 : 6;
@@ -765,7 +801,11 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // ------------------------- TMA producer -------------------------
         if (lane == 0) {
             prefetch_map(&tmA);
+            prefetch_map(&tmA32);
             prefetch_map(&tmB);
+            unsigned gmask = 0;
+            for (int gr = 0; gr < 4; ++gr)
+                if (p.perm[slot0 + 32 * gr] >= 0) gmask |= 1u << gr;
             int arow[3] = {0, 0, 0}, brow[3] = {0, 0, 0};
 #pragma unroll
             for (int a = 0; a < NA; ++a) arow[a] = g.a_row[a] + slot0;
@@ -773,10 +813,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int b = 0; b < NB; ++b) brow[b] = g.b_row[b] + ri * g.b_rho_stride + row0;
             int issued = 0;
             const bool ok = produce<NA, NB, BN, STAGES, L::kStage, L::kA>(
-                &tmA, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK, arow[0], arow[1],
-                arow[2], brow[0], brow[1], brow[2], issued);
+                &tmA, &tmA32, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK, arow[0],
+                arow[1], arow[2], brow[0], brow[1], brow[2], gmask, issued);
             if (!ok) {
-                atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                wait_failed(g.err, WS_PROD_EMPTY);
                 s_fail = 1;
                 // wait (bounded) for the copies already in flight
                 for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
@@ -796,7 +836,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mma_commit(smem_u32(&bars[2 * STAGES]));
             // keep TMEM alive until the MMAs have landed
             if (!mbar_wait(smem_u32(&bars[2 * STAGES]), 0) || !ok) {
-                atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                wait_failed(g.err, ok ? WS_MMA_ACC : WS_MMA_FULL);
                 s_fail = 1;
             }
         }
@@ -828,7 +868,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 // operand pair (j - 1) & 1 and writes pair j & 1 (both written only by the
 // epilogues of the CTAs of the same slot tile): after its epilogue a CTA adds
 // one to the tile's counter, and a producer requests the operand of layer j
-// only once the counter shows every CTA of the tile done with layer j - 1.
+// only once the counter shows every CTA of the tile done with layer j - 1.  The
+// counters start at zero and the tile's last CTA puts them back to zero at the
+// end (launches are in stream order, without programmatic overlap).
 // That also orders the reuse of TMEM and of the receive buffers (a partner
 // sends layer j's partial sums only after all of layer j - 1 is done).  The
 // CTAs of a tile must be co-resident: the host launches it only when the grid
@@ -841,13 +883,15 @@ struct ChunkArgs {
     __nv_bfloat16* OP;         // operand parts: pair 0 = parts 0, 1; pair 1 = parts 2, 3
     size_t opart;              // elements per part
     int slots;                 // rows per part in the operand tensor map
-    unsigned* sync;            // per slot tile: CTAs done with layers so far (zero at launch)
+    unsigned* sync;            // per slot tile: CTAs done with layers so far (zero at launch), then
+                               // at sync + done_off the CTAs done with the whole launch
+    int done_off;
 };
 
 template <int BN, int STAGES, int KS>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-    tc_chunk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, BatchParams p,
-                    TcArgs g, ChunkArgs c) {
+    tc_chunk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA32,
+                    const __grid_constant__ CUtensorMap tmB, BatchParams p, TcArgs g, ChunkArgs c) {
     constexpr int TCOLS = tmem_cols(2 * BN);
     constexpr int OWN = BN / KS;
     constexpr int HALVES = OWN >= 32 ? 2 : 1;
@@ -875,7 +919,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float* xpose = reinterpret_cast<float*>(smem + STAGES * L::kStage);
     float* recv = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+    // bars[2S] accumulator ready, bars[2S+1] partners' partial sums received,
+    // bars[2S+2] accumulator consumed (the epilogue warps read all of a layer's TMEM)
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
     int& s_fail = *reinterpret_cast<int*>(tmem_holder + 1);   // in the dynamic area: no static shared memory
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -886,6 +932,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         }
         mbar_init(smem_u32(&bars[2 * STAGES]), 1);
         mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * HALVES);
+        mbar_init(smem_u32(&bars[2 * STAGES + 2]), 4 * HALVES);   // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -906,18 +953,23 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         // ------------------------- TMA producer -------------------------
         if (lane == 0) {
             prefetch_map(&tmA);
+            prefetch_map(&tmA32);
             prefetch_map(&tmB);
+            unsigned gmask = 0;
+            for (int gr = 0; gr < 4; ++gr)
+                if (p.perm[slot0 + 32 * gr] >= 0) gmask |= 1u << gr;
             const int b0 = g.b_row[0] + ri * g.b_rho_stride + row0, b1 = g.b_row[1] + ri * g.b_rho_stride + row0;
             int issued = 0;
+            bool sync_failed = false;
             for (int j = 1; j <= c.nl; ++j) {
                 if (*(volatile int*)&s_fail) break;
                 const int a0 = 2 * ((j - 1) & 1) * c.slots + slot0;
                 const bool ok = produce_layer<2, BN, STAGES, L::kStage, L::kA>(
-                    &tmA, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK,
-                    (j - 1) * kb_count, a0, a0 + c.slots, b0, b1, j == 1 ? nullptr : c.sync + tile,
-                    (unsigned)(j - 1) * nct, issued);
+                    &tmA, &tmA32, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK,
+                    (j - 1) * kb_count, a0, a0 + c.slots, b0, b1, gmask, j == 1 ? nullptr : c.sync + tile,
+                    (unsigned)(j - 1) * nct, issued, sync_failed);
                 if (!ok) {
-                    atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                    wait_failed(g.err, sync_failed ? WS_PROD_SYNC : WS_PROD_EMPTY);
                     s_fail = 1;
                     break;
                 }
@@ -932,20 +984,29 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             int commits = 0;
             for (int j = 1; j <= c.nl; ++j) {
                 if (*(volatile int*)&s_fail) break;
+                // the accumulators of layer j - 1 must have been read by every epilogue
+                // warp before layer j writes them (this also keeps the ready barrier
+                // from completing a phase the epilogue has not seen)
+                if (j > 1 && !mbar_wait(smem_u32(&bars[2 * STAGES + 2]), (uint32_t)((j - 2) & 1))) {
+                    wait_failed(g.err, WS_MMA_ACC);
+                    s_fail = 1;
+                    break;
+                }
+                fence_after();
                 const bool ok = issue_layer<BN, STAGES, L::kStage, L::kA>(smem_u32(smem), smem_u32(bars), tmem,
                                                                         kb_count, (j - 1) * kb_count);
                 // committed also after a failure, so that the MMAs already issued are waited for
                 mma_commit(smem_u32(&bars[2 * STAGES]));
                 ++commits;
                 if (!ok) {
-                    atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                    wait_failed(g.err, WS_MMA_FULL);
                     s_fail = 1;
                     break;
                 }
             }
             // keep TMEM alive until the last MMAs have landed
             if (commits > 0 && !mbar_wait(smem_u32(&bars[2 * STAGES]), (commits - 1) & 1)) {
-                atomicExch(g.err, RELU_QP_ERR_TIMEOUT);
+                wait_failed(g.err, WS_MMA_ACC);
                 s_fail = 1;
             }
         }
@@ -963,6 +1024,10 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                                                       smem_u32(&bars[2 * STAGES]), (uint32_t)((j - 1) & 1),
                                                       smem_u32(&bars[2 * STAGES + 1]), (uint32_t)((j - 1) & 1),
                                                       &s_fail);
+            // this warp has read all of layer j's accumulators
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars[2 * STAGES + 2]));
             // release this CTA's part of layer j: its operand and state stores, then
             // its TMEM reads, before the tile's counter moves on
             asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -980,7 +1045,17 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             if (any) break;
             if (warp == 2 && lane == 0) {
                 __threadfence();
-                asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c.sync + tile) : "memory");
+                if (j < c.nl) {
+                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c.sync + tile) : "memory");
+                } else {
+                    // after the last layer nobody waits on the counter: the tile's last CTA
+                    // to get here puts it (and the done count) back to zero for the next launch
+                    const unsigned done = atomicAdd(c.sync + c.done_off + tile, 1u) + 1u;
+                    if (done == nct) {
+                        atomicExch(c.sync + tile, 0u);
+                        atomicExch(c.sync + c.done_off + tile, 0u);
+                    }
+                }
             }
         }
     }
@@ -1000,8 +1075,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// tile widths (rows of Wt per CTA) of the refined layer; the 3-part modes use 64 or 128
-constexpr int kLayerBN[] = {32, 64, 96, 128, 160, 192, 256};
+// tile widths (rows of Wt per CTA) of the refined layer; the 3-part modes use 64
+constexpr int kLayerBN[] = {16, 32, 64, 96, 128, 160, 192, 256};
 constexpr int kNumLayerBN = sizeof(kLayerBN) / sizeof(int);
 
 int bn_index(int bn) {
@@ -1012,13 +1087,12 @@ int bn_index(int bn) {
 
 struct TcState {
     EncodeTiledFn encode = nullptr;
-    int bn_layer = 128, bn_check = 128;
-    std::vector<int> bn_by_tiles;        // refined-layer width per number of active slot tiles
-    int ks = 1;                          // K split of the refined layer (fixed per handle by the tuner)
+    LayerCfg cfg{1, 128};                // refined layer: K split and width when no table is set
+    std::vector<LayerCfg> cfg_by_tiles;  // [t] = the tuned configuration for t active slot tiles
     bool chunk_ok = true;                // persistent chunk kernel usable (cleared after a refused launch)
     int* err = nullptr;                  // = counters + CNT_ERR
     // encoded maps, keyed by box rows
-    CUtensorMap opnd_map, ck_map;
+    CUtensorMap opnd_map[2], ck_map[2];  // operand tensors, boxes of 128 and of 32 slot rows
     CUtensorMap wb_map[kNumLayerBN];     // weights, box rows kLayerBN[i]
     CUtensorMap wcb_map[2];              // check matrix, box rows 64 and 128
 };
@@ -1047,7 +1121,7 @@ constexpr int stages_for() {
 // set-up and first weight loads overlap the end of the previous kernel in the
 // stream (the kernel waits for that kernel's results before it touches them)
 template <int MODE, int BN, int KS>
-int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
+int launch_tc(relu_qp_t h, const CUtensorMap* a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
               int tiles, bool pdl) {
     constexpr int S = stages_for<MODE, BN, KS>();
     static_assert(S >= 2, "not enough shared memory for two stages");
@@ -1076,12 +1150,12 @@ int launch_tc(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const Bat
     }
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    RQ_CUDA(h, cudaLaunchKernelEx(&cfg, kern, a, b, p, g));
+    RQ_CUDA(h, cudaLaunchKernelEx(&cfg, kern, a[0], a[1], b, p, g));
     return RELU_QP_OK;
 }
 
 template <int BN, int KS>
-int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
+int launch_chunk(relu_qp_t h, const CUtensorMap* a, const CUtensorMap& b, const BatchParams& p, const TcArgs& g,
                  const ChunkArgs& c, int tiles_y) {
     constexpr int S = stages_for<MODE_LAYER_REFINED, BN, KS>();
     using L = TcSmem<2, 2, BN, S, KS>;
@@ -1092,7 +1166,7 @@ int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const 
     cfg.blockDim = dim3(kThreadsTC);
     cfg.dynamicSmemBytes = L::kBytes;
     cfg.stream = h->stream;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     int na = 0;
     if (KS > 1) {
         attr[na].id = cudaLaunchAttributeClusterDimension;
@@ -1101,12 +1175,11 @@ int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const 
         attr[na].val.clusterDim.z = 1;
         ++na;
     }
-    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[na].val.programmaticStreamSerializationAllowed = 1;
-    ++na;
+    // no programmatic dependent launch: the layer counters must be at zero (stream
+    // order after the previous launch and the host's reset) before any CTA starts
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, b, p, g, c);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a[0], a[1], b, p, g, c);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return RELU_QP_ERR_UNSUPPORTED;     // the caller falls back to one launch per layer
@@ -1114,25 +1187,33 @@ int launch_chunk(relu_qp_t h, const CUtensorMap& a, const CUtensorMap& b, const 
     return RELU_QP_OK;
 }
 
+// (K split, width) pairs the persistent chunk kernel is built for
+bool chunk_has(int ks, int bn) {
+    if (ks == 4) return bn == 64 || bn == 128;
+    if (ks == 2) return bn == 64 || bn == 128 || bn == 192;
+    return ks == 1 && (bn == 16 || bn == 32 || bn == 64 || bn == 96 || bn == 128);
+}
+
 int dispatch_chunk(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
-                   const CUtensorMap& a, const ChunkArgs& c, int tiles_y) {
+                   const CUtensorMap* a, const ChunkArgs& c, int tiles_y) {
     if (ks == 4) {
         switch (bn) {
-            case 64: return launch_chunk<64, 4>(h, a, wmaps[1], p, g, c, tiles_y);
-            case 128: return launch_chunk<128, 4>(h, a, wmaps[3], p, g, c, tiles_y);
+            case 64: return launch_chunk<64, 4>(h, a, wmaps[2], p, g, c, tiles_y);
+            case 128: return launch_chunk<128, 4>(h, a, wmaps[4], p, g, c, tiles_y);
         }
     } else if (ks == 2) {
         switch (bn) {
-            case 64: return launch_chunk<64, 2>(h, a, wmaps[1], p, g, c, tiles_y);
-            case 128: return launch_chunk<128, 2>(h, a, wmaps[3], p, g, c, tiles_y);
-            case 192: return launch_chunk<192, 2>(h, a, wmaps[5], p, g, c, tiles_y);
+            case 64: return launch_chunk<64, 2>(h, a, wmaps[2], p, g, c, tiles_y);
+            case 128: return launch_chunk<128, 2>(h, a, wmaps[4], p, g, c, tiles_y);
+            case 192: return launch_chunk<192, 2>(h, a, wmaps[6], p, g, c, tiles_y);
         }
     } else {
         switch (bn) {
-            case 64: return launch_chunk<64, 1>(h, a, wmaps[1], p, g, c, tiles_y);
-            case 128: return launch_chunk<128, 1>(h, a, wmaps[3], p, g, c, tiles_y);
-            case 192: return launch_chunk<192, 1>(h, a, wmaps[5], p, g, c, tiles_y);
-            case 256: return launch_chunk<256, 1>(h, a, wmaps[6], p, g, c, tiles_y);
+            case 16: return launch_chunk<16, 1>(h, a, wmaps[0], p, g, c, tiles_y);
+            case 32: return launch_chunk<32, 1>(h, a, wmaps[1], p, g, c, tiles_y);
+            case 64: return launch_chunk<64, 1>(h, a, wmaps[2], p, g, c, tiles_y);
+            case 96: return launch_chunk<96, 1>(h, a, wmaps[3], p, g, c, tiles_y);
+            case 128: return launch_chunk<128, 1>(h, a, wmaps[4], p, g, c, tiles_y);
         }
     }
     return RELU_QP_ERR_UNSUPPORTED;
@@ -1143,31 +1224,32 @@ int dispatch_chunk(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const 
 // buffers), KS = 2 takes 64, 128 and 192 (BN = 256 would not leave room for
 // the receive buffer), KS = 1 any width of kLayerBN (BN / 2 columns per warp).
 int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const BatchParams& p, const TcArgs& g,
-                     const CUtensorMap& a, int tiles, bool pdl) {
+                     const CUtensorMap* a, int tiles, bool pdl) {
     constexpr int M = MODE_LAYER_REFINED;
     if (ks == 4) {
         switch (bn) {
-            case 64: return launch_tc<M, 64, 4>(h, a, wmaps[1], p, g, tiles, pdl);
-            case 128: return launch_tc<M, 128, 4>(h, a, wmaps[3], p, g, tiles, pdl);
+            case 64: return launch_tc<M, 64, 4>(h, a, wmaps[2], p, g, tiles, pdl);
+            case 128: return launch_tc<M, 128, 4>(h, a, wmaps[4], p, g, tiles, pdl);
             default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
         }
     }
     if (ks == 2) {
         switch (bn) {
-            case 64: return launch_tc<M, 64, 2>(h, a, wmaps[1], p, g, tiles, pdl);
-            case 128: return launch_tc<M, 128, 2>(h, a, wmaps[3], p, g, tiles, pdl);
-            case 192: return launch_tc<M, 192, 2>(h, a, wmaps[5], p, g, tiles, pdl);
+            case 64: return launch_tc<M, 64, 2>(h, a, wmaps[2], p, g, tiles, pdl);
+            case 128: return launch_tc<M, 128, 2>(h, a, wmaps[4], p, g, tiles, pdl);
+            case 192: return launch_tc<M, 192, 2>(h, a, wmaps[6], p, g, tiles, pdl);
             default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
         }
     }
     switch (bn) {
-        case 32: return launch_tc<M, 32, 1>(h, a, wmaps[0], p, g, tiles, pdl);
-        case 64: return launch_tc<M, 64, 1>(h, a, wmaps[1], p, g, tiles, pdl);
-        case 96: return launch_tc<M, 96, 1>(h, a, wmaps[2], p, g, tiles, pdl);
-        case 128: return launch_tc<M, 128, 1>(h, a, wmaps[3], p, g, tiles, pdl);
-        case 160: return launch_tc<M, 160, 1>(h, a, wmaps[4], p, g, tiles, pdl);
-        case 192: return launch_tc<M, 192, 1>(h, a, wmaps[5], p, g, tiles, pdl);
-        case 256: return launch_tc<M, 256, 1>(h, a, wmaps[6], p, g, tiles, pdl);
+        case 16: return launch_tc<M, 16, 1>(h, a, wmaps[0], p, g, tiles, pdl);
+        case 32: return launch_tc<M, 32, 1>(h, a, wmaps[1], p, g, tiles, pdl);
+        case 64: return launch_tc<M, 64, 1>(h, a, wmaps[2], p, g, tiles, pdl);
+        case 96: return launch_tc<M, 96, 1>(h, a, wmaps[3], p, g, tiles, pdl);
+        case 128: return launch_tc<M, 128, 1>(h, a, wmaps[4], p, g, tiles, pdl);
+        case 160: return launch_tc<M, 160, 1>(h, a, wmaps[5], p, g, tiles, pdl);
+        case 192: return launch_tc<M, 192, 1>(h, a, wmaps[6], p, g, tiles, pdl);
+        case 256: return launch_tc<M, 256, 1>(h, a, wmaps[7], p, g, tiles, pdl);
         default: return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width " + std::to_string(bn));
     }
 }
@@ -1175,7 +1257,7 @@ int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, cons
 // 3-part modes: b64 / b128 are the maps with 64- and 128-row boxes
 template <int MODE>
 int dispatch_3part(relu_qp_t h, int bn, const CUtensorMap& b64, const CUtensorMap& b128, const BatchParams& p,
-                   const TcArgs& g, const CUtensorMap& a, int tiles) {
+                   const TcArgs& g, const CUtensorMap* a, int tiles) {
     // the drained accumulation keeps FP32 sums of BN / 2 columns per epilogue warp in
     // shared memory: BN = 64 leaves room for two pipeline stages
     (void)bn;
@@ -1197,11 +1279,11 @@ int tc_prepare(relu_qp_t h) {
         return fail(h, RELU_QP_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled is not available");
     st->encode = reinterpret_cast<EncodeTiledFn>(fn);
     st->err = w.counters + CNT_ERR;
-    // the K split is a property of the problem (never of the batch size); tc_tune
-    // may switch it between the splits the problem allows before the first solve
-    st->ks = w.ldk / kBK >= 2 ? 2 : 1;
-    RQ_TRY(encode_2d(h, st, &st->opnd_map, w.OPND, 7ull * w.slots, w.ldk, kSlotTile));
-    RQ_TRY(encode_2d(h, st, &st->ck_map, w.CK, 3ull * w.slots, w.ldkc, kSlotTile));
+    st->cfg = LayerCfg{w.ldk / kBK >= 4 ? 2 : 1, w.ldk / kBK >= 4 ? 128 : 64};
+    for (int i = 0; i < 2; ++i) {
+        RQ_TRY(encode_2d(h, st, &st->opnd_map[i], w.OPND, 7ull * w.slots, w.ldk, i == 0 ? kSlotTile : 32));
+        RQ_TRY(encode_2d(h, st, &st->ck_map[i], w.CK, 3ull * w.slots, w.ldkc, i == 0 ? kSlotTile : 32));
+    }
     for (int i = 0; i < kNumLayerBN; ++i)
         RQ_TRY(encode_2d(h, st, &st->wb_map[i], w.WB, (uint64_t)h->nr * 3 * w.Rpad, w.ldk, kLayerBN[i]));
     for (int i = 0; i < 2; ++i)
@@ -1214,54 +1296,44 @@ void tc_release(relu_qp_t h) {
     h->bw.tc = nullptr;
 }
 
-bool width_ok(const TcState* st, int bn) {
-    if (st->ks == 4) return bn == 64 || bn == 128;
-    return st->ks == 2 ? (bn == 64 || bn == 128 || bn == 192) : bn_index(bn) >= 0;
-}
-
-// K splits the problem allows: every rank of a split needs at least two k-blocks
-int tc_splits(relu_qp_t h, int* out, int cap) {
+// (K split, width) pairs of the refined layer: a split needs two k-blocks per rank;
+// KS = 4 takes widths 64 and 128 (each CTA finalises 16 or 32 columns, and wider
+// tiles leave no room for the receive buffers), KS = 2 takes 64, 128 and 192, no
+// split any width of kLayerBN
+bool cfg_ok(relu_qp_t h, LayerCfg c) {
     const int nkb = h->bw.ldk / kBK;
-    int k = 0;
+    if (c.ks == 4) return nkb >= 8 && (c.bn == 64 || c.bn == 128);
+    if (c.ks == 2) return nkb >= 4 && (c.bn == 64 || c.bn == 128 || c.bn == 192);
+    return c.ks == 1 && bn_index(c.bn) >= 0;
+}
+
+int tc_layer_cfgs(relu_qp_t h, std::vector<LayerCfg>& out) {
+    out.clear();
     for (int ks : {1, 2, 4})
-        if ((ks == 1 || nkb >= 2 * ks) && k < cap) out[k++] = ks;
-    return k;
+        for (int i = 0; i < kNumLayerBN; ++i)
+            if (cfg_ok(h, LayerCfg{ks, kLayerBN[i]})) out.push_back(LayerCfg{ks, kLayerBN[i]});
+    return (int)out.size();
 }
 
-int tc_set_split(relu_qp_t h, int ks) {
+int tc_set_layer_cfg(relu_qp_t h, LayerCfg c) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
-    if (ks != 1 && ks != 2 && ks != 4) return fail(h, RELU_QP_ERR_INVALID, "unsupported K split");
-    st->ks = ks;
-    st->bn_layer = ks == 1 ? 128 : 64;
-    st->bn_by_tiles.clear();
+    if (!cfg_ok(h, c)) return fail(h, RELU_QP_ERR_INVALID, "unsupported refined-layer configuration");
+    st->cfg = c;
+    st->cfg_by_tiles.clear();
     return RELU_QP_OK;
 }
 
-int tc_split(relu_qp_t h) { return static_cast<const TcState*>(h->bw.tc)->ks; }
-
-int tc_set_tiles(relu_qp_t h, int bn_layer, int bn_check) {
+int tc_set_layer_table(relu_qp_t h, const std::vector<LayerCfg>& by_tiles) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
-    if (!width_ok(st, bn_layer)) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
-    st->bn_layer = bn_layer;
-    st->bn_check = bn_check;
-    st->bn_by_tiles.clear();
+    for (size_t t = 1; t < by_tiles.size(); ++t)
+        if (!cfg_ok(h, by_tiles[t])) return fail(h, RELU_QP_ERR_INVALID, "unsupported refined-layer configuration");
+    st->cfg_by_tiles = by_tiles;
     return RELU_QP_OK;
 }
 
-int tc_set_tiles_for(relu_qp_t h, const std::vector<int>& bn_by_tiles) {
-    TcState* st = static_cast<TcState*>(h->bw.tc);
-    for (size_t t = 1; t < bn_by_tiles.size(); ++t)
-        if (!width_ok(st, bn_by_tiles[t])) return fail(h, RELU_QP_ERR_INVALID, "unsupported tile width");
-    st->bn_by_tiles = bn_by_tiles;
-    return RELU_QP_OK;
-}
-
-int tc_layer_widths(relu_qp_t h, int* out, int cap) {
-    const TcState* st = static_cast<const TcState*>(h->bw.tc);
-    int k = 0;
-    for (int i = 0; i < kNumLayerBN; ++i)
-        if (width_ok(st, kLayerBN[i]) && k < cap) out[k++] = kLayerBN[i];
-    return k;
+LayerCfg cfg_for(const TcState* st, int active_tiles) {
+    if (st->cfg_by_tiles.empty()) return st->cfg;
+    return st->cfg_by_tiles[std::max(1, std::min<int>(active_tiles, (int)st->cfg_by_tiles.size() - 1))];
 }
 
 int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles, bool pdl) {
@@ -1273,30 +1345,27 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int 
     g.err = st->err;
     g.b_rho_stride = 3 * w.Rpad;
     for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
-    // the width tuned for this many active slot tiles (narrower ones give the
-    // convergence tail more CTAs)
-    int bn = st->bn_layer;
-    if (!st->bn_by_tiles.empty())
-        bn = st->bn_by_tiles[std::max(1, std::min<int>(active_tiles, (int)st->bn_by_tiles.size() - 1))];
     if (operand_set < 0) {   // accurate: s1, s2, s3 are parts 4..6
         for (int a = 0; a < 3; ++a) g.a_row[a] = (4 + a) * w.slots;
-        return dispatch_3part<MODE_LAYER_ACCURATE>(h, bn, st->wb_map[1], st->wb_map[3], p, g, st->opnd_map, tiles);
+        return dispatch_3part<MODE_LAYER_ACCURATE>(h, 64, st->wb_map[2], st->wb_map[4], p, g, st->opnd_map, tiles);
     }
+    // the configuration tuned for this many active slot tiles
+    const LayerCfg c = cfg_for(st, active_tiles);
     g.a_row[0] = (2 * operand_set) * w.slots;
     g.a_row[1] = (2 * operand_set + 1) * w.slots;
-    return dispatch_refined(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, tiles, pdl);
+    return dispatch_refined(h, c.bn, c.ks, st->wb_map, p, g, st->opnd_map, tiles, pdl);
 }
 
 int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active_tiles) {
     BatchWork& w = h->bw;
     TcState* st = static_cast<TcState*>(w.tc);
     if (!st->chunk_ok || nl < 1 || active_tiles < 1) return RELU_QP_ERR_UNSUPPORTED;
-    int bn = st->bn_layer;
-    if (!st->bn_by_tiles.empty())
-        bn = st->bn_by_tiles[std::max(1, std::min<int>(active_tiles, (int)st->bn_by_tiles.size() - 1))];
+    const LayerCfg lc = cfg_for(st, active_tiles);
+    const int bn = lc.bn;
+    if (!chunk_has(lc.ks, bn)) return RELU_QP_ERR_UNSUPPORTED;
     const int tiles_y = std::min(active_tiles, w.slots / kSlotTile);
     // all CTAs of the active tiles co-resident, one per SM
-    if ((long long)st->ks * ceil_div(h->R, bn) * tiles_y > h->num_sms) return RELU_QP_ERR_UNSUPPORTED;
+    if ((long long)lc.ks * ceil_div(h->R, bn) * tiles_y > h->num_sms) return RELU_QP_ERR_UNSUPPORTED;
     TcArgs g{};
     g.num_kb = w.ldk / kBK;
     g.rows = h->R;
@@ -1310,7 +1379,8 @@ int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int
     c.opart = (size_t)w.slots * w.ldk;
     c.slots = w.slots;
     c.sync = w.chunk_sync;
-    const int rc = dispatch_chunk(h, bn, st->ks, st->wb_map, p, g, st->opnd_map, c, tiles_y);
+    c.done_off = w.slots / kSlotTile;
+    const int rc = dispatch_chunk(h, bn, lc.ks, st->wb_map, p, g, st->opnd_map, c, tiles_y);
     if (rc == RELU_QP_ERR_UNSUPPORTED) st->chunk_ok = false;   // launch refused: not again for this handle
     return rc;
 }
@@ -1331,17 +1401,18 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
         g.b_row[a] = a * w.npad;
     }
     if (phase == 1)
-        return dispatch_3part<MODE_CHECK1>(h, st->bn_check, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
-    return dispatch_3part<MODE_CHECK2>(h, st->bn_check, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
+        return dispatch_3part<MODE_CHECK1>(h, 64, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
+    return dispatch_3part<MODE_CHECK2>(h, 64, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
 }
 
-int tc_error(relu_qp_t h) {
+int tc_error(relu_qp_t h, int* site) {
     TcState* st = static_cast<TcState*>(h->bw.tc);
     if (!st) return 0;
-    int e = 0;
-    cudaMemcpy(&e, st->err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e) cudaMemset(st->err, 0, sizeof(int));
-    return e;
+    int e[2] = {0, 0};
+    cudaMemcpy(e, st->err, sizeof(e), cudaMemcpyDeviceToHost);
+    if (e[0]) cudaMemset(st->err, 0, sizeof(e));
+    if (site) *site = e[1];
+    return e[0];
 }
 
 }  // namespace rq

@@ -108,6 +108,8 @@ struct BatchWork {
     unsigned *TRED = nullptr, *TBAR = nullptr;
     int* TLIST = nullptr;
     int tail_grid = 0;                     // CTAs of its cooperative launch (0: unavailable)
+    int tail_rpc = 0, tail_cache = 0;      // rows per CTA; 1 = those rows of Wt cached in shared memory
+    size_t tail_smem = 0;                  // its dynamic shared memory
     unsigned* chunk_sync = nullptr;        // per slot tile: layer counters of the persistent chunk kernel
 };
 
