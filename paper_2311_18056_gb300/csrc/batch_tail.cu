@@ -28,7 +28,7 @@ namespace rq {
 
 namespace {
 
-constexpr int kTailThreads = 256;
+constexpr int kTailThreads = 384;   // 12 warps: one row of the layer each
 
 struct TailArgs {
     BatchParams p;              // state (QP-indexed rows), bank scalars; Sout / CK32 set per phase
@@ -194,7 +194,16 @@ __device__ __forceinline__ void warp_rows(const float* __restrict__ opnd, int op
 #pragma unroll
             for (int i = 0; i < kRB; ++i) {
                 const float* q = pb + (i * kTailMax + lane) * kPbs;
-                for (int l = 0; l < nc; ++l) acc[i] += q[l];
+                if (nc == 32) {
+                    // all loads first, then the additions in step order
+                    float v[32];
+#pragma unroll
+                    for (int l = 0; l < 32; ++l) v[l] = q[l];
+#pragma unroll
+                    for (int l = 0; l < 32; ++l) acc[i] += v[l];
+                } else {
+                    for (int l = 0; l < nc; ++l) acc[i] += q[l];
+                }
             }
         }
         __syncwarp();
@@ -221,7 +230,7 @@ __device__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const 
     }
 }
 
-__global__ void __launch_bounds__(kTailThreads, 2) batch_tail_kernel(TailArgs a) {
+__global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) float tsm[];
     __shared__ int s_ok, s_live[kTailMax], s_ri[kTailMax], s_act[kTailMax], s_nri[kTailMax], s_any;
     __shared__ unsigned s_red[kTailMax][RW_WORDS];
@@ -452,31 +461,25 @@ int batch_tail_alloc(relu_qp_t h) {
     int smem_max = 0;
     RQ_CUDA(h, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     w.tail_grid = 0;
-    // one CTA per SM with the CTA's rows of Wt in shared memory when they fit, else two
-    // CTAs per SM reading Wt through L1 (every CTA co-resident: grid barrier)
-    const int rpc1 = ceil_div(h->R, h->num_sms);
-    const size_t smem1 = tail_smem(w, rpc1);
-    const size_t smem2 = tail_smem(w, 0);
-    int per_sm = 0;
-    if (smem1 + 1024 <= (size_t)smem_max) {
-        RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1));
-        RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem1));
-        if (per_sm >= 1) {
-            w.tail_grid = h->num_sms;
-            w.tail_rpc = rpc1;
-            w.tail_cache = 1;
-            w.tail_smem = smem1;
-            return RELU_QP_OK;
-        }
+    // one CTA per SM and (while the SMs suffice) one row of the layer per warp; the CTA's
+    // rows of Wt cached in shared memory when they fit (every CTA co-resident: grid barrier)
+    constexpr int kWarps = kTailThreads / 32;
+    const int grid = std::min(h->num_sms, ceil_div(h->R, kWarps));
+    const int rpc = ceil_div(h->R, grid);
+    for (int cache = 1; cache >= 0; --cache) {
+        const size_t smem = tail_smem(w, cache ? rpc : 0);
+        if (smem + 1024 > (size_t)smem_max) continue;
+        RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem));
+        if (per_sm < 1) continue;
+        w.tail_grid = grid;
+        w.tail_rpc = rpc;
+        w.tail_cache = cache;
+        w.tail_smem = smem;
+        return RELU_QP_OK;
     }
-    if (smem2 + 1024 > (size_t)smem_max) return RELU_QP_OK;   // problem too large: no tail kernel
-    RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-    RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem2));
-    w.tail_grid = std::min(per_sm, 2) * h->num_sms;
-    w.tail_rpc = w.tail_grid > 0 ? ceil_div(h->R, w.tail_grid) : 0;
-    w.tail_cache = 0;
-    w.tail_smem = smem2;
-    return RELU_QP_OK;
+    return RELU_QP_OK;   // problem too large for the staged operands: no tail kernel
 }
 
 int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, int it0, int max_iter) {
