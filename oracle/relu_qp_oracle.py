@@ -21,6 +21,10 @@ H -> P, g -> q, G -> A, c,d -> l,u, primal y -> x, dual lambda -> lam.
   Scaling Heuristics" (nearest entry of a rho list): ``rho_estimate``,
   ``nearest_rho_index``.
 * Sec. II-B "Warm Starting" and Algorithm 1: ``solve``.
+* Algorithm 1 "Scale problem" and Sec. III-D "Preconditioning" (a modified
+  Ruiz equilibration that, like OSQP, scales the variables and the cost):
+  ``ruiz_scaling``, and ``solve_scaled`` = Algorithm 1 on the scaled problem
+  with the solution mapped back.
 * ``reference_solution``: an accurate optimum (ADMM to 1e-10 then an exact
   equality-constrained KKT solve on the identified active set), used as the
   "converged answer" that GPU results are compared to.
@@ -46,6 +50,14 @@ Readings of points the paper leaves open:
   R7 checks at iterations i with i % check_interval == 0 (i counts from 1).
   R8 cold start v0 = 0; warm start x = x_w, lam = lam_w, z = A x_w.
   R9 the 1e-4 floors of Eq. rho_update are kept as printed.
+  R10 scaling (details unstated in the paper): Ruiz iterations on the
+     infinity norms of the columns of the KKT matrix [[P, A^T], [A, 0]]
+     (norms below 1e-4 are left unscaled, above 1e4 clipped), each followed by
+     a cost scale 1 / max(mean column norm of P, |q|_inf); the scaled problem
+     is min 1/2 xb^T (c D P D) xb + (c D q)^T xb, E l <= (E A D) xb <= E u, with
+     x = D xb, z = zb / E, lam = E lamb / c; the stop test and the penalty rule
+     use the residuals and norms of the original problem at the mapped-back
+     iterate (OSQP's default, unscaled termination).
 """
 from __future__ import annotations
 
@@ -58,7 +70,7 @@ __all__ = [
     "rho_vector", "kkt_matrix", "kkt_inverse", "relu_layer_weights", "relu_layer_step",
     "admm_step_standard", "admm_step_modified", "residuals", "rho_estimate",
     "nearest_rho_index", "solve", "SolveResult", "reference_solution", "brute_force_qp",
-    "kkt_violation", "std_multiplier", "layer_iterates", "admm_iterates",
+    "kkt_violation", "std_multiplier", "layer_iterates", "admm_iterates", "ruiz_scaling", "solve_scaled",
 ]
 
 
@@ -217,14 +229,16 @@ class SolveResult:
 
 def solve(P, q, A, l, u, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), rho0=0.1, eps_abs=1e-3,
           eps_rel=0.0, check_interval=25, max_iter=4000, x_warm=None, lam_warm=None,
-          rho_index_warm=None, eq_scale=1e3, adaptive_rho=True, weights=None):
+          rho_index_warm=None, eq_scale=1e3, adaptive_rho=True, weights=None, residual_fn=None):
     """Algorithm 1 (Sec. III-B) in FP64 with the readings R1-R9.
 
     Offline: W and b operator for every rho in the bank (Eq. gpu_update).
     Online: v <- clamp(W v + b) each iteration; every check_interval
     iterations: residuals (Eqs. primal, dual), convergence test, then the
     penalty rule (Eq. rho_update) and the nearest bank entry.
-    ``weights`` may pass a precomputed list of (W, Bop) per bank entry.
+    ``weights`` may pass a precomputed list of (W, Bop) per bank entry;
+    ``residual_fn(x, z, lam)`` replaces the residuals of this problem (the
+    scaled solve measures them on the original problem, R10).
     """
     P = np.asarray(P, np.float64)
     q = np.asarray(q, np.float64)
@@ -260,7 +274,7 @@ def solve(P, q, A, l, u, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), rho0=0.1, eps_ab
         if check_interval > 0 and it % check_interval == 0:
             x, z, lam_l = v[:n], v[n:n + m], v[n + m:]
             lam = std_multiplier(A, x, z, lam_l, rvecs[ri])
-            res = residuals(P, q, A, x, z, lam)
+            res = residuals(P, q, A, x, z, lam) if residual_fn is None else residual_fn(x, z, lam)
             eps_p = eps_abs + eps_rel * max(res["Ax"], res["z"])
             eps_d = eps_abs + eps_rel * max(res["Px"], res["Atl"], res["q"])
             if res["r_prim"] <= eps_p and res["r_dual"] <= eps_d:
@@ -277,9 +291,68 @@ def solve(P, q, A, l, u, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), rho0=0.1, eps_ab
                     history.append(ri)
     x, z, lam_l = v[:n], v[n:n + m], v[n + m:]
     lam = std_multiplier(A, x, z, lam_l, rvecs[ri])
-    res = residuals(P, q, A, x, z, lam)
+    res = residuals(P, q, A, x, z, lam) if residual_fn is None else residual_fn(x, z, lam)
     return SolveResult(x.copy(), z.copy(), lam, max_iter, "max_iter", ri, res["r_prim"],
                        res["r_dual"], history)
+
+
+def ruiz_scaling(P, A, q, iters=10, norm_min=1e-4, norm_max=1e4):
+    """Modified Ruiz equilibration (Algorithm 1 "Scale problem", Sec. III-D), reading R10.
+
+    Each iteration divides every column of the KKT matrix K = [[P, A^T], [A, 0]]
+    (and, symmetrically, every row) by the square root of its infinity norm,
+    which drives all those norms towards 1, and then rescales the cost so that
+    max(mean column norm of P, |q|_inf) = 1.  Returns (D, E, c, Pb, Ab, qb) with
+    Pb = c D P D, Ab = E A D, qb = c D q (D, E as vectors)."""
+    P = np.asarray(P, np.float64)
+    A = np.asarray(A, np.float64)
+    q = np.asarray(q, np.float64)
+    n, m = P.shape[0], A.shape[0]
+    D, E, c = np.ones(n), np.ones(m), 1.0
+    Pb, Ab, qb = P.copy(), A.copy(), q.copy()
+
+    def inv_sqrt(norms):
+        norms = np.where(norms < norm_min, 1.0, np.minimum(norms, norm_max))
+        return 1.0 / np.sqrt(norms)
+
+    for _ in range(iters):
+        # column j < n of K: column j of P and of A; column n + i: row i of A
+        col_x = np.abs(Pb).max(axis=0)
+        if m:
+            col_x = np.maximum(col_x, np.abs(Ab).max(axis=0))
+        col_z = np.abs(Ab).max(axis=1) if m else np.zeros(0)
+        dx, dz = inv_sqrt(col_x), inv_sqrt(col_z)
+        Pb = dx[:, None] * Pb * dx[None, :]
+        Ab = dz[:, None] * Ab * dx[None, :]
+        qb = dx * qb
+        D, E = D * dx, E * dz
+        cost = max(np.abs(Pb).max(axis=0).mean(), np.abs(qb).max() if n else 0.0)
+        cost = 1.0 if cost < norm_min else min(cost, norm_max)
+        gamma = 1.0 / cost
+        Pb, qb, c = gamma * Pb, gamma * qb, gamma * c
+    return D, E, c, Pb, Ab, qb
+
+
+def solve_scaled(P, q, A, l, u, scaling_iters=10, x_warm=None, lam_warm=None, **kw):
+    """Algorithm 1 with its offline "Scale problem" step (reading R10): solve the
+    equilibrated problem and map x, z, lam back.  The stop test and the penalty
+    rule use the residuals of the original problem at the mapped-back iterate,
+    which are also the ones returned."""
+    P = np.asarray(P, np.float64)
+    A = np.asarray(A, np.float64)
+    q = np.asarray(q, np.float64)
+    D, E, c, Pb, Ab, qb = ruiz_scaling(P, A, q, scaling_iters)
+    lb = E * np.asarray(l, np.float64)
+    ub = E * np.asarray(u, np.float64)
+    xw = None if x_warm is None else np.asarray(x_warm, np.float64) / D
+    lw = None if lam_warm is None else c * np.asarray(lam_warm, np.float64) / E
+
+    def original(xb, zb, lamb):
+        return residuals(P, q, A, D * xb, zb / E, E * lamb / c)
+
+    r = solve(Pb, qb, Ab, lb, ub, x_warm=xw, lam_warm=lw, residual_fn=original, **kw)
+    return SolveResult(D * r.x, r.z / E, E * r.lam / c, r.iters, r.status, r.rho_index, r.r_prim, r.r_dual,
+                       r.rho_history)
 
 
 def layer_iterates(P, q, A, l, u, sigma, rho, iters, x0=None, z0=None, lam0=None, eq_scale=1e3):

@@ -14,7 +14,10 @@ Pins (all CPU):
   * the penalty rule (Eq. rho_update) on cases whose answer is fixed by
     the formula's structure (balanced residuals, scaling, guards, ties);
   * planted mistakes (a flipped sign, a dropped term, a transposed block, a
-    wrong multiplier index) are caught by the pins above.
+    wrong multiplier index) are caught by the pins above;
+  * the scaling step (Algorithm 1 "Scale problem", reading R10): a closed form
+    for diagonal P, the optimum unchanged by the change of variables, the
+    equilibration property, and the unscaled stop test on badly scaled QPs.
 """
 import json
 import math
@@ -312,3 +315,67 @@ def test_planted_index_shift_mistake_is_caught():
     std = O.admm_iterates(P, q, A, l, u, 1e-6, 1.0, 30)
     diff = max(np.max(np.abs(v[n + m:] - s[2])) for v, s in zip(lay, std))
     assert diff > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 "Scale problem": modified Ruiz equilibration (reading R10)
+# ---------------------------------------------------------------------------
+
+def test_ruiz_diagonal_closed_form():
+    """P diagonal, no constraints: one iteration scales every variable by
+    1/sqrt(p_j), making the scaled P the identity before the cost scale
+    c = 1 / max(1, |q / sqrt(p)|_inf)."""
+    p = np.array([4.0, 0.25, 9.0, 1.0])
+    q = np.array([1.0, -3.0, 0.5, 2.0])
+    D, E, c, Pb, Ab, qb = O.ruiz_scaling(np.diag(p), np.zeros((0, 4)), q, iters=1)
+    assert E.size == 0 and Ab.shape == (0, 4)
+    np.testing.assert_allclose(D, 1.0 / np.sqrt(p), rtol=1e-15)
+    c_expected = 1.0 / max(1.0, np.max(np.abs(q / np.sqrt(p))))
+    assert c == pytest.approx(c_expected, rel=1e-15)
+    np.testing.assert_allclose(Pb, c_expected * np.eye(4), atol=1e-15)
+    np.testing.assert_allclose(qb, c_expected * q / np.sqrt(p), rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_ruiz_keeps_the_optimum(seed):
+    """The scaled problem's optimum, mapped back (x = D xb, lam = E lamb / c),
+    is the original problem's optimum: scaling is a change of variables."""
+    from workloads import mpc
+    P, q, A, l, u = mpc.badly_scaled_qp(seed, 14, 9)
+    D, E, c, Pb, Ab, qb = O.ruiz_scaling(P, A, q, iters=10)
+    ref = O.reference_solution(P, q, A, l, u)
+    refb = O.reference_solution(Pb, qb, Ab, E * l, E * u)
+    assert ref["kkt"] < 1e-7 and refb["kkt"] < 1e-7
+    np.testing.assert_allclose(D * refb["x"], ref["x"], atol=1e-7 * (1 + np.abs(ref["x"]).max()))
+    np.testing.assert_allclose(E * refb["lam"] / c, ref["lam"], atol=1e-6 * (1 + np.abs(ref["lam"]).max()))
+
+
+def test_ruiz_equilibrates_the_kkt_matrix():
+    """The iterations drive the infinity norms of the columns of the scaled KKT
+    matrix [[Pb, Ab^T], [Ab, 0]] towards 1: a spread of more than 1000 between
+    the largest and the smallest shrinks below 1.2 in 25 iterations (the cost
+    step rescales P after each one, so the norms approach 1 gradually)."""
+    from workloads import mpc
+    P, q, A, l, u = mpc.badly_scaled_qp(3, 20, 12)
+    before = np.abs(np.block([[P, A.T], [A, np.zeros((12, 12))]])).max(axis=0)
+    D, E, c, Pb, Ab, qb = O.ruiz_scaling(P, A, np.zeros(20), iters=25)
+    K = np.block([[Pb, Ab.T], [Ab, np.zeros((12, 12))]])
+    after = np.abs(K).max(axis=0)
+    assert before.max() / before.min() > 1e3
+    assert after.max() / after.min() < 1.2
+
+
+def test_scaled_solve_meets_the_unscaled_stop_test_and_helps():
+    """Badly scaled QPs: without scaling ADMM does not reach eps = 1e-3 in 4000
+    layers; with it, it stops at a point whose original-problem residuals meet
+    eps and which is within 1e-3 of the optimum."""
+    from workloads import mpc
+    P, q, A, l, u = mpc.badly_scaled_qp(0, 40, 30)
+    plain = O.solve(P, q, A, l, u, eps_abs=1e-3, max_iter=4000)
+    r = O.solve_scaled(P, q, A, l, u, scaling_iters=10, eps_abs=1e-3, max_iter=4000)
+    ref = O.reference_solution(P, q, A, l, u)
+    res = O.residuals(P, q, A, r.x, r.z, r.lam)
+    assert plain.status == "max_iter"
+    assert r.status == "solved" and r.iters < 2000
+    assert res["r_prim"] <= 1e-3 and res["r_dual"] <= 1e-3
+    assert np.max(np.abs(r.x - ref["x"])) <= 1e-3

@@ -318,3 +318,24 @@ def workload(name: str, count: int = 1, x0_std: float | None = None):
 def disturbances(pq: ParametricQP, steps: int, std: float, sub_id: int = 3):
     """Closed-loop process noise w_t ~ N(0, std^2), shape (steps, nx)."""
     return std * rng_for(pq.meta["workload_id"], sub_id).standard_normal((steps, pq.nx))
+
+
+def badly_scaled_qp(seed: int, n: int, m: int):
+    """A dense QP whose variables and constraint rows span three orders of
+    magnitude (row scales r, variable scales s in 10^U[-1.5, 1.5]):
+    P = S (M M^T / n + I) S, A = R N S^{-1}, q = S g, and l <= A x <= u around
+    A x_s with widths proportional to r, so that about half the rows bind.
+    Workload of the scaling tests (Algorithm 1's "Scale problem" step)."""
+    rng = rng_for(90, seed)
+    s = 10.0 ** rng.uniform(-1.5, 1.5, n)
+    M = rng.standard_normal((n, n))
+    P = (s[:, None] * (M @ M.T / n + np.eye(n))) * s[None, :]
+    P = 0.5 * (P + P.T)
+    r = 10.0 ** rng.uniform(-1.5, 1.5, m)
+    A = r[:, None] * rng.standard_normal((m, n)) / s[None, :]
+    q = s * rng.standard_normal(n)
+    xs = rng.standard_normal(n) / s
+    Ax = A @ xs
+    l = Ax - r * rng.uniform(0.1, 1.0, m)
+    u = Ax + r * rng.uniform(0.1, 1.0, m)
+    return P, q, A, l, u
