@@ -67,6 +67,21 @@ typedef struct relu_qp_opts {
     int    max_batch;       /* capacity of batched solves (0: single-QP handle) */
     int    batch_precision; /* RELU_QP_PREC_FP32 or RELU_QP_PREC_BF16X3 */
     void*  stream;          /* cudaStream_t for all work; NULL = the legacy default stream */
+    int    scaling_iters;   /* Algorithm 1 "Scale problem" (Sec. III-D "Preconditioning"):
+                               iterations of the modified Ruiz equilibration done in
+                               FP64 at setup (0 = off, the default; 10 is typical).
+                               The layer bank is built for the scaled problem
+                               min 1/2 xb' (c D P D) xb + (c D q)' xb, E l <= E A D xb <= E u
+                               (D, E diagonal, c > 0: every column of the KKT matrix
+                               [[P, A'], [A, 0]] divided by the square root of its
+                               infinity norm each iteration, then the cost rescaled);
+                               every entry point takes and returns the original
+                               problem's data and iterates (x = D xb, z = zb / E,
+                               lam = E lamb / c), and the stop test, the residuals in
+                               relu_qp_info and the penalty rule use the original
+                               problem's residuals and norms.  relu_qp_get_layer
+                               returns the scaled problem's layer; relu_qp_solve_noalloc
+                               refuses a scaled handle. */
 } relu_qp_opts;
 
 #define RELU_QP_PREC_FP32    0   /* batched layer product in FP32 on the CUDA cores */
@@ -84,7 +99,7 @@ typedef struct relu_qp_info {
 } relu_qp_info;
 
 /* Fill *opts with the defaults above (check 25, adaptive, rho0 0.1, eq 1000,
- * no FP64 copy, single-QP, FP32, default stream). */
+ * no FP64 copy, single-QP, FP32, default stream, no scaling). */
 void relu_qp_default_opts(relu_qp_opts* opts);
 
 /*
@@ -162,7 +177,8 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
  * first call on each device looks the array's device address up
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.
- * Errors: INVALID, UNSUPPORTED (device ordinal >= 64), CUDA, TIMEOUT.
+ * Errors: INVALID, UNSUPPORTED (device ordinal >= 64, or a handle set up with
+ * scaling_iters > 0), CUDA, TIMEOUT.
  */
 int relu_qp_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index_warm,
                           double eps_abs, double eps_rel, int max_iter, float* x_out, float* z_out,

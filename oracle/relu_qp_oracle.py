@@ -333,15 +333,26 @@ def ruiz_scaling(P, A, q, iters=10, norm_min=1e-4, norm_max=1e4):
     return D, E, c, Pb, Ab, qb
 
 
-def solve_scaled(P, q, A, l, u, scaling_iters=10, x_warm=None, lam_warm=None, **kw):
+def solve_scaled(P, q, A, l, u, scaling_iters=10, x_warm=None, lam_warm=None, scaling=None, **kw):
     """Algorithm 1 with its offline "Scale problem" step (reading R10): solve the
     equilibrated problem and map x, z, lam back.  The stop test and the penalty
     rule use the residuals of the original problem at the mapped-back iterate,
-    which are also the ones returned."""
+    which are also the ones returned.
+
+    The scaling step is offline: a parametric problem keeps the (D, E, c) that
+    ruiz_scaling found for the q it was set up with while q, l, u change
+    online.  `scaling` = (D, E, c) applies such a fixed scaling; None computes it
+    from this q."""
     P = np.asarray(P, np.float64)
     A = np.asarray(A, np.float64)
     q = np.asarray(q, np.float64)
-    D, E, c, Pb, Ab, qb = ruiz_scaling(P, A, q, scaling_iters)
+    if scaling is None:
+        D, E, c, Pb, Ab, qb = ruiz_scaling(P, A, q, scaling_iters)
+    else:
+        D, E, c = (np.asarray(scaling[0], np.float64), np.asarray(scaling[1], np.float64), float(scaling[2]))
+        Pb = c * D[:, None] * P * D[None, :]
+        Ab = E[:, None] * A * D[None, :]
+        qb = c * D * q
     lb = E * np.asarray(l, np.float64)
     ub = E * np.asarray(u, np.float64)
     xw = None if x_warm is None else np.asarray(x_warm, np.float64) / D

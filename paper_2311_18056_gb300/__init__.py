@@ -30,7 +30,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class Opts(ctypes.Structure):
     _fields_ = [("check_interval", _c_int), ("adaptive_rho", _c_int), ("rho0", _c_double),
                 ("eq_scale", _c_double), ("keep_fp64", _c_int), ("max_batch", _c_int),
-                ("batch_precision", _c_int), ("stream", _c_void_p)]
+                ("batch_precision", _c_int), ("stream", _c_void_p), ("scaling_iters", _c_int)]
 
 
 class Prof(ctypes.Structure):
@@ -153,7 +153,7 @@ class ReluQP:
 
     def __init__(self, P, A, l, u, q=None, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), *, check_interval=25,
                  adaptive_rho=True, rho0=0.1, eq_scale=1e3, keep_fp64=False, max_batch=0,
-                 precision=PREC_FP32, stream=None):
+                 precision=PREC_FP32, stream=None, scaling_iters=0):
         L = lib()
         P = _f64(P)
         n = P.shape[0]
@@ -173,6 +173,7 @@ class ReluQP:
         o.max_batch = int(max_batch)
         o.batch_precision = int(precision)
         o.stream = _stream_handle(stream)
+        o.scaling_iters = int(scaling_iters)
         h = _c_void_p()
         rc = L.relu_qp_setup(ctypes.byref(h), n, m, _ptr(P), _ptr(q), _ptr(A) if m else None,
                              _ptr(l) if m else None, _ptr(u) if m else None, float(sigma), _ptr(bank),

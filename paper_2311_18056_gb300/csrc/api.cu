@@ -1,6 +1,7 @@
 // C ABI entry points of librelu_qp.so (declared in include/relu_qp.h).
 #include "common.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -30,12 +31,99 @@ std::vector<float> to_f32(const double* p, size_t n) {
     return v;
 }
 
+// Algorithm 1 "Scale problem" (Sec. III-D "Preconditioning"): a modified Ruiz
+// equilibration of the KKT matrix K = [[P, A^T], [A, 0]] in FP64.  Each iteration
+// divides column j of K (and row j, K being symmetric) by the square root of its
+// infinity norm (norms below 1e-4 count as 1, above 1e4 as 1e4) and then divides
+// the cost by max(mean column infinity norm of P, |q|_inf) with the same limits.
+// On return Ps = c D P D and As = E A D (row-major, in place).
+void ruiz_equilibrate(int n, int m, std::vector<double>& Ps, std::vector<double>& As, const std::vector<double>& q,
+                      int iters, std::vector<double>& D, std::vector<double>& E, double& c) {
+    constexpr double kNormMin = 1e-4, kNormMax = 1e4;
+    auto inv_sqrt = [&](double v) { return 1.0 / std::sqrt(v < kNormMin ? 1.0 : std::fmin(v, kNormMax)); };
+    D.assign(n, 1.0);
+    E.assign(m, 1.0);
+    c = 1.0;
+    std::vector<double> qs = q, cx(n), cz(m);
+    for (int it = 0; it < iters; ++it) {
+        std::fill(cx.begin(), cx.end(), 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) cx[j] = std::fmax(cx[j], std::fabs(Ps[(size_t)i * n + j]));
+        for (int i = 0; i < m; ++i) {
+            double r = 0.0;
+            for (int j = 0; j < n; ++j) {
+                const double a = std::fabs(As[(size_t)i * n + j]);
+                cx[j] = std::fmax(cx[j], a);
+                r = std::fmax(r, a);
+            }
+            cz[i] = r;
+        }
+        for (int j = 0; j < n; ++j) cx[j] = inv_sqrt(cx[j]);
+        for (int i = 0; i < m; ++i) cz[i] = inv_sqrt(cz[i]);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) Ps[(size_t)i * n + j] *= cx[i] * cx[j];
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) As[(size_t)i * n + j] *= cz[i] * cx[j];
+        for (int j = 0; j < n; ++j) {
+            qs[j] *= cx[j];
+            D[j] *= cx[j];
+        }
+        for (int i = 0; i < m; ++i) E[i] *= cz[i];
+        // cost scale
+        std::fill(cx.begin(), cx.end(), 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) cx[j] = std::fmax(cx[j], std::fabs(Ps[(size_t)i * n + j]));
+        double mean = 0.0, qn = 0.0;
+        for (int j = 0; j < n; ++j) {
+            mean += cx[j];
+            qn = std::fmax(qn, std::fabs(qs[j]));
+        }
+        mean /= n;
+        double cost = std::fmax(mean, qn);
+        cost = cost < kNormMin ? 1.0 : std::fmin(cost, kNormMax);
+        const double gamma = 1.0 / cost;
+        for (double& v : Ps) v *= gamma;
+        for (double& v : qs) v *= gamma;
+        c *= gamma;
+    }
+}
+
+// Factor vectors of a scaled handle on the device (FP32).
+int upload_scaling(relu_qp_t h) {
+    const int n = h->n, m = h->m, mm = m > 0 ? m : 1;
+    std::vector<float> f(n > mm ? n : mm);
+    auto put = [&](float** dst, int len, auto fn) -> int {
+        RQ_TRY(rq::alloc(h, dst, (size_t)len));
+        for (int k = 0; k < len; ++k) f[k] = (float)fn(k);
+        RQ_CUDA(h, cudaMemcpy(*dst, f.data(), sizeof(float) * len, cudaMemcpyHostToDevice));
+        return RELU_QP_OK;
+    };
+    const std::vector<double>& D = h->sD;
+    const std::vector<double>& E = h->sE;
+    const double c = h->sC;
+    RQ_TRY(put(&h->sc_q, n, [&](int k) { return c * D[k]; }));
+    RQ_TRY(put(&h->sc_x, n, [&](int k) { return D[k]; }));
+    RQ_TRY(put(&h->sc_xi, n, [&](int k) { return 1.0 / D[k]; }));
+    RQ_TRY(put(&h->sc_rx, n, [&](int k) { return 1.0 / (c * D[k]); }));
+    RQ_TRY(put(&h->sc_e, mm, [&](int i) { return i < m ? E[i] : 1.0; }));
+    RQ_TRY(put(&h->sc_z, mm, [&](int i) { return i < m ? 1.0 / E[i] : 1.0; }));
+    RQ_TRY(put(&h->sc_l, mm, [&](int i) { return i < m ? E[i] / c : 1.0; }));
+    RQ_TRY(put(&h->sc_li, mm, [&](int i) { return i < m ? c / E[i] : 1.0; }));
+    return RELU_QP_OK;
+}
+
 int upload_problem(relu_qp_t h) {
     const int n = h->n, m = h->m;
-    std::vector<float> q = to_f32(h->h_q.data(), n);
+    std::vector<float> q(n);
+    for (int j = 0; j < n; ++j) q[j] = (float)(h->scaled ? h->sC * h->sD[j] * h->h_q[j] : h->h_q[j]);
     RQ_CUDA(h, cudaMemcpyAsync(h->q32, q.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
     if (m > 0) {
-        std::vector<float> l = to_f32(h->h_l.data(), m), u = to_f32(h->h_u.data(), m);
+        std::vector<float> l(m), u(m);
+        for (int i = 0; i < m; ++i) {
+            const double e = h->scaled ? h->sE[i] : 1.0;
+            l[i] = (float)(e * h->h_l[i]);
+            u[i] = (float)(e * h->h_u[i]);
+        }
         RQ_CUDA(h, cudaMemcpyAsync(h->l32, l.data(), sizeof(float) * m, cudaMemcpyHostToDevice, h->stream));
         RQ_CUDA(h, cudaMemcpyAsync(h->u32, u.data(), sizeof(float) * m, cudaMemcpyHostToDevice, h->stream));
         RQ_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -104,6 +192,17 @@ int setup_impl(relu_qp_t h, const double* P, const double* q, const double* A, c
     RQ_TRY(rq::alloc(h, &w.out_i, 8));
     RQ_TRY(rq::alloc(h, &w.out_f, 8));
     if (h->opts.max_batch > 0) RQ_TRY(rq::batch_alloc(h));
+    // problem scaling: the offline stage below sees the scaled P and A
+    std::vector<double> Ps, As;
+    if (h->opts.scaling_iters > 0) {
+        Ps.assign(P, P + (size_t)n * n);
+        if (m > 0) As.assign(A, A + (size_t)m * n);
+        ruiz_equilibrate(n, m, Ps, As, h->h_q, h->opts.scaling_iters, h->sD, h->sE, h->sC);
+        P = Ps.data();
+        A = m > 0 ? As.data() : A;
+        h->scaled = 1;
+        RQ_TRY(upload_scaling(h));
+    }
     // FP64 inputs for the offline stage (freed at the end of setup)
     double *dP = nullptr, *dA = nullptr;
     cudaError_t e1 = cudaMalloc(&dP, sizeof(double) * n * n);
@@ -188,6 +287,7 @@ void relu_qp_default_opts(relu_qp_opts* o) {
     o->max_batch = 0;
     o->batch_precision = RELU_QP_PREC_FP32;
     o->stream = nullptr;
+    o->scaling_iters = 0;
 }
 
 int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q, const double* A,
@@ -214,8 +314,10 @@ int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q
     relu_qp_opts o;
     relu_qp_default_opts(&o);
     if (opts) o = *opts;
-    if (o.check_interval < 0 || !(o.rho0 > 0.0) || !(o.eq_scale > 0.0))
-        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: check_interval >= 0, rho0 > 0, eq_scale > 0");
+    if (o.check_interval < 0 || !(o.rho0 > 0.0) || !(o.eq_scale > 0.0) || o.scaling_iters < 0 ||
+        o.scaling_iters > 100)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID,
+                        "opts: check_interval >= 0, rho0 > 0, eq_scale > 0, 0 <= scaling_iters <= 100");
     if (o.max_batch < 0 || o.max_batch > (1 << 20) ||
         (o.batch_precision != RELU_QP_PREC_FP32 && o.batch_precision != RELU_QP_PREC_BF16X3))
         return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: 0 <= max_batch <= 2^20, batch_precision FP32 or BF16X3");
@@ -274,11 +376,14 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
     const float* xin = nullptr;
     const float* lin = nullptr;
     if (x_warm) {
-        std::vector<float> xf = to_f32(x_warm, n);
+        // scaled handles: xb = x / D, lamb = c lam / E
+        std::vector<float> xf(n);
+        for (int j = 0; j < n; ++j) xf[j] = (float)(h->scaled ? x_warm[j] / h->sD[j] : x_warm[j]);
         RQ_CUDA(h, cudaMemcpyAsync(h->sw.xin, xf.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
         xin = h->sw.xin;
         if (lam_warm && m > 0) {
-            std::vector<float> lf = to_f32(lam_warm, m);
+            std::vector<float> lf(m);
+            for (int i = 0; i < m; ++i) lf[i] = (float)(h->scaled ? h->sC * lam_warm[i] / h->sE[i] : lam_warm[i]);
             RQ_CUDA(h, cudaMemcpyAsync(h->sw.lin, lf.data(), sizeof(float) * m, cudaMemcpyHostToDevice,
                                        h->stream));
             lin = h->sw.lin;
@@ -287,16 +392,18 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
     }
     relu_qp_info inf{};
     RQ_TRY(rq::single_solve(h, xin, lin, ri, eps_abs, eps_rel, max_iter, &inf));
+    // scaled handles: x = D xb, z = zb / E, lam = E lamb / c
+    const bool sc = h->scaled != 0;
     std::vector<float> buf((size_t)(n > m ? n : m));
     RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.y, sizeof(float) * n, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < n; ++i) x_out[i] = buf[i];
+    for (int i = 0; i < n; ++i) x_out[i] = sc ? h->sD[i] * (double)buf[i] : buf[i];
     if (z_out && m > 0) {
         RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.z, sizeof(float) * m, cudaMemcpyDeviceToHost));
-        for (int i = 0; i < m; ++i) z_out[i] = buf[i];
+        for (int i = 0; i < m; ++i) z_out[i] = sc ? (double)buf[i] / h->sE[i] : buf[i];
     }
     if (lam_out && m > 0) {
         RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.lstd, sizeof(float) * m, cudaMemcpyDeviceToHost));
-        for (int i = 0; i < m; ++i) lam_out[i] = buf[i];
+        for (int i = 0; i < m; ++i) lam_out[i] = sc ? h->sE[i] * (double)buf[i] / h->sC : buf[i];
     }
     if (info) *info = inf;
     return RELU_QP_OK;
@@ -310,6 +417,8 @@ int relu_qp_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_war
         rho_index_warm >= h->nr || (lam_warm && !x_warm))
         return rq::fail(h, RELU_QP_ERR_INVALID, "solve_noalloc: x_out required, max_iter >= 1, eps >= 0, "
                                                 "rho_index_warm in [-1, n_rho), lam_warm needs x_warm");
+    if (h->scaled)
+        return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "solve_noalloc: the handle was set up with scaling_iters > 0");
     const int ri = rho_index_warm >= 0 ? rho_index_warm : nearest_index(h, h->opts.rho0);
     return rq::single_solve_noalloc(h, x_warm, lam_warm, ri, eps_abs, eps_rel, max_iter, x_out, z_out, lam_out,
                                     info);

@@ -476,15 +476,27 @@ __global__ void batch_init_kernel(BatchParams p, int B, int warm, int lam_given,
         for (int k = lane; k < p.n; k += 32) p.Y[(size_t)qp * p.ldn + k] = 0.f;
 }
 
-__global__ void row_absmax_kernel(const float* __restrict__ X, int rows, int cols, int ld, float* out) {
+// out[r] = max_k |X[r][k] f[k]| (f = nullptr: 1).
+__global__ void row_absmax_kernel(const float* __restrict__ X, int rows, int cols, int ld,
+                                  const float* __restrict__ f, float* out) {
     const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= rows) return;
     float v = 0.f;
-    for (int k = lane; k < cols; k += 32) v = fmaxf(v, fabsf(X[(size_t)r * ld + k]));
+    for (int k = lane; k < cols; k += 32) v = fmaxf(v, fabsf(f ? X[(size_t)r * ld + k] * f[k] : X[(size_t)r * ld + k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0) out[r] = v;
+}
+
+// X[r][k] *= f[k] for rows [0, rows): the problem scaling's maps between the
+// original and the scaled problem's data and iterates.
+__global__ void scale_rows_kernel(float* X, int rows, int cols, int ld, const float* __restrict__ f) {
+    const size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), k = (int)(e % cols);
+        X[(size_t)r * ld + k] *= f[k];
+    }
 }
 
 // Check matrix [[P, A^T], [A, 0]] in FP32: x columns [0, n64), multiplier
@@ -536,10 +548,22 @@ BatchParams base_params(relu_qp_t h) {
         p.rhod[r] = h->be[r].rho;
     }
     p.rs = h->rs32;
+    p.rsx = h->sc_rx;
+    p.rsz = h->sc_z;
     p.Y = w.Y; p.Z = w.Z; p.LAM = w.LAM; p.AY = w.AY; p.RR = w.RR; p.LSTD = w.LSTD; p.C = w.C; p.SREF = w.SREF; p.PY = w.PY;
     p.L = w.L; p.U = w.U; p.Q = w.Q; p.BIAS = w.BIAS; p.QN = w.QN;
     p.perm = w.perm; p.tile_rho = w.tile_rho; p.counters = w.counters; p.RED = w.RED;
     return p;
+}
+
+int scale_rows(relu_qp_t h, float* X, int rows, int cols, int ld, const float* f) {
+    if (!f || rows <= 0 || cols <= 0) return RELU_QP_OK;
+    const size_t total = (size_t)rows * cols;
+    const int g = (int)std::min<size_t>((total + 255) / 256, 4096);
+    scale_rows_kernel<<<g, 256, 0, h->stream>>>(X, rows, cols, ld, f);
+    RQ_CUDA(h, cudaGetLastError());
+    ++h->launches;
+    return RELU_QP_OK;
 }
 
 int copy_rows_in(relu_qp_t h, float* dst, int ld, const float* src, int rows, int cols) {
@@ -751,11 +775,15 @@ int batch_update(relu_qp_t h, int B, const float* Q, const float* L, const float
     if (Q) RQ_TRY(copy_rows_in(h, w.Q, w.ldn, Q, B, n));
     if (L && m > 0) RQ_TRY(copy_rows_in(h, w.L, w.ldm, L, B, m));
     if (U && m > 0) RQ_TRY(copy_rows_in(h, w.U, w.ldm, U, B, m));
+    // scaled handles: q -> c D q, l -> E l, u -> E u
+    if (Q) RQ_TRY(scale_rows(h, w.Q, B, n, w.ldn, h->sc_q));
+    if (L && m > 0) RQ_TRY(scale_rows(h, w.L, B, m, w.ldm, h->sc_e));
+    if (U && m > 0) RQ_TRY(scale_rows(h, w.U, B, m, w.ldm, h->sc_e));
     if (Q) {
         for (int r = 0; r < h->nr; ++r)
             RQ_TRY(sgemm_nt(h, B, R, n, w.Q, w.ldn, h->be[r].Bop, n, 1.f, nullptr,
                             w.BIAS + (size_t)r * w.cap * w.ldR, w.ldR));
-        row_absmax_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(w.Q, B, n, w.ldn, w.QN);
+        row_absmax_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(w.Q, B, n, w.ldn, h->sc_rx, w.QN);
         RQ_CUDA(h, cudaGetLastError());
         ++h->launches;
     }
@@ -779,20 +807,25 @@ int batch_set_parametric(relu_qp_t h, int nx, const double* F, const double* E, 
         RQ_TRY(alloc(h, &w.X0, (size_t)w.cap * w.ldx));
         for (int r = 0; r < h->nr; ++r) RQ_TRY(alloc(h, &w.G[r], (size_t)R * w.ldx));
     }
+    // scaled handles: F -> c D F, E -> E E, l0 -> E l0, u0 -> E u0 (in FP64)
+    const bool sc = h->scaled != 0;
     std::vector<float> f((size_t)n * w.ldx, 0.f), ft((size_t)nx * w.ldn, 0.f);
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
+        const double fi = sc ? h->sC * h->sD[i] : 1.0;
         for (int k = 0; k < nx; ++k) {
-            f[(size_t)i * w.ldx + k] = (float)F[(size_t)i * nx + k];
-            ft[(size_t)k * w.ldn + i] = (float)F[(size_t)i * nx + k];
+            f[(size_t)i * w.ldx + k] = (float)(fi * F[(size_t)i * nx + k]);
+            ft[(size_t)k * w.ldn + i] = (float)(fi * F[(size_t)i * nx + k]);
         }
+    }
     RQ_CUDA(h, cudaMemcpy(w.F32, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
     RQ_CUDA(h, cudaMemcpy(w.Ft32, ft.data(), sizeof(float) * ft.size(), cudaMemcpyHostToDevice));
     if (m > 0) {
         std::vector<float> e((size_t)m * w.ldx, 0.f), lo(m), up(m);
         for (int i = 0; i < m; ++i) {
-            for (int k = 0; k < nx; ++k) e[(size_t)i * w.ldx + k] = (float)E[(size_t)i * nx + k];
-            lo[i] = (float)l0[i];
-            up[i] = (float)u0[i];
+            const double ei = sc ? h->sE[i] : 1.0;
+            for (int k = 0; k < nx; ++k) e[(size_t)i * w.ldx + k] = (float)(ei * E[(size_t)i * nx + k]);
+            lo[i] = (float)(ei * l0[i]);
+            up[i] = (float)(ei * u0[i]);
         }
         RQ_CUDA(h, cudaMemcpy(w.E32, e.data(), sizeof(float) * e.size(), cudaMemcpyHostToDevice));
         RQ_CUDA(h, cudaMemcpy(w.l0, lo.data(), sizeof(float) * m, cudaMemcpyHostToDevice));
@@ -816,7 +849,7 @@ int batch_update_x0(relu_qp_t h, int B, const float* X0) {
     for (int r = 0; r < h->nr; ++r)
         RQ_TRY(sgemm_nt(h, B, R, nx, w.X0, w.ldx, w.G[r], w.ldx, 1.f, nullptr, w.BIAS + (size_t)r * w.cap * w.ldR,
                         w.ldR));
-    row_absmax_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(w.Q, B, n, w.ldn, w.QN);
+    row_absmax_kernel<<<ceil_div(B * 32, 256), 256, 0, h->stream>>>(w.Q, B, n, w.ldn, h->sc_rx, w.QN);
     RQ_CUDA(h, cudaGetLastError());
     ++h->launches;
     w.B = B;
@@ -980,11 +1013,16 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         RQ_CUDA(h, cudaMemcpyAsync(w.iters, rw, sizeof(int) * B, cudaMemcpyDefault, h->stream));
         rw_dev = w.iters;   // staged; batch_init copies it into rho_idx before resetting iters
     }
+    // scaled handles: warm starts xb = x / D, lamb = c lam / E
     if (Xw) {
         RQ_TRY(copy_rows_in(h, w.Y, w.ldn, Xw, B, n));
+        RQ_TRY(scale_rows(h, w.Y, B, n, w.ldn, h->sc_xi));
         if (m > 0) RQ_TRY(sgemm_nt(h, B, m, n, w.Y, w.ldn, h->A32, (int)round_up(n, 4), 1.f, nullptr, w.AY, w.ldm));
     }
-    if (Lw && m > 0) RQ_TRY(copy_rows_in(h, w.LSTD, w.ldm, Lw, B, m));
+    if (Lw && m > 0) {
+        RQ_TRY(copy_rows_in(h, w.LSTD, w.ldm, Lw, B, m));
+        RQ_TRY(scale_rows(h, w.LSTD, B, m, w.ldm, h->sc_li));
+    }
     RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
     batch_init_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, h->stream>>>(p, B, Xw != nullptr, Lw != nullptr && m > 0,
                                                                         rw_dev, rho0, w.status, w.rho_idx, w.iters,
@@ -1052,7 +1090,10 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         h->layer_timed += h->prof_span_launches[e / 2];
     }
     h->prof_span_launches.clear();
-    // ---- outputs ----
+    // ---- outputs (scaled handles: x = D xb, z = zb / E, lam = E lamb / c) ----
+    RQ_TRY(scale_rows(h, w.XO, B, n, n, h->sc_x));
+    if (Zo && m > 0) RQ_TRY(scale_rows(h, w.ZO, B, m, m, h->sc_z));
+    if (Lo && m > 0) RQ_TRY(scale_rows(h, w.LO, B, m, m, h->sc_l));
     RQ_CUDA(h, cudaMemcpyAsync(Xo, w.XO, sizeof(float) * B * n, cudaMemcpyDefault, h->stream));
     if (Zo && m > 0) RQ_CUDA(h, cudaMemcpyAsync(Zo, w.ZO, sizeof(float) * B * m, cudaMemcpyDefault, h->stream));
     if (Lo && m > 0) RQ_CUDA(h, cudaMemcpyAsync(Lo, w.LO, sizeof(float) * B * m, cudaMemcpyDefault, h->stream));
@@ -1147,7 +1188,7 @@ __global__ void serve_scatter_kernel(BatchParams p, int k, const int* __restrict
     for (int t = lane; t < p.n; t += 32) {
         const float v = Qc[(size_t)j * p.ldn + t];
         Q[(size_t)qp * p.ldn + t] = v;
-        qn = fmaxf(qn, fabsf(v));
+        qn = fmaxf(qn, fabsf(p.rsx ? v * p.rsx[t] : v));   // |q|_inf of the original problem
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) qn = fmaxf(qn, __shfl_xor_sync(0xffffffffu, qn, o));
@@ -1170,15 +1211,16 @@ __global__ void serve_gather_kernel(BatchParams p, const int* __restrict__ done,
                                     const int* __restrict__ client_of, int* status, const int* __restrict__ iters,
                                     const int* __restrict__ rho_idx, const int* __restrict__ nsw,
                                     const float* __restrict__ rp, const float* __restrict__ rd,
-                                    const float* __restrict__ XO, float* Wx, float* Wl, int* Wr, int* Wv, float* out,
-                                    int ldo) {
+                                    const float* __restrict__ XO, const float* __restrict__ sx, float* Wx, float* Wl,
+                                    int* Wr, int* Wv, float* out, int ldo) {
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (j >= *cnt) return;
     const int qp = done[j];
     const int c = client_of[qp];
     float* o = out + (size_t)j * ldo;
-    for (int t = lane; t < p.n; t += 32) o[t] = XO[(size_t)qp * p.n + t];
+    // x of the original problem (x = D xb when scaled); the client's warm start stays scaled
+    for (int t = lane; t < p.n; t += 32) o[t] = sx ? XO[(size_t)qp * p.n + t] * sx[t] : XO[(size_t)qp * p.n + t];
     if (c >= 0) {
         for (int t = lane; t < p.n; t += 32) Wx[(size_t)c * p.ldn + t] = p.Y[(size_t)qp * p.ldn + t];
         for (int i = lane; i < p.m; i += 32) Wl[(size_t)c * p.ldm + i] = p.LSTD[(size_t)qp * p.ldm + i];
@@ -1348,8 +1390,8 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
     batch_decide_kernel<<<w.cap, kDecideThreads, 0, f.stream>>>(p, dd);
     RQ_SCUDA(s, cudaGetLastError());
     serve_gather_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(
-        p, f.d.done, f.d.cnt, f.d.client_of, w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, w.XO, f.d.Wx, f.d.Wl,
-        f.d.Wr, f.d.Wv, f.d.out, f.ldo);
+        p, f.d.done, f.d.cnt, f.d.client_of, w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, w.XO, h->sc_x, f.d.Wx,
+        f.d.Wl, f.d.Wr, f.d.Wv, f.d.out, f.ldo);
     RQ_SCUDA(s, cudaGetLastError());
     h->launches += 2;
     RQ_SCUDA(s, cudaMemcpyAsync(f.h_cnt, f.d.cnt, sizeof(int), cudaMemcpyDeviceToHost, f.stream));

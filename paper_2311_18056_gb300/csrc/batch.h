@@ -38,6 +38,9 @@ struct BatchParams {
     float rho[RQ_MAX_RHO];
     double rhod[RQ_MAX_RHO];
     const float* rs;                         // per-row penalty scale (1 or eq_scale)
+    // scaled problems: the residual and norm factors back to the original problem,
+    // 1/(c D) for rows of x and 1/E for constraint rows (nullptr without scaling)
+    const float *rsx, *rsz;
     float *Y, *Z, *LAM, *AY, *LSTD, *C, *SREF, *PY;
     float* RR;                               // refined layers: r = (Ax) - z + lam'/rho for the next layer
     const float *L, *U, *Q, *BIAS, *QN;
@@ -323,11 +326,13 @@ __device__ __forceinline__ void red_slot(unsigned* RED, int qp, int word, float 
 // for the second product; A x refreshes the carried Ax, gives the primal
 // residual A x - z and the multiplier lam_std = lam' + rho (A x - z), which
 // goes into the check operand.
+// (Scaled problems: the maxima are those of the original problem's quantities,
+// each row's value times its factor rsx or rsz.)
 __device__ __forceinline__ void check1_elem(const BatchParams& p, int slot, int qp, int ri, int r, float acc,
                                             float& rp, float& nax, float& nz, float& npx) {
     if (r < p.n) {
         p.PY[(size_t)qp * p.ldn + r] = acc;
-        npx = nmax(npx, fabsf(acc));
+        npx = nmax(npx, fabsf(p.rsx ? acc * p.rsx[r] : acc));
     } else {
         const int i = r - p.n;
         const size_t o = (size_t)qp * p.ldm + i;
@@ -337,16 +342,18 @@ __device__ __forceinline__ void check1_elem(const BatchParams& p, int slot, int 
         p.AY[o] = acc;
         p.LSTD[o] = ls;
         put_check(p, slot, p.n64 + i, ls);
-        rp = nmax(rp, fabsf(d));
-        nax = nmax(nax, fabsf(acc));
-        nz = nmax(nz, fabsf(zi));
+        const float f = p.rsz ? p.rsz[i] : 1.f;
+        rp = nmax(rp, fabsf(p.rsz ? d * f : d));
+        nax = nmax(nax, fabsf(p.rsz ? acc * f : acc));
+        nz = nmax(nz, fabsf(p.rsz ? zi * f : zi));
     }
 }
 
 // Second residual product, row j of A^T lam_std: dual residual P x + q + A^T lam_std.
 __device__ __forceinline__ void check2_elem(const BatchParams& p, int qp, int j, float acc, float& rd, float& natl) {
-    rd = nmax(rd, fabsf(p.PY[(size_t)qp * p.ldn + j] + p.Q[(size_t)qp * p.ldn + j] + acc));
-    natl = nmax(natl, fabsf(acc));
+    const float r = p.PY[(size_t)qp * p.ldn + j] + p.Q[(size_t)qp * p.ldn + j] + acc;
+    rd = nmax(rd, fabsf(p.rsx ? r * p.rsx[j] : r));
+    natl = nmax(natl, fabsf(p.rsx ? acc * p.rsx[j] : acc));
 }
 
 struct DecideArgs {

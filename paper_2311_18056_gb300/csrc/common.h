@@ -128,6 +128,17 @@ struct relu_qp_s {
     float *P32 = nullptr, *A32 = nullptr, *At32 = nullptr;   // check matrices (FP32)
     float *q32 = nullptr, *l32 = nullptr, *u32 = nullptr, *rs32 = nullptr;
     double qnorm = 0.0;
+    // problem scaling (opts.scaling_iters > 0): the device holds the scaled problem
+    // (c D P D, c D q, E A D, E l, E u); x = D xb, z = zb / E, lam = E lamb / c.
+    // Host FP64 D, E, c and device FP32 factor vectors, all nullptr without scaling:
+    // sc_q = c D (q in), sc_x = D (x out), sc_xi = 1/D (x in), sc_e = E (l, u in),
+    // sc_z = 1/E (z out; residual rows of constraints), sc_l = E/c (lam out),
+    // sc_li = c/E (lam in), sc_rx = 1/(c D) (residual rows of x)
+    int scaled = 0;
+    std::vector<double> sD, sE;
+    double sC = 1.0;
+    float *sc_q = nullptr, *sc_x = nullptr, *sc_xi = nullptr, *sc_e = nullptr, *sc_z = nullptr, *sc_l = nullptr,
+          *sc_li = nullptr, *sc_rx = nullptr;
     rq::SingleWork sw;
     rq::BatchWork bw;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -36,6 +36,7 @@ struct SP {
     const float* bias[RQ_MAX_RHO];
     double rho[RQ_MAX_RHO];
     const float *P, *A, *At, *q, *l, *u, *rs;
+    const float *rsx, *rsz;   // scaled problems: residual factors 1/(c D), 1/E (else nullptr)
     float *y, *z, *lam, *Ay, *s0, *s1, *Py, *Axf, *lstd;
     unsigned* red;
     unsigned* bar;
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
                 const float v = row_dot_global(p.P + (size_t)r * p.ldp, sv, p.ldp, lane);
                 if (lane == 0) {
                     p.Py[r] = v;
-                    red_max(slot, RED_PX, v);
+                    red_max(slot, RED_PX, p.rsx ? v * p.rsx[r] : v);
                 }
             } else {
                 const int i = r - n;
@@ -233,9 +234,10 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
                     const float rho_i = (float)(p.rho[ri] * (double)__ldg(p.rs + i));
                     p.Axf[i] = v;
                     p.lstd[i] = p.lam[i] + rho_i * (v - zi);
-                    red_max(slot, RED_RP, v - zi);
-                    red_max(slot, RED_AX, v);
-                    red_max(slot, RED_Z, zi);
+                    const float f = p.rsz ? p.rsz[i] : 1.f;
+                    red_max(slot, RED_RP, (v - zi) * f);
+                    red_max(slot, RED_AX, v * f);
+                    red_max(slot, RED_Z, zi * f);
                 }
             }
         }
@@ -245,8 +247,9 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
         for (int j = r2_0 + warp; j < r2_1; j += kWarps) {
             const float v = (m > 0) ? row_dot_global(p.At + (size_t)j * p.ldt, sv, p.ldt, lane) : 0.f;
             if (lane == 0) {
-                red_max(slot, RED_RD, __ldcg(p.Py + j) + __ldg(p.q + j) + v);
-                red_max(slot, RED_ATL, v);
+                const float f = p.rsx ? p.rsx[j] : 1.f;
+                red_max(slot, RED_RD, (__ldcg(p.Py + j) + __ldg(p.q + j) + v) * f);
+                red_max(slot, RED_ATL, v * f);
             }
         }
         if (!grid_barrier(p, &s_ok)) return;
@@ -418,6 +421,8 @@ int launch(relu_qp_t h, int grid, int cached, int rho_index, double eps_abs, dou
     p.eps_abs = eps_abs;
     p.eps_rel = eps_rel;
     p.qnorm = h->qnorm;
+    p.rsx = h->sc_rx;
+    p.rsz = h->sc_z;
     SingleWork& w = h->sw;
     RQ_CUDA(h, cudaMemsetAsync(w.red, 0, sizeof(unsigned) * 3 * RED_WORDS, h->stream));
     RQ_CUDA(h, cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2, h->stream));
@@ -618,6 +623,8 @@ int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm
     p.eps_abs = eps_abs;
     p.eps_rel = eps_rel;
     p.qnorm = h->qnorm;
+    p.rsx = h->sc_rx;
+    p.rsz = h->sc_z;
     // parts that must start at zero: x and lam_std padding (read as whole
     // padded vectors by the check), reduction slots, barrier and result words
     RQ_CUDA(h, cudaMemsetAsync(y, 0, sizeof(float) * ldw, h->stream));

@@ -379,3 +379,15 @@ def test_scaled_solve_meets_the_unscaled_stop_test_and_helps():
     assert r.status == "solved" and r.iters < 2000
     assert res["r_prim"] <= 1e-3 and res["r_dual"] <= 1e-3
     assert np.max(np.abs(r.x - ref["x"])) <= 1e-3
+
+
+def test_fixed_scaling_is_the_computed_one_for_the_setup_q():
+    """solve_scaled with the (D, E, c) that ruiz_scaling returns for this q is the
+    same computation as letting it scale: identical iterates and result."""
+    from workloads import mpc
+    P, q, A, l, u = mpc.badly_scaled_qp(1, 30, 20)
+    D, E, c, *_ = O.ruiz_scaling(P, A, q, 10)
+    a = O.solve_scaled(P, q, A, l, u, scaling_iters=10, eps_abs=1e-3, max_iter=2000)
+    b = O.solve_scaled(P, q, A, l, u, scaling=(D, E, c), eps_abs=1e-3, max_iter=2000)
+    assert a.iters == b.iters and a.status == b.status
+    assert np.max(np.abs(a.x - b.x)) <= 1e-12 * max(1.0, np.max(np.abs(a.x)))
