@@ -3,8 +3,9 @@ against the FP64 oracle's modified Ruiz equilibration, through the C ABI.
 
 * setup: a scaled handle's layer bank is the oracle's layer of the
   equilibrated problem (c D P D, E A D) to 1e-9 relative, so D, E and c agree;
-* iterates: 50 fixed-rho FP32 layers, mapped back to the original problem
-  (x = D xb, z = zb / E, lam = E lamb / c), match the oracle's to 1e-5;
+* iterates: 50 fixed-rho FP32 layers of the equilibrated problem match the
+  oracle's to 1e-5 (returned x, z, lam mapped into the scaled problem with
+  xb = x / D, zb = E z, lamb = c lam / E);
 * converged solves (single, batched FP32 and BF16 split, server): status
   SOLVED on QPs that do not converge unscaled, FP64-recomputed residuals of
   the ORIGINAL problem within eps_abs (the stop test runs on them), x within
@@ -96,10 +97,12 @@ def test_scaled_iterates_map_back(rq, seed, dims):
     v = O.layer_iterates(Pb, qb, Ab, lb, ub, SIGMA, BANK[1], 50)[-1]
     xb, zb, lam_l = v[:n], v[n:n + m], v[n + m:]
     lamb = O.std_multiplier(Ab, xb, zb, lam_l, O.rho_vector(lb, ub, BANK[1]))
+    # compared in the scaled problem, where the FP32 layers run (the map back
+    # multiplies each component by a factor between 1e-2 and 1e2)
     assert out["iters"] == 50
-    assert rel(out["x"], D * xb) <= 1e-5
-    assert rel(out["z"], zb / E) <= 1e-5
-    assert rel(out["lam"], E * lamb / c) <= 1e-5
+    assert rel(out["x"] / D, xb) <= 1e-5
+    assert rel(out["z"] * E, zb) <= 1e-5
+    assert rel(c * out["lam"] / E, lamb) <= 1e-5
 
 
 @pytest.mark.parametrize("seed,dims", [(0, (40, 30)), (1, (203, 77)), (2, (130, 250))])

@@ -323,16 +323,19 @@ def disturbances(pq: ParametricQP, steps: int, std: float, sub_id: int = 3):
 def badly_scaled_qp(seed: int, n: int, m: int):
     """A dense QP whose variables and constraint rows span three orders of
     magnitude (row scales r, variable scales s in 10^U[-1.5, 1.5]):
-    P = S (M M^T / n + I) S, A = R N S^{-1}, q = S g, and l <= A x <= u around
-    A x_s with widths proportional to r, so that about half the rows bind.
-    Workload of the scaling tests (Algorithm 1's "Scale problem" step)."""
+    P = S (M M^T / n + I) S, A = R N S / sqrt(n), q = S g, and l <= A x <= u
+    around A x_s (x_s = h / s) with widths proportional to r, so that about
+    half the rows bind.  The entries of P and A span six orders of magnitude
+    while x, A x and P x at the optimum stay below about 100, so that an
+    absolute tolerance of 1e-3 is within FP32's reach once the problem is
+    scaled.  Workload of the scaling tests (Algorithm 1's "Scale problem" step)."""
     rng = rng_for(90, seed)
     s = 10.0 ** rng.uniform(-1.5, 1.5, n)
     M = rng.standard_normal((n, n))
     P = (s[:, None] * (M @ M.T / n + np.eye(n))) * s[None, :]
     P = 0.5 * (P + P.T)
     r = 10.0 ** rng.uniform(-1.5, 1.5, m)
-    A = r[:, None] * rng.standard_normal((m, n)) / s[None, :]
+    A = r[:, None] * rng.standard_normal((m, n)) * s[None, :] / np.sqrt(n)
     q = s * rng.standard_normal(n)
     xs = rng.standard_normal(n) / s
     Ax = A @ xs
