@@ -412,10 +412,14 @@ def kkt_violation(P, q, A, l, u, x, lam):
     # lam > 0 only where Ax = u, lam < 0 only where Ax = l
     pos = np.maximum(lam, 0.0)
     neg = np.minimum(lam, 0.0)
-    up_gap = np.where(np.isfinite(u), np.abs(u - Ax), np.inf)
-    lo_gap = np.where(np.isfinite(l), np.abs(Ax - l), np.inf)
-    comp_u = np.max(np.where(pos > 0, np.minimum(pos, 1.0) * np.minimum(up_gap, 1e300), 0.0))
-    comp_l = np.max(np.where(neg < 0, np.minimum(-neg, 1.0) * np.minimum(lo_gap, 1e300), 0.0))
+    # a finite bound: |lam| (capped at 1) times the distance to the bound; an
+    # infinite bound can never be active, so there the multiplier itself must
+    # vanish and its size is the violation
+    fu, fl = np.isfinite(u), np.isfinite(l)
+    up_gap = np.abs(np.where(fu, u, 0.0) - Ax)
+    lo_gap = np.abs(Ax - np.where(fl, l, 0.0))
+    comp_u = np.max(np.where(fu, np.minimum(pos, 1.0) * up_gap, pos))
+    comp_l = np.max(np.where(fl, np.minimum(-neg, 1.0) * lo_gap, -neg))
     return float(max(stat, feas, comp_u, comp_l))
 
 
