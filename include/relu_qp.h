@@ -82,11 +82,20 @@ typedef struct relu_qp_opts {
                                problem's residuals and norms.  relu_qp_get_layer
                                returns the scaled problem's layer; relu_qp_solve_noalloc
                                refuses a scaled handle. */
+    int    single_precision; /* arithmetic of relu_qp_solve: RELU_QP_PREC_FP32 (default:
+                               FP32 layers and checks, the paper's GPU arithmetic) or
+                               RELU_QP_PREC_FP64 (FP64 layer bank, iterates, residuals
+                               and outputs; for tolerances FP32 cannot resolve, e.g.
+                               1e-6 with the 1000x penalty of equality rows, Sec. II-B
+                               and Sec. V-A).  FP64 keeps the FP64 bank (as keep_fp64)
+                               and FP64 copies of P and A; relu_qp_solve_noalloc
+                               refuses it. */
 } relu_qp_opts;
 
 #define RELU_QP_PREC_FP32    0   /* batched layer product in FP32 on the CUDA cores */
 #define RELU_QP_PREC_BF16X3  1   /* batched layer product on tcgen05 tensor cores,
                                     BF16 hi+lo split operands, FP32 accumulate */
+#define RELU_QP_PREC_FP64    2   /* single-QP solve in FP64 (opts.single_precision) */
 
 typedef struct relu_qp_info {
     int    status;       /* RELU_QP_SOLVED / RELU_QP_MAX_ITER / RELU_QP_NUMERICAL */
@@ -148,8 +157,9 @@ int relu_qp_update(relu_qp_t h, const double* q, const double* l, const double* 
  *   x_out             n FP64 (required); z_out, lam_out m FP64 (may be NULL).
  *                     lam_out is the standard ADMM multiplier lam' + rho (Ax - z).
  *   info              may be NULL
- * The whole loop runs in one cooperative kernel on the device; the host
- * waits only for its end.  Errors: INVALID, CUDA, TIMEOUT.
+ * The whole loop runs in one cooperative kernel on the device (FP32, or FP64
+ * when opts.single_precision = RELU_QP_PREC_FP64); the host waits only for
+ * its end.  Errors: INVALID, CUDA, TIMEOUT.
  */
 int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int rho_index_warm,
                   double eps_abs, double eps_rel, int max_iter, double* x_out, double* z_out,

@@ -13,14 +13,14 @@ import os
 import numpy as np
 
 __all__ = ["ReluQP", "ReluQPError", "lib", "library_path", "OK", "SOLVED", "MAX_ITER", "NUMERICAL",
-           "PREC_FP32", "PREC_BF16X3", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result"]
+           "PREC_FP32", "PREC_BF16X3", "PREC_FP64", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "librelu_qp.so")
 
 OK = 0
 SOLVED, MAX_ITER, NUMERICAL = 0, 1, 2
-PREC_FP32, PREC_BF16X3 = 0, 1
+PREC_FP32, PREC_BF16X3, PREC_FP64 = 0, 1, 2
 ERRORS = {-1: "INVALID", -2: "NOT_PD", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "UNSUPPORTED"}
 
 _c_int, _c_double, _c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -30,7 +30,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class Opts(ctypes.Structure):
     _fields_ = [("check_interval", _c_int), ("adaptive_rho", _c_int), ("rho0", _c_double),
                 ("eq_scale", _c_double), ("keep_fp64", _c_int), ("max_batch", _c_int),
-                ("batch_precision", _c_int), ("stream", _c_void_p), ("scaling_iters", _c_int)]
+                ("batch_precision", _c_int), ("stream", _c_void_p), ("scaling_iters", _c_int),
+                ("single_precision", _c_int)]
 
 
 class Prof(ctypes.Structure):
@@ -153,7 +154,7 @@ class ReluQP:
 
     def __init__(self, P, A, l, u, q=None, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), *, check_interval=25,
                  adaptive_rho=True, rho0=0.1, eq_scale=1e3, keep_fp64=False, max_batch=0,
-                 precision=PREC_FP32, stream=None, scaling_iters=0):
+                 precision=PREC_FP32, stream=None, scaling_iters=0, single_precision=PREC_FP32):
         L = lib()
         P = _f64(P)
         n = P.shape[0]
@@ -174,6 +175,7 @@ class ReluQP:
         o.batch_precision = int(precision)
         o.stream = _stream_handle(stream)
         o.scaling_iters = int(scaling_iters)
+        o.single_precision = int(single_precision)
         h = _c_void_p()
         rc = L.relu_qp_setup(ctypes.byref(h), n, m, _ptr(P), _ptr(q), _ptr(A) if m else None,
                              _ptr(l) if m else None, _ptr(u) if m else None, float(sigma), _ptr(bank),

@@ -131,6 +131,16 @@ int upload_problem(relu_qp_t h) {
     double qn = 0.0;
     for (int i = 0; i < n; ++i) qn = std::fmax(qn, std::fabs(h->h_q[i]));
     h->qnorm = qn;
+    if (h->opts.single_precision == RELU_QP_PREC_FP64) {
+        std::vector<double> q64(n), l64(m), u64(m);
+        for (int j = 0; j < n; ++j) q64[j] = h->scaled ? h->sC * h->sD[j] * h->h_q[j] : h->h_q[j];
+        for (int i = 0; i < m; ++i) {
+            const double e = h->scaled ? h->sE[i] : 1.0;
+            l64[i] = e * h->h_l[i];
+            u64[i] = e * h->h_u[i];
+        }
+        RQ_TRY(rq::single64_upload(h, q64.data(), l64.data(), u64.data()));
+    }
     RQ_TRY(rq::compute_bias(h));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return RELU_QP_OK;
@@ -221,12 +231,14 @@ int setup_impl(relu_qp_t h, const double* P, const double* q, const double* A, c
     if (rc == RELU_QP_OK) rc = rq::build_bank(h, dP, dA, row_scale);
     if (rc == RELU_QP_OK && h->bw.cap > 0 && h->bw.prec == RELU_QP_PREC_BF16X3)
         rc = rq::pack_bf16_check(h, dP, dA);
+    if (rc == RELU_QP_OK && h->opts.single_precision == RELU_QP_PREC_FP64) rc = rq::single64_alloc(h, P, A);
     cudaStreamSynchronize(h->stream);
     cudaFree(dP);
     cudaFree(dA);
     if (rc != RELU_QP_OK) return rc;
     RQ_TRY(upload_problem(h));
     RQ_TRY(rq::single_prepare(h));
+    if (h->opts.single_precision == RELU_QP_PREC_FP64) RQ_TRY(rq::single64_prepare(h));
     if (h->bw.cap > 0) RQ_TRY(rq::batch_finish_setup(h));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return RELU_QP_OK;
@@ -288,6 +300,7 @@ void relu_qp_default_opts(relu_qp_opts* o) {
     o->batch_precision = RELU_QP_PREC_FP32;
     o->stream = nullptr;
     o->scaling_iters = 0;
+    o->single_precision = RELU_QP_PREC_FP32;
 }
 
 int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q, const double* A,
@@ -321,6 +334,9 @@ int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q
     if (o.max_batch < 0 || o.max_batch > (1 << 20) ||
         (o.batch_precision != RELU_QP_PREC_FP32 && o.batch_precision != RELU_QP_PREC_BF16X3))
         return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: 0 <= max_batch <= 2^20, batch_precision FP32 or BF16X3");
+    if (o.single_precision != RELU_QP_PREC_FP32 && o.single_precision != RELU_QP_PREC_FP64)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: single_precision FP32 or FP64");
+    if (o.single_precision == RELU_QP_PREC_FP64) o.keep_fp64 = 1;   // the FP64 solve reads the FP64 bank
     relu_qp_t h = new (std::nothrow) relu_qp_s;
     if (!h) return rq::fail(nullptr, RELU_QP_ERR_OOM, "host allocation failed");
     h->n = n;
@@ -373,6 +389,33 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
     if (x_warm && !finite_all(x_warm, n)) return rq::fail(h, RELU_QP_ERR_INVALID, "x_warm must be finite");
     if (lam_warm && !finite_all(lam_warm, m)) return rq::fail(h, RELU_QP_ERR_INVALID, "lam_warm must be finite");
     const int ri = rho_index_warm >= 0 ? rho_index_warm : nearest_index(h, h->opts.rho0);
+    const bool sc = h->scaled != 0;
+    if (h->opts.single_precision == RELU_QP_PREC_FP64) {
+        // scaled handles: xb = x / D, lamb = c lam / E in; x = D xb, z = zb / E, lam = E lamb / c out
+        std::vector<double> xw, lw, zb(m), lb(m);
+        if (x_warm) {
+            xw.assign(x_warm, x_warm + n);
+            if (sc)
+                for (int j = 0; j < n; ++j) xw[j] /= h->sD[j];
+            if (lam_warm && m > 0) {
+                lw.assign(lam_warm, lam_warm + m);
+                if (sc)
+                    for (int i = 0; i < m; ++i) lw[i] *= h->sC / h->sE[i];
+            }
+        }
+        relu_qp_info inf{};
+        RQ_TRY(rq::single64_solve(h, x_warm ? xw.data() : nullptr, lw.empty() ? nullptr : lw.data(), ri, eps_abs,
+                                  eps_rel, max_iter, x_out, m > 0 ? zb.data() : nullptr,
+                                  m > 0 ? lb.data() : nullptr, &inf));
+        if (sc)
+            for (int j = 0; j < n; ++j) x_out[j] *= h->sD[j];
+        for (int i = 0; i < m; ++i) {
+            if (z_out) z_out[i] = sc ? zb[i] / h->sE[i] : zb[i];
+            if (lam_out) lam_out[i] = sc ? h->sE[i] * lb[i] / h->sC : lb[i];
+        }
+        if (info) *info = inf;
+        return RELU_QP_OK;
+    }
     const float* xin = nullptr;
     const float* lin = nullptr;
     if (x_warm) {
@@ -393,7 +436,6 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
     relu_qp_info inf{};
     RQ_TRY(rq::single_solve(h, xin, lin, ri, eps_abs, eps_rel, max_iter, &inf));
     // scaled handles: x = D xb, z = zb / E, lam = E lamb / c
-    const bool sc = h->scaled != 0;
     std::vector<float> buf((size_t)(n > m ? n : m));
     RQ_CUDA(h, cudaMemcpy(buf.data(), h->sw.y, sizeof(float) * n, cudaMemcpyDeviceToHost));
     for (int i = 0; i < n; ++i) x_out[i] = sc ? h->sD[i] * (double)buf[i] : buf[i];
@@ -419,6 +461,8 @@ int relu_qp_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_war
                                                 "rho_index_warm in [-1, n_rho), lam_warm needs x_warm");
     if (h->scaled)
         return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "solve_noalloc: the handle was set up with scaling_iters > 0");
+    if (h->opts.single_precision != RELU_QP_PREC_FP32)
+        return rq::fail(h, RELU_QP_ERR_UNSUPPORTED, "solve_noalloc: the handle was set up for FP64 solves");
     const int ri = rho_index_warm >= 0 ? rho_index_warm : nearest_index(h, h->opts.rho0);
     return rq::single_solve_noalloc(h, x_warm, lam_warm, ri, eps_abs, eps_rel, max_iter, x_out, z_out, lam_out,
                                     info);

@@ -53,8 +53,9 @@ struct BankEntry {
     float* Wt = nullptr;      // R x ldw FP32, rows [x; Ax], cols [x; 2 rho z - lam'] (padded)
     float* Bop = nullptr;     // R x n FP32: [-D; -A D]
     float* bias = nullptr;    // R FP32 = Bop q (single-QP path)
-    double* Wt64 = nullptr;   // R x R FP64 (keep_fp64 only)
-    double* Bop64 = nullptr;  // R x n FP64 (keep_fp64 only)
+    double* Wt64 = nullptr;   // R x R FP64 (keep_fp64 or the FP64 single solve)
+    double* Bop64 = nullptr;  // R x n FP64 (same)
+    double* bias64 = nullptr; // R FP64 = Bop64 q (FP64 single solve)
 };
 
 // Workspace of the single-QP cooperative solve.
@@ -71,6 +72,19 @@ struct SingleWork {
     int grid = 0;               // CTAs of the cooperative launch (autotuned)
     int cached_rows = 0;        // rows of W each CTA keeps in shared memory
     int rows_per_cta = 0;
+};
+
+// Workspace of the FP64 single-QP solve (opts.single_precision = FP64).
+struct SingleWork64 {
+    double *y = nullptr, *z = nullptr, *lam = nullptr, *Ay = nullptr;
+    double *s0 = nullptr, *s1 = nullptr;
+    double *Py = nullptr, *Axf = nullptr, *lstd = nullptr;
+    double *xin = nullptr, *lin = nullptr;
+    unsigned long long* red = nullptr;   // 3 slots x 8 reduction words (bits of non-negative doubles)
+    unsigned* bar = nullptr;             // grid barrier [count, generation]
+    int* out_i = nullptr;                // status, iters, rho_index, switches, err
+    double* out_f = nullptr;             // r_prim, r_dual
+    int grid = 0;
 };
 
 // Workspace of batched solves (allocated when opts.max_batch > 0).
@@ -139,6 +153,10 @@ struct relu_qp_s {
     double sC = 1.0;
     float *sc_q = nullptr, *sc_x = nullptr, *sc_xi = nullptr, *sc_e = nullptr, *sc_z = nullptr, *sc_l = nullptr,
           *sc_li = nullptr, *sc_rx = nullptr;
+    double *sc64_rx = nullptr, *sc64_z = nullptr;   // the residual factors in FP64 (FP64 single solve)
+    // FP64 single solve: check matrices and problem data (scaled problem when scaled)
+    double *P64 = nullptr, *A64 = nullptr, *At64 = nullptr, *q64 = nullptr, *l64 = nullptr, *u64 = nullptr;
+    rq::SingleWork64 sw64;
     rq::SingleWork sw;
     rq::BatchWork bw;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -177,6 +195,13 @@ int single_prepare(relu_qp_t h);
 int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index, double eps_abs,
                          double eps_rel, int max_iter, float* x_out, float* z_out, float* lam_out,
                          relu_qp_info* info);
+// FP64 single-QP solve (single_solve64.cu).
+int single64_alloc(relu_qp_t h, const double* P, const double* A);
+int single64_upload(relu_qp_t h, const double* q, const double* l, const double* u);
+int single64_prepare(relu_qp_t h);
+int single64_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int rho_index, double eps_abs,
+                   double eps_rel, int max_iter, double* x_out, double* z_out, double* lam_out,
+                   relu_qp_info* info);
 // Batched solves (batch.cu).
 int batch_alloc(relu_qp_t h);
 int batch_update(relu_qp_t h, int B, const float* Q, const float* L, const float* U);

@@ -112,3 +112,41 @@ def test_humanoid_workload_structure():
         assert np.max(np.abs(np.linalg.eigvals(A[s:s + 10, s:s + 10]))) == pytest.approx(1.0)
         off[s:s + 10, s:s + 10] = 0
     assert np.all(off == 0)
+
+
+def test_random_qp_sizes_and_structure():
+    """Sec. V-A: ten sizes log-spaced 10..2000, n/4 equality and n/4 inequality rows."""
+    from workloads import random_qp as R
+    assert R.SIZES[0] == 10 and R.SIZES[-1] == 2000 and len(R.SIZES) == 10
+    assert all(b > a for a, b in zip(R.SIZES, R.SIZES[1:]))
+    for n in (10, 105, 342):
+        P, q, A, l, u = R.random_dense_qp(0, n)
+        me = n // 4
+        assert A.shape == (2 * me, n) and P.shape == (n, n) and q.shape == (n,)
+        assert np.all(l[:me] == u[:me]) and np.all(np.isneginf(l[me:])) and np.all(np.isfinite(u))
+        assert np.all(np.linalg.eigvalsh(P) > 5e-3)
+        assert np.allclose(P, P.T)
+    # reproducible and distinct per seed
+    a = R.random_dense_qp(3, 58)
+    b = R.random_dense_qp(3, 58)
+    c = R.random_dense_qp(4, 58)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert not np.array_equal(a[0], c[0])
+
+
+def test_random_qp_oracle_meets_1e6_and_kkt():
+    """The FP64 oracle reaches residuals of 1e-6 on the small sizes, and its
+    point agrees with the accurate KKT solution (active set + exact solve)."""
+    from oracle import relu_qp_oracle as O
+    from workloads import random_qp as R
+    for n in (10, 32, 105):
+        P, q, A, l, u = R.random_dense_qp(1, n)
+        r = O.solve(P, q, A, l, u, eps_abs=1e-6, max_iter=4000)
+        res = O.residuals(P, q, A, r.x, r.z, r.lam)
+        assert r.status == "solved", n
+        assert res["r_prim"] <= 1e-6 and res["r_dual"] <= 1e-6
+        ref = O.reference_solution(P, q, A, l, u)
+        assert O.kkt_violation(P, q, A, l, u, ref["x"], ref["lam"]) <= 1e-9
+        assert np.max(np.abs(r.x - ref["x"])) <= 1e-4
+        me = n // 4
+        assert np.max(np.abs(A[:me] @ r.x - l[:me])) <= 1e-6   # equalities hold to the tolerance
