@@ -11,7 +11,8 @@ The offline stage (FP64 factorisation and layer bank) runs once before
 timing.  Inputs are synthetic and seeded (workloads/mpc.py).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-on the same workload instead.
+on the same workload instead.  `--serve` measures the served stream and
+`--random-qp` the random dense QPs of Sec. V-A (their own JSON lines).
 """
 from __future__ import annotations
 
@@ -52,6 +53,9 @@ def parse():
                     help="run the served stream (Poisson arrivals over three resident families) instead")
     ap.add_argument("--rate", type=float, default=2000.0, help="served stream: requests per second")
     ap.add_argument("--duration", type=float, default=10.0, help="served stream: measured seconds")
+    ap.add_argument("--random-qp", action="store_true",
+                    help="random dense QPs of Sec. V-A: FP64 single solves to 1e-6 per size")
+    ap.add_argument("--rqp-count", type=int, default=10, help="random QPs per size")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -505,10 +509,62 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_random_qp(args):
+    """Random dense QPs (Sec. V-A): for each of the ten sizes n = 10..2000 with
+    n/4 equality and n/4 inequality rows, `rqp_count` seeded problems, each set
+    up (FP64 bank, not timed) and solved cold to residuals below 1e-6 by the
+    FP64 single-QP kernel.  Reports per size the device time of the solve
+    (CUDA events around the cooperative launch), its p50 and max, the layers,
+    and the FP64 NumPy oracle's time on the first problem of the size."""
+    import paper_2311_18056_gb300 as rq
+    from workloads import random_qp as R
+    eps = 1e-6
+    per_size = []
+    cores = blas_threads()
+    for n in R.SIZES:
+        ms, iters, solved, wall = [], [], 0, []
+        for seed in range(args.rqp_count):
+            P, q, A, l, u = R.random_dense_qp(seed, n)
+            s = rq.ReluQP(P, A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, single_precision=rq.PREC_FP64)
+            s.solve(eps_abs=eps, max_iter=50)            # first launch of this handle (not timed)
+            t0 = time.perf_counter()
+            r = s.solve(eps_abs=eps, max_iter=4000)
+            wall.append((time.perf_counter() - t0) * 1e3)
+            s.close()
+            ms.append(r["solve_ms"])
+            iters.append(r["iters"])
+            solved += int(r["status"] == rq.SOLVED)
+        from oracle import relu_qp_oracle as O
+        P, q, A, l, u = R.random_dense_qp(0, n)
+        t0 = time.perf_counter()
+        O.solve(P, q, A, l, u, sigma=SIGMA, rho_bank=BANK, eps_abs=eps, max_iter=4000)
+        oracle_ms = (time.perf_counter() - t0) * 1e3
+        per_size.append({"n": n, "m": 2 * (n // 4), "problems": args.rqp_count, "solved": solved,
+                         "p50_ms": float(np.percentile(ms, 50)), "max_ms": float(np.max(ms)),
+                         "p50_call_ms": float(np.percentile(wall, 50)), "mean_layers": float(np.mean(iters)),
+                         "us_per_layer": float(np.sum(ms) * 1e3 / np.sum(iters)),
+                         "oracle_ms_first_problem": oracle_ms})
+        print(f"n={n}: p50 {per_size[-1]['p50_ms']:.3f} ms, layers {np.mean(iters):.0f}, solved {solved}/"
+              f"{args.rqp_count}", file=sys.stderr, flush=True)
+    big = per_size[-1]
+    line = {"metric": "random dense QP solve time at eps=1e-6 (FP64 single QP, n=2000, one GB300)",
+            "value": big["p50_ms"], "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "random dense QPs, n/4 equality + n/4 inequality rows, sizes 10..2000 "
+                                   "log-spaced, seeded, eps_abs=1e-6, rho bank [0.1, 1.0, 10.0], sigma 1e-6, "
+                                   "cold starts"},
+            "per_size": per_size, "vs_baseline": None,
+            "cpu_baseline": {"value": big["oracle_ms_first_problem"], "unit": "ms", "cores": cores,
+                             "kind": "oracle", "sample": "first problem of n = 2000 solved by the FP64 oracle"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.serve:
         run_serve(args)
+    elif args.random_qp:
+        run_random_qp(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -12,7 +12,7 @@
 // benchmark (Sec. V-A); in FP64 the same noise is ~1e-16 |Ax| rho_eq.
 //
 // Work split: the R = n + m rows of Wt (FP64, R x R) are cut into contiguous
-// slices, one per CTA; each warp produces one row at a time (lanes over the
+// slices, one per CTA of 16 warps; each warp produces one row at a time (lanes over the
 // columns, shuffle reduction); the operand s lives in shared memory.  Rows
 // stream from L2 (the FP64 bank of n + m = 3000 is 72 MB).  A grid barrier
 // with a deadline separates layers.
@@ -24,7 +24,7 @@
 namespace rq {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 // operand s in shared memory: n + m doubles at most
 constexpr int kMaxRows64 = 24576;
@@ -98,17 +98,22 @@ __device__ bool grid_barrier(const SP64& p, int* s_ok) {
 }
 
 // Dot product of a row (global, read-only) with a vector in shared memory;
-// the result is valid in every lane.
+// the result is valid in every lane.  Eight independent loads per lane are in
+// flight per step: a row streams from L2, and with one CTA of 8 warps per SM
+// fewer loads in flight leave the FP64 pipe waiting on L2 latency.
 __device__ __forceinline__ double row_dot(const double* __restrict__ w, const double* __restrict__ s, int len,
                                           int lane) {
-    double a0 = 0.0, a1 = 0.0;
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int k = lane;
-    for (; k + 32 < len; k += 64) {
-        a0 = fma(__ldg(w + k), s[k], a0);
-        a1 = fma(__ldg(w + k + 32), s[k + 32], a1);
+    for (; k + 7 * 32 < len; k += 8 * 32) {
+        double wv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) wv[t] = __ldg(w + k + 32 * t);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) a[t] = fma(wv[t], s[k + 32 * t], a[t]);
     }
-    if (k < len) a0 = fma(__ldg(w + k), s[k], a0);
-    return warp_sum(a0 + a1);
+    for (; k < len; k += 32) a[0] = fma(__ldg(w + k), s[k], a[0]);   // at most 7 steps
+    return warp_sum(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
 }
 
 // Vector written by other CTAs into shared memory, bypassing L1.
