@@ -241,6 +241,52 @@ int relu_qp_set_parametric(relu_qp_t h, int nx, const double* F, const double* E
 int relu_qp_update_batch_x0(relu_qp_t h, int B, const float* X0);
 
 /*
+ * relu_qp_condense_mpc -- the dense, LQR-preconditioned condensing of a linear
+ * MPC problem (Sec. IV "Dense Model-Predictive Control"), in FP64 on the GPU.
+ * It produces the parametric QP that relu_qp_setup (P, A_con, l0, u0) and
+ * relu_qp_set_parametric (F, E, l0, u0) take.
+ *
+ * Plant x_{k+1} = A x_k + B u_k (k = 0..N-1).  Controls are u_k = -K x_k +
+ * du_k.  K is the infinite-horizon LQR gain, used as a preconditioner.  The
+ * decision vector is du = [du_0; ..; du_{N-1}], so n = N nu.  The trajectory
+ * is y = [u_0; x_1; ..; u_{N-1}; x_N] = S du + M x0, with S and M as printed
+ * in Sec. IV.  With H = blkdiag(R, Q, .., R, Q_N) the QP is
+ *   min 1/2 du' P du + (F x0)' du,  P = S' H S,  F = S' H M,
+ *   l0 - E x0 <= A_con du <= u0 - E x0.
+ * The constraint rows are, in this order:
+ *   - the control limits umin <= u_k <= umax for every k (N nu rows);
+ *   - the state limits xmin <= x_{k+1} <= xmax (N nx rows), present only when
+ *     xmin or xmax is given.
+ * A_con holds the matching rows of S and E the matching rows of M.
+ *
+ *   nx, nu, N     state and control sizes, horizon (>= 1; N nu <= 40000)
+ *   A, B, Q, R    nx x nx, nx x nu, nx x nx, nu x nu, row-major FP64 (host).
+ *                 Q_N: nx x nx terminal weight, NULL = Q.
+ *   umin, umax    nu each; NULL = unbounded on that side; +-INFINITY allowed
+ *   xmin, xmax    nx each; both NULL = no state rows; one NULL = unbounded side
+ *   K             nu x nx gain to use.  NULL with lqr_precondition = 1: the
+ *                 infinite-horizon LQR gain, computed by the fixed-point
+ *                 Riccati iteration X <- Q + A'X(A - B K(X)) until
+ *                 max|dX| <= 1e-13 max(1, max|X|).  NULL with
+ *                 lqr_precondition = 0: K = 0, plain condensing.
+ *   stream        cudaStream_t for the work (NULL = legacy default stream)
+ * Outputs (host FP64, caller-allocated; m = N nu + (state rows ? N nx : 0)):
+ *   P (n x n), A_con (m x n), F (n x nx), E (m x nx), l0, u0 (m),
+ *   K_out (nu x nx, may be NULL): the gain used.
+ * Errors (message in relu_qp_last_error(NULL)):
+ *   INVALID  sizes, NULL inputs, non-finite matrices, umin > umax or
+ *            xmin > xmax, a Riccati iteration that diverges or does not
+ *            converge (e.g. (A, B) not stabilizable)
+ *   NOT_PD   R + B'XB not positive definite
+ *   OOM, CUDA
+ */
+int relu_qp_condense_mpc(int nx, int nu, int N, const double* A, const double* B, const double* Q,
+                         const double* R, const double* Q_N, const double* umin, const double* umax,
+                         const double* xmin, const double* xmax, const double* K, int lqr_precondition,
+                         void* stream, double* P, double* A_con, double* F, double* E, double* l0,
+                         double* u0, double* K_out);
+
+/*
  * relu_qp_solve_batch -- Algorithm 1 for the first B QPs of the last batch update.
  *   X_warm (B x n), Lam_warm (B x m), rho_warm (B, bank indices): warm start
  *     (z = A x_warm); NULL = cold start (rho_warm needs X_warm)

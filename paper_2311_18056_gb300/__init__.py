@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 __all__ = ["ReluQP", "ReluQPError", "lib", "library_path", "OK", "SOLVED", "MAX_ITER", "NUMERICAL",
-           "PREC_FP32", "PREC_BF16X3", "PREC_FP64", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result"]
+           "PREC_FP32", "PREC_BF16X3", "PREC_FP64", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result",
+           "condense_mpc"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(_HERE, "librelu_qp.so")
@@ -70,6 +71,8 @@ _SIGNATURES = {
     "relu_qp_update_batch": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p]),
     "relu_qp_set_parametric": (_c_int, [_c_void_p, _c_int, _dp, _dp, _dp, _dp]),
     "relu_qp_update_batch_x0": (_c_int, [_c_void_p, _c_int, _c_void_p]),
+    "relu_qp_condense_mpc": (_c_int, [_c_int, _c_int, _c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                      _c_int, _c_void_p, _dp, _dp, _dp, _dp, _dp, _dp, _dp]),
     "relu_qp_solve_batch": (_c_int, [_c_void_p, _c_int, _c_void_p, _c_void_p, _c_void_p, _c_double, _c_double, _c_int,
                                      _c_void_p, _c_void_p, _c_void_p, ctypes.POINTER(Info)]),
     "relu_qp_profile": (_c_int, [_c_void_p, _c_int, _c_int, ctypes.POINTER(Prof)]),
@@ -307,6 +310,36 @@ class ReluQP:
         o.adaptive_rho = 1 if adaptive_rho is None else int(bool(adaptive_rho))
         o.rho0 = 0.1 if rho0 is None else float(rho0)
         self._check(lib().relu_qp_set_opts(self._h, ctypes.byref(o)))
+
+
+def condense_mpc(A, B, Q, R, N, QN=None, umin=None, umax=None, xmin=None, xmax=None, K=None,
+                 lqr_precondition=True, stream=None):
+    """LQR-preconditioned condensing of the MPC problem x+ = A x + B u (Sec. IV) on the GPU in FP64.
+
+    Returns dict(P, A, F, E, l0, u0, K): the QP min 1/2 du'P du + (F x0)'du,
+    l0 - E x0 <= A du <= u0 - E x0 over du = [du_0; ..; du_{N-1}], the rows being
+    the control limits of every stage, then (with xmin/xmax) the state limits."""
+    L = lib()
+    A = _f64(A)
+    B = _f64(B)
+    nx, nu, N = A.shape[0], B.shape[1], int(N)
+    Q = _f64(Q, (nx, nx))
+    R = _f64(R, (nu, nu))
+    QN = _f64(QN, (nx, nx))
+    umin, umax = _f64(umin, (nu,)), _f64(umax, (nu,))
+    xmin, xmax = _f64(xmin, (nx,)), _f64(xmax, (nx,))
+    K = _f64(K, (nu, nx))
+    n = N * nu
+    m = N * nu + (N * nx if (xmin is not None or xmax is not None) else 0)
+    P, Acon, F, E = np.empty((n, n)), np.empty((m, n)), np.empty((n, nx)), np.empty((m, nx))
+    l0, u0, Kout = np.empty(m), np.empty(m), np.empty((nu, nx))
+    rc = L.relu_qp_condense_mpc(nx, nu, N, _ptr(A), _ptr(B), _ptr(Q), _ptr(R), _ptr(QN), _ptr(umin), _ptr(umax),
+                                _ptr(xmin), _ptr(xmax), _ptr(K), int(bool(lqr_precondition)),
+                                _stream_handle(stream), _ptr(P), _ptr(Acon), _ptr(F), _ptr(E), _ptr(l0), _ptr(u0),
+                                _ptr(Kout))
+    if rc != OK:
+        raise ReluQPError(rc, L.relu_qp_last_error(None).decode())
+    return {"P": P, "A": Acon, "F": F, "E": E, "l0": l0, "u0": u0, "K": Kout}
 
 
 class Server:

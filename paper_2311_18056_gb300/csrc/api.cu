@@ -558,6 +558,49 @@ int relu_qp_update_batch_x0(relu_qp_t h, int B, const float* X0) {
     return rq::batch_update_x0(h, B, X0);
 }
 
+int relu_qp_condense_mpc(int nx, int nu, int N, const double* A, const double* B, const double* Q,
+                         const double* R, const double* Q_N, const double* umin, const double* umax,
+                         const double* xmin, const double* xmax, const double* K, int lqr_precondition,
+                         void* stream, double* P, double* A_con, double* F, double* E, double* l0,
+                         double* u0, double* K_out) {
+    if (nx < 1 || nu < 1 || N < 1 || (long)N * nu > 40000 || (long)N * nx > 1000000)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "condense: nx, nu, N >= 1 and N nu <= 40000");
+    if (!A || !B || !Q || !R || !P || !A_con || !F || !E || !l0 || !u0)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "condense: A, B, Q, R and every output but K_out are required");
+    if (!finite_all(A, (size_t)nx * nx) || !finite_all(B, (size_t)nx * nu) || !finite_all(Q, (size_t)nx * nx) ||
+        !finite_all(R, (size_t)nu * nu) || (Q_N && !finite_all(Q_N, (size_t)nx * nx)) ||
+        (K && !finite_all(K, (size_t)nu * nx)))
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "condense: A, B, Q, R, Q_N and K must be finite");
+    for (int i = 0; i < nu; ++i) {
+        const double lo = umin ? umin[i] : -INFINITY, hi = umax ? umax[i] : INFINITY;
+        if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+            return rq::fail(nullptr, RELU_QP_ERR_INVALID, "condense: need umin <= umax, no NaN");
+    }
+    for (int i = 0; (xmin || xmax) && i < nx; ++i) {
+        const double lo = xmin ? xmin[i] : -INFINITY, hi = xmax ? xmax[i] : INFINITY;
+        if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+            return rq::fail(nullptr, RELU_QP_ERR_INVALID, "condense: need xmin <= xmax, no NaN");
+    }
+    const bool state = xmin || xmax;
+    std::string err;
+    const int rc = rq::condense_mpc(nx, nu, N, A, B, Q, R, Q_N, state, K, lqr_precondition, stream, P, A_con, F,
+                                    E, K_out, &err);
+    if (rc != RELU_QP_OK) return rq::fail(nullptr, rc, err);
+    // bounds of the constraint rows: the limits of every stage
+    for (int k = 0; k < N; ++k)
+        for (int i = 0; i < nu; ++i) {
+            l0[(size_t)k * nu + i] = umin ? umin[i] : -INFINITY;
+            u0[(size_t)k * nu + i] = umax ? umax[i] : INFINITY;
+        }
+    if (state)
+        for (int k = 0; k < N; ++k)
+            for (int i = 0; i < nx; ++i) {
+                l0[(size_t)N * nu + (size_t)k * nx + i] = xmin ? xmin[i] : -INFINITY;
+                u0[(size_t)N * nu + (size_t)k * nx + i] = xmax ? xmax[i] : INFINITY;
+            }
+    return RELU_QP_OK;
+}
+
 int relu_qp_solve_batch(relu_qp_t h, int B, const float* X_warm, const float* Lam_warm, const int* rho_warm,
                         double eps_abs, double eps_rel, int max_iter, float* X_out, float* Z_out, float* Lam_out,
                         relu_qp_info* infos) {

@@ -181,6 +181,19 @@ int alloc(relu_qp_t h, T** p, size_t count) {
     return dev_alloc(h, reinterpret_cast<void**>(p), count * sizeof(T) + 16);
 }
 
+// FP64 building blocks of the offline stage (setup_fp64.cu), on h->stream:
+// C = alpha op(A) op(B) + beta C (row-major); in-place blocked Cholesky K = L L^T
+// (Linv: ceil(n / kCholNB) diagonal-block inverses of kCholNB^2, T: n x kCholNB
+// scratch, *flag set on a pivot <= 0); Rhs (n x NR) <- K^{-1} Rhs (T2: kCholNB x NR).
+constexpr int kCholNB = 64;
+int dgemm(relu_qp_t h, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, int lda,
+          const double* B, int ldb, double beta, double* C, int ldc);
+int cholesky(relu_qp_t h, double* Km, int n, double* Linv, double* T, int* flag);
+int chol_solve(relu_qp_t h, const double* L, int n, const double* Linv, double* Rhs, int NR, double* T2);
+// Condensing of a linear MPC problem (condense.cu); error text in *err.
+int condense_mpc(int nx, int nu, int N, const double* A, const double* B, const double* Q, const double* R,
+                 const double* QN, bool state_rows, const double* K, int precondition, void* stream, double* P,
+                 double* Acon, double* F, double* E, double* K_out, std::string* err);
 // FP64 setup (setup_fp64.cu): builds every bank entry of h from P, A (device FP64).
 int build_bank(relu_qp_t h, const double* dP, const double* dA, const std::vector<double>& rho_rows_scale);
 // FP32 copies of P, A, A^T from FP64 device arrays (setup_fp64.cu).

@@ -26,7 +26,7 @@ namespace rq {
 
 namespace {
 
-constexpr int NB = 64;   // Cholesky / triangular-solve block size
+constexpr int NB = kCholNB;   // Cholesky / triangular-solve block size
 
 // C = alpha * op(A) * op(B) + beta * C, row-major, 64x64 tiles, 4x4 per thread.
 // FP64 on GB300 runs at a small fraction of the FP32 rate, so this kernel is
@@ -283,6 +283,8 @@ int grid1d(size_t total) {
     return (int)g;
 }
 
+}  // namespace
+
 int dgemm(relu_qp_t h, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
           int lda, const double* B, int ldb, double beta, double* C, int ldc) {
     if (M <= 0 || N <= 0) return RELU_QP_OK;
@@ -349,6 +351,8 @@ int chol_solve(relu_qp_t h, const double* L, int n, const double* Linv, double* 
     }
     return RELU_QP_OK;
 }
+
+namespace {
 
 struct Scratch {
     relu_qp_t h;
