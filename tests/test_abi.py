@@ -56,3 +56,47 @@ def test_setup_error_reporting_without_gpu(libpath):
     with pytest.raises(rq.ReluQPError) as e:
         rq.ReluQP(np.array([[np.nan]]), None, None, None)
     assert e.value.kind == "INVALID"
+
+
+def header_struct_fields(name):
+    """Field names, in order, of `typedef struct name { ... } name;` in include/relu_qp.h."""
+    text = open(os.path.join(ROOT, "include", "relu_qp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct " + name + r"\s*\{(.*?)\}\s*" + name + ";", text, flags=re.S).group(1)
+    return [m.group(1) for m in re.finditer(r"([A-Za-z_][A-Za-z0-9_]*)\s*;", body)]
+
+
+def test_binding_structs_mirror_the_header(libpath):
+    import paper_2311_18056_gb300 as rq
+    for cname, pyt in (("relu_qp_opts", rq.Opts), ("relu_qp_info", rq.Info)):
+        assert header_struct_fields(cname) == [f for f, _ in pyt._fields_], cname
+
+
+def test_default_opts_without_gpu(libpath):
+    """relu_qp_default_opts makes no CUDA call: the defaults of every field, the new ones included."""
+    import paper_2311_18056_gb300 as rq
+    o = rq.Opts()
+    rq.lib().relu_qp_default_opts(ctypes.byref(o))
+    assert (o.check_interval, o.adaptive_rho, o.rho0, o.eq_scale) == (25, 1, 0.1, 1e3)
+    assert (o.keep_fp64, o.max_batch, o.batch_precision) == (0, 0, rq.PREC_FP32)
+    assert o.scaling_iters == 0 and o.single_precision == rq.PREC_FP32
+
+
+def test_new_options_are_validated_without_gpu(libpath):
+    import numpy as np
+    import paper_2311_18056_gb300 as rq
+    P, A, l, u = np.eye(2), np.eye(2), -np.ones(2), np.ones(2)
+    for kw in ({"scaling_iters": -1}, {"scaling_iters": 101}, {"single_precision": 5}):
+        with pytest.raises(rq.ReluQPError) as e:
+            rq.ReluQP(P, A, l, u, **kw)
+        assert e.value.kind == "INVALID", kw
+    # condensing: limits and sizes are checked before any GPU work
+    with pytest.raises(rq.ReluQPError) as e:
+        rq.condense_mpc(np.eye(2), np.ones((2, 1)), np.eye(2), np.eye(1), 5, umin=[1.0], umax=[-1.0])
+    assert e.value.kind == "INVALID"
+    with pytest.raises(rq.ReluQPError) as e:
+        rq.condense_mpc(np.eye(2), np.ones((2, 1)), np.eye(2), np.eye(1), 0)
+    assert e.value.kind == "INVALID"
+    with pytest.raises(rq.ReluQPError) as e:
+        rq.condense_mpc(np.array([[np.inf, 0], [0, 1]]), np.ones((2, 1)), np.eye(2), np.eye(1), 3)
+    assert e.value.kind == "INVALID"

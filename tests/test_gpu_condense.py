@@ -100,3 +100,15 @@ def test_condensed_problem_solves_like_oracle(rq):
         r = O.solve(o["P"], q, o["A"], l, u, eps_abs=1e-3)
         assert out["status"][b] == rq.SOLVED and r.status == "solved"
         assert np.max(np.abs(out["x"][b] - r.x)) <= 1e-3, b
+
+
+def test_condense_smallest_shapes(rq):
+    """A scalar plant (nx = nu = 1) over one stage, and a single-input plant with N = 1."""
+    for (A, B) in ((np.array([[1.2]]), np.array([[0.5]])), (np.array([[1.0, 0.1], [0.0, 1.0]]), np.array([[0.0], [0.1]]))):
+        nx, nu = B.shape
+        Q, R = np.eye(nx), 0.1 * np.eye(nu)
+        for N in (1, 3):
+            g = rq.condense_mpc(A, B, Q, R, N, umin=-np.ones(nu), umax=np.ones(nu))
+            o = C.condense_mpc(A, B, Q, R, N, umin=-np.ones(nu), umax=np.ones(nu))
+            for k in ("P", "A", "F", "E", "K"):
+                assert close(g[k], o[k], 1e-9), (nx, N, k)

@@ -132,3 +132,20 @@ def test_fp64_noalloc_is_refused(rq):
                                         x.ctypes.data_as(ctypes.c_void_p), None, None, ctypes.byref(info))
     s.close()
     assert rq.ERRORS[rc] == "UNSUPPORTED"
+
+
+def test_fp64_degenerate_shapes(rq):
+    """m = 0 (the solve is x = -P^-1 q), n = m = 1, and max_iter = 1."""
+    P, q, A, l, u = R.random_dense_qp(5, 58)
+    s = rq.ReluQP(P, None, None, None, q=q, sigma=SIGMA, rho_bank=BANK, single_precision=rq.PREC_FP64)
+    out = s.solve(eps_abs=1e-9, max_iter=4000)
+    s.close()
+    assert out["status"] == rq.SOLVED
+    assert np.max(np.abs(out["x"] + np.linalg.solve(P, q))) <= 1e-7
+    s = rq.ReluQP([[2.0]], [[1.0]], [0.5], [0.5], q=[1.0], sigma=SIGMA, rho_bank=BANK,
+                  single_precision=rq.PREC_FP64)
+    out = s.solve(eps_abs=EPS, max_iter=4000)
+    assert out["status"] == rq.SOLVED and abs(out["x"][0] - 0.5) <= 1e-6
+    one = s.solve(eps_abs=EPS, max_iter=1)
+    s.close()
+    assert one["iters"] == 1 and one["status"] == rq.MAX_ITER

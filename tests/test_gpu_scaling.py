@@ -219,3 +219,31 @@ def test_noalloc_refuses_a_scaled_handle(rq):
                                         x.ctypes.data_as(ctypes.c_void_p), None, None, ctypes.byref(info))
     assert rq.ERRORS[rc] == "UNSUPPORTED"
     s.close()
+
+
+def test_scaled_equality_and_infinite_rows(rq):
+    """Equality rows (1000x penalty, Sec. II-B) and one-sided rows in a badly scaled QP:
+    the scaled problem keeps the row pattern (E l = E u exactly where l = u)."""
+    P, q, A, l, u = mpc.badly_scaled_qp(3, 120, 60)
+    x_f = np.linalg.lstsq(A, 0.5 * (l + u), rcond=None)[0]
+    l, u = l.copy(), u.copy()
+    l[:6] = u[:6] = (A @ x_f)[:6]          # equalities at a point inside the other bounds' range
+    l[6:20] = -np.inf
+    u[20:30] = np.inf
+    s = rq.ReluQP(P, A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, scaling_iters=ITERS)
+    out = s.solve(eps_abs=EPS, max_iter=4000)
+    s.close()
+    orc = O.solve_scaled(P, q, A, l, u, scaling_iters=ITERS, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS, max_iter=4000)
+    assert orc.status == "solved"
+    check_solution(rq, P, q, A, l, u, out["x"], out["z"], out["lam"], out["status"], orc.x)
+    assert np.all(np.isneginf(out["z"][6:20]) == False)   # z is finite where a bound is infinite
+
+
+def test_scaled_unconstrained(rq):
+    P, q, A, l, u = mpc.badly_scaled_qp(4, 50, 10)
+    s = rq.ReluQP(P, None, None, None, q=q, sigma=SIGMA, rho_bank=BANK, scaling_iters=ITERS)
+    out = s.solve(eps_abs=1e-4, max_iter=4000)
+    s.close()
+    assert out["status"] == rq.SOLVED
+    x = -np.linalg.solve(P, q)
+    assert np.max(np.abs(out["x"] - x)) <= 1e-3 * (1 + np.max(np.abs(x)))
