@@ -353,7 +353,6 @@ __device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtenso
                 sync_failed = true;
                 return false;
             }
-            __nanosleep(64);
         }
         // the operand was written by generic stores of other CTAs; order them before the TMA reads
         asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -1044,10 +1043,12 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 : "memory");
             if (any) break;
             if (warp == 2 && lane == 0) {
-                __threadfence();
                 if (j < c.nl) {
+                    // a release at GPU scope: it orders this CTA's stores of layer j (those of the
+                    // other epilogue warps through the barrier above) before the counter's increment
                     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c.sync + tile) : "memory");
                 } else {
+                    __threadfence();
                     // after the last layer nobody waits on the counter: the tile's last CTA
                     // to get here puts it (and the done count) back to zero for the next launch
                     const unsigned done = atomicAdd(c.sync + c.done_off + tile, 1u) + 1u;
