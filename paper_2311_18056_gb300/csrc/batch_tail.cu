@@ -21,6 +21,7 @@
 // Every barrier wait has a deadline after which the kernel records
 // RELU_QP_ERR_TIMEOUT and returns.
 #include "batch.h"
+#include "grid_sync.h"
 
 #include <algorithm>
 
@@ -47,45 +48,9 @@ struct TailArgs {
     long long timeout_ns;
 };
 
-__device__ __forceinline__ long long tail_timer() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Grid-wide barrier; false in every thread of the CTA if the wait passed its
-// deadline or another CTA reported an error.
-__device__ bool tail_barrier(const TailArgs& a, int* s_ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (gridDim.x > 1) {
-            volatile unsigned* gen = a.bar + 1;
-            const unsigned g = *gen;
-            __threadfence();
-            const unsigned arrived = atomicAdd(a.bar, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(a.bar, 0u);
-                __threadfence();
-                atomicAdd(a.bar + 1, 1u);
-            } else {
-                const long long t0 = tail_timer();
-                while (*gen == g) {
-                    if (tail_timer() - t0 > a.timeout_ns) {
-                        atomicExch(a.err, RELU_QP_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            __threadfence();
-        }
-        if (*((volatile int*)a.err) != 0) ok = 0;
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
+// Grid-wide barrier over all CTAs of the cooperative launch (grid_sync.h).
+__device__ __forceinline__ bool tail_barrier(const TailArgs& a, int* s_ok) {
+    return grid_sync(a.bar, a.err, a.timeout_ns, s_ok);
 }
 
 constexpr int kStep = 16;       // k per partial (the tiled kernels' step)

@@ -16,6 +16,7 @@
 // barrier wait has a deadline after which the kernel records
 // RELU_QP_ERR_TIMEOUT and returns.
 #include "common.h"
+#include "grid_sync.h"
 
 #include <cmath>
 #include <mutex>
@@ -48,52 +49,15 @@ struct SP {
     long long timeout_ns;
 };
 
-__device__ __forceinline__ long long global_timer() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Grid-wide barrier over all CTAs of the cooperative launch.  Returns false
-// (in every thread of the CTA) if the wait passed its deadline or another CTA
-// already reported an error; the caller then returns from the kernel.
-__device__ bool grid_barrier(const SP& p, int* s_ok) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        if (gridDim.x > 1) {
-            volatile unsigned* gen = p.bar + 1;
-            const unsigned g = *gen;
-            __threadfence();
-            const unsigned arrived = atomicAdd(p.bar, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(p.bar, 0u);
-                __threadfence();
-                atomicAdd(p.bar + 1, 1u);
-            } else {
-                const long long t0 = global_timer();
-                while (*gen == g) {
-                    if (global_timer() - t0 > p.timeout_ns) {
-                        atomicExch(p.out_i + OUT_ERR, RELU_QP_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
-            __threadfence();
-        }
-        if (*((volatile int*)(p.out_i + OUT_ERR)) != 0) ok = 0;
-        *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
+// Grid-wide barrier over all CTAs of the cooperative launch (grid_sync.h).
+__device__ __forceinline__ bool grid_barrier(const SP& p, int* s_ok) {
+    return grid_sync(p.bar, p.out_i + OUT_ERR, p.timeout_ns, s_ok);
 }
 
 // Dot product of a padded row with a padded vector in shared memory; the
