@@ -83,19 +83,25 @@ typedef struct relu_qp_opts {
                                returns the scaled problem's layer; relu_qp_solve_noalloc
                                refuses a scaled handle. */
     int    single_precision; /* arithmetic of relu_qp_solve: RELU_QP_PREC_FP32 (default:
-                               FP32 layers and checks, the paper's GPU arithmetic) or
+                               FP32 layers and checks, the paper's GPU arithmetic),
                                RELU_QP_PREC_FP64 (FP64 layer bank, iterates, residuals
                                and outputs; for tolerances FP32 cannot resolve, e.g.
                                1e-6 with the 1000x penalty of equality rows, Sec. II-B
-                               and Sec. V-A).  FP64 keeps the FP64 bank (as keep_fp64)
-                               and FP64 copies of P and A; relu_qp_solve_noalloc
-                               refuses it. */
+                               and Sec. V-A) or RELU_QP_PREC_FP64R (the same with FP32
+                               products of the layer increments between FP64 anchor
+                               layers: faster, iterates within rounding of FP64).  Both
+                               keep the FP64 bank (as keep_fp64) and FP64 copies of P
+                               and A; relu_qp_solve_noalloc refuses them. */
 } relu_qp_opts;
 
 #define RELU_QP_PREC_FP32    0   /* batched layer product in FP32 on the CUDA cores */
 #define RELU_QP_PREC_BF16X3  1   /* batched layer product on tcgen05 tensor cores,
                                     BF16 hi+lo split operands, FP32 accumulate */
 #define RELU_QP_PREC_FP64    2   /* single-QP solve in FP64 (opts.single_precision) */
+#define RELU_QP_PREC_FP64R   3   /* single-QP solve with FP64 state, residuals and one FP64 layer
+                                    product per check interval (the anchor c = Wt s_ref + b); the
+                                    other layers apply the FP32 bank to the increment only,
+                                    t = c + Wt (s - s_ref) (opts.single_precision) */
 
 typedef struct relu_qp_info {
     int    status;       /* RELU_QP_SOLVED / RELU_QP_MAX_ITER / RELU_QP_NUMERICAL */

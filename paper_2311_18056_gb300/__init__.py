@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 __all__ = ["ReluQP", "ReluQPError", "lib", "library_path", "OK", "SOLVED", "MAX_ITER", "NUMERICAL",
-           "PREC_FP32", "PREC_BF16X3", "PREC_FP64", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result",
+           "PREC_FP32", "PREC_BF16X3", "PREC_FP64", "PREC_FP64R", "EXPORTED_SYMBOLS", "Info", "Opts", "Prof", "Server", "Result",
            "condense_mpc"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -21,7 +21,7 @@ library_path = os.path.join(_HERE, "librelu_qp.so")
 
 OK = 0
 SOLVED, MAX_ITER, NUMERICAL = 0, 1, 2
-PREC_FP32, PREC_BF16X3, PREC_FP64 = 0, 1, 2
+PREC_FP32, PREC_BF16X3, PREC_FP64, PREC_FP64R = 0, 1, 2, 3
 ERRORS = {-1: "INVALID", -2: "NOT_PD", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "UNSUPPORTED"}
 
 _c_int, _c_double, _c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p

@@ -131,7 +131,7 @@ int upload_problem(relu_qp_t h) {
     double qn = 0.0;
     for (int i = 0; i < n; ++i) qn = std::fmax(qn, std::fabs(h->h_q[i]));
     h->qnorm = qn;
-    if (h->opts.single_precision == RELU_QP_PREC_FP64) {
+    if (h->opts.single_precision != RELU_QP_PREC_FP32) {
         std::vector<double> q64(n), l64(m), u64(m);
         for (int j = 0; j < n; ++j) q64[j] = h->scaled ? h->sC * h->sD[j] * h->h_q[j] : h->h_q[j];
         for (int i = 0; i < m; ++i) {
@@ -231,14 +231,14 @@ int setup_impl(relu_qp_t h, const double* P, const double* q, const double* A, c
     if (rc == RELU_QP_OK) rc = rq::build_bank(h, dP, dA, row_scale);
     if (rc == RELU_QP_OK && h->bw.cap > 0 && h->bw.prec == RELU_QP_PREC_BF16X3)
         rc = rq::pack_bf16_check(h, dP, dA);
-    if (rc == RELU_QP_OK && h->opts.single_precision == RELU_QP_PREC_FP64) rc = rq::single64_alloc(h, P, A);
+    if (rc == RELU_QP_OK && h->opts.single_precision != RELU_QP_PREC_FP32) rc = rq::single64_alloc(h, P, A);
     cudaStreamSynchronize(h->stream);
     cudaFree(dP);
     cudaFree(dA);
     if (rc != RELU_QP_OK) return rc;
     RQ_TRY(upload_problem(h));
     RQ_TRY(rq::single_prepare(h));
-    if (h->opts.single_precision == RELU_QP_PREC_FP64) RQ_TRY(rq::single64_prepare(h));
+    if (h->opts.single_precision != RELU_QP_PREC_FP32) RQ_TRY(rq::single64_prepare(h));
     if (h->bw.cap > 0) RQ_TRY(rq::batch_finish_setup(h));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
     return RELU_QP_OK;
@@ -334,9 +334,10 @@ int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q
     if (o.max_batch < 0 || o.max_batch > (1 << 20) ||
         (o.batch_precision != RELU_QP_PREC_FP32 && o.batch_precision != RELU_QP_PREC_BF16X3))
         return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: 0 <= max_batch <= 2^20, batch_precision FP32 or BF16X3");
-    if (o.single_precision != RELU_QP_PREC_FP32 && o.single_precision != RELU_QP_PREC_FP64)
-        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: single_precision FP32 or FP64");
-    if (o.single_precision == RELU_QP_PREC_FP64) o.keep_fp64 = 1;   // the FP64 solve reads the FP64 bank
+    if (o.single_precision != RELU_QP_PREC_FP32 && o.single_precision != RELU_QP_PREC_FP64 &&
+        o.single_precision != RELU_QP_PREC_FP64R)
+        return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: single_precision FP32, FP64 or FP64R");
+    if (o.single_precision != RELU_QP_PREC_FP32) o.keep_fp64 = 1;   // the FP64 solves read the FP64 bank
     relu_qp_t h = new (std::nothrow) relu_qp_s;
     if (!h) return rq::fail(nullptr, RELU_QP_ERR_OOM, "host allocation failed");
     h->n = n;
@@ -390,7 +391,7 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
     if (lam_warm && !finite_all(lam_warm, m)) return rq::fail(h, RELU_QP_ERR_INVALID, "lam_warm must be finite");
     const int ri = rho_index_warm >= 0 ? rho_index_warm : nearest_index(h, h->opts.rho0);
     const bool sc = h->scaled != 0;
-    if (h->opts.single_precision == RELU_QP_PREC_FP64) {
+    if (h->opts.single_precision != RELU_QP_PREC_FP32) {
         // scaled handles: xb = x / D, lamb = c lam / E in; x = D xb, z = zb / E, lam = E lamb / c out
         std::vector<double> xw, lw, zb(m), lb(m);
         if (x_warm) {

@@ -74,12 +74,13 @@ struct SingleWork {
     int rows_per_cta = 0;
 };
 
-// Workspace of the FP64 single-QP solve (opts.single_precision = FP64).
+// Workspace of the FP64 single-QP solve (opts.single_precision = FP64 or FP64R).
 struct SingleWork64 {
     double *y = nullptr, *z = nullptr, *lam = nullptr, *Ay = nullptr;
     double *s0 = nullptr, *s1 = nullptr;
     double *Py = nullptr, *Axf = nullptr, *lstd = nullptr;
     double *xin = nullptr, *lin = nullptr;
+    double *c = nullptr, *sref = nullptr;   // refined form: anchor layer product and its operand
     unsigned long long* red = nullptr;   // 3 slots x 8 reduction words (bits of non-negative doubles)
     unsigned* bar = nullptr;             // grid barrier [count, generation]
     int* out_i = nullptr;                // status, iters, rho_index, switches, err

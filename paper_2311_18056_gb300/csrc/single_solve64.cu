@@ -11,6 +11,14 @@
 // equality rows near 1e-5..1e-4, above the 1e-6 tolerance of the random-QP
 // benchmark (Sec. V-A); in FP64 the same noise is ~1e-16 |Ax| rho_eq.
 //
+// Refined form (opts.single_precision = RELU_QP_PREC_FP64R): the FP64 layer
+// product is computed once per check interval (the anchor), c = Wt s_ref + b,
+// and the other layers apply the FP32 bank to the increment only,
+// t = c + Wt32 (s - s_ref), with the element-wise step, the state and the
+// checks in FP64.  The FP32 rounding then scales with |s - s_ref|, which
+// shrinks as the solve converges, and each layer costs an FP32 row product
+// instead of an FP64 one (GB300's FP64 rate is ~1/60 of its FP32 rate).
+//
 // Work split: the R = n + m rows of Wt (FP64, R x R) are cut into contiguous
 // slices, one per CTA of 16 warps; each warp produces one row at a time (lanes over the
 // columns, shuffle reduction); the operand s lives in shared memory.  Rows
@@ -36,6 +44,9 @@ enum { OUT_STATUS = 0, OUT_ITERS, OUT_RHO, OUT_SWITCHES, OUT_ERR, OUT_WORDS = 8 
 struct SP64 {
     int n, m, R, nr;
     const double* Wt[RQ_MAX_RHO];
+    const float* Wt32[RQ_MAX_RHO];   // refined form: FP32 bank, rows of ldw floats (zero padded)
+    int ldw, anchor_every;
+    double *c, *sref;                // refined form: anchor product and operand (R each)
     const double* bias[RQ_MAX_RHO];
     double rho[RQ_MAX_RHO];
     const double *P, *A, *At, *q, *l, *u;
@@ -81,6 +92,26 @@ __device__ __forceinline__ double row_dot(const double* __restrict__ w, const do
     return warp_sum(((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7])));
 }
 
+// FP32 row (ld floats, 16-byte aligned, zero padded) times an FP32 vector in
+// shared memory; the result is valid in every lane.
+__device__ __forceinline__ float row_dot32(const float* __restrict__ w, const float* __restrict__ s, int ld, int lane) {
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int k = lane; k < (ld >> 2); k += 32) {
+        const float4 a = __ldg(w4 + k);
+        const float4 b = s4[k];
+        a0 = fmaf(a.x, b.x, a0);
+        a1 = fmaf(a.y, b.y, a1);
+        a2 = fmaf(a.z, b.z, a2);
+        a3 = fmaf(a.w, b.w, a3);
+    }
+    float v = (a0 + a1) + (a2 + a3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Vector written by other CTAs into shared memory, bypassing L1.
 __device__ __forceinline__ void load_shared_cg(double* dst, const double* src, int len) {
     for (int k = threadIdx.x; k < len; k += blockDim.x) dst[k] = __ldcg(src + k);
@@ -94,8 +125,9 @@ __device__ __forceinline__ double red_get(const unsigned long long* slot, int wo
     return __longlong_as_double((long long)__ldcg(slot + word));
 }
 
+template <bool REFINED>
 __global__ void __launch_bounds__(kThreads, 1) single64_kernel(SP64 p) {
-    extern __shared__ __align__(16) double sv[];   // R doubles
+    extern __shared__ __align__(16) double sv[];   // R doubles (refined layers: ldw floats of the increment)
     __shared__ int s_ok;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n, m = p.m, R = p.R;
@@ -110,15 +142,34 @@ __global__ void __launch_bounds__(kThreads, 1) single64_kernel(SP64 p) {
         // ---------------- one layer: s[cur] -> s[cur^1] ----------------
         const double* scur = cur ? p.s1 : p.s0;
         double* snext = cur ? p.s0 : p.s1;
-        load_shared_cg(sv, scur, R);
+        // refined form: an FP64 anchor layer at the start of every check interval (so also
+        // after every bank switch), FP32 increment layers in between
+        const bool anchor = !REFINED || (it - 1) % p.anchor_every == 0;
+        float* dv = reinterpret_cast<float*>(sv);
+        if (anchor) {
+            load_shared_cg(sv, scur, R);
+        } else {
+            for (int k = threadIdx.x; k < p.ldw; k += blockDim.x)
+                dv[k] = k < R ? (float)(__ldcg(scur + k) - __ldcg(p.sref + k)) : 0.f;
+        }
         __syncthreads();
         const double* Wg = p.Wt[ri];
         const double* bias = p.bias[ri];
         const double rho = p.rho[ri];
         for (int r = row0 + warp; r < row1; r += kWarps) {
-            const double acc = row_dot(Wg + (size_t)r * R, sv, R, lane);
+            const double acc = anchor ? row_dot(Wg + (size_t)r * R, sv, R, lane)
+                                      : (double)row_dot32(p.Wt32[ri] + (size_t)r * p.ldw, dv, p.ldw, lane);
             if (lane == 0) {
-                const double t = acc + __ldg(bias + r);
+                double t;
+                if (!REFINED) {
+                    t = acc + __ldg(bias + r);
+                } else if (anchor) {
+                    t = acc + __ldg(bias + r);
+                    p.c[r] = t;
+                    p.sref[r] = scur[r];
+                } else {
+                    t = p.c[r] + acc;
+                }
                 if (r < n) {
                     p.y[r] = t;
                     snext[r] = t;
@@ -293,7 +344,12 @@ void fill_params(relu_qp_t h, SP64& p, int grid) {
     p.m = h->m;
     p.R = h->R;
     p.nr = h->nr;
+    p.ldw = h->ldw;
+    p.anchor_every = h->opts.check_interval > 0 ? h->opts.check_interval : 25;
+    p.c = h->sw64.c;
+    p.sref = h->sw64.sref;
     for (int r = 0; r < h->nr; ++r) {
+        p.Wt32[r] = h->be[r].Wt;
         p.Wt[r] = h->be[r].Wt64;
         p.bias[r] = h->be[r].bias64;
         p.rho[r] = h->be[r].rho;
@@ -312,7 +368,16 @@ void fill_params(relu_qp_t h, SP64& p, int grid) {
     p.qnorm = h->qnorm;
 }
 
-size_t smem64(relu_qp_t h) { return sizeof(double) * (size_t)h->R; }
+// the operand in shared memory: R doubles, or (refined layers) ldw floats of the increment
+size_t smem64(relu_qp_t h) {
+    return std::max(sizeof(double) * (size_t)h->R, sizeof(float) * (size_t)h->ldw);
+}
+
+bool refined(relu_qp_t h) { return h->opts.single_precision == RELU_QP_PREC_FP64R; }
+
+const void* kernel_for(relu_qp_t h) {
+    return refined(h) ? (const void*)single64_kernel<true> : (const void*)single64_kernel<false>;
+}
 
 int init_state(relu_qp_t h, const double* x, const double* lam, int rho_index) {
     SingleWork64& w = h->sw64;
@@ -341,9 +406,9 @@ int launch(relu_qp_t h, int grid, int rho_index, double eps_abs, double eps_rel,
     RQ_CUDA(h, cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2, h->stream));
     RQ_CUDA(h, cudaMemsetAsync(w.out_i, 0, sizeof(int) * OUT_WORDS, h->stream));
     const size_t smem = smem64(h);
-    RQ_CUDA(h, cudaFuncSetAttribute(single64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RQ_CUDA(h, cudaFuncSetAttribute(kernel_for(h), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     void* args[] = {&p};
-    RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)single64_kernel, dim3(grid), dim3(kThreads), args, smem,
+    RQ_CUDA(h, cudaLaunchCooperativeKernel(kernel_for(h), dim3(grid), dim3(kThreads), args, smem,
                                            h->stream));
     return RELU_QP_OK;
 }
@@ -363,7 +428,7 @@ int single64_alloc(relu_qp_t h, const double* P, const double* A) {
     RQ_TRY(alloc(h, &h->u64, (size_t)mm));
     for (int r = 0; r < h->nr; ++r) RQ_TRY(alloc(h, &h->be[r].bias64, (size_t)R));
     SingleWork64& w = h->sw64;
-    for (double** v : {&w.y, &w.z, &w.lam, &w.Ay, &w.s0, &w.s1, &w.Py, &w.Axf, &w.lstd, &w.xin, &w.lin})
+    for (double** v : {&w.y, &w.z, &w.lam, &w.Ay, &w.s0, &w.s1, &w.Py, &w.Axf, &w.lstd, &w.xin, &w.lin, &w.c, &w.sref})
         RQ_TRY(alloc(h, v, (size_t)R));
     RQ_TRY(alloc(h, &w.red, 3 * RED_WORDS));
     RQ_TRY(alloc(h, &w.bar, 2));
@@ -411,8 +476,8 @@ int single64_upload(relu_qp_t h, const double* q, const double* l, const double*
 int single64_prepare(relu_qp_t h) {
     int per_sm = 0;
     const size_t smem = smem64(h);
-    RQ_CUDA(h, cudaFuncSetAttribute(single64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, single64_kernel, kThreads, smem));
+    RQ_CUDA(h, cudaFuncSetAttribute(kernel_for(h), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(h), kThreads, smem));
     if (per_sm < 1) return fail(h, RELU_QP_ERR_UNSUPPORTED, "FP64 solve kernel does not fit on an SM");
     std::vector<int> cands;
     for (int g = 1; g <= h->num_sms; g *= 2) cands.push_back(g);

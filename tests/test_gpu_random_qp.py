@@ -9,7 +9,10 @@ FP64 oracle, through the C ABI.
   the oracle's, residuals recomputed in FP64 from the returned vectors within
   1e-6 and the reported ones equal to them;
 * with the scaling step, warm starts, and the equality-row accuracy that FP32
-  cannot reach (the FP32 path stalls above 1e-6 on the same problem).
+  cannot reach (the FP32 path stalls above 1e-6 on the same problem);
+* the FP64-anchored form (FP32 products of the layer increments between FP64
+  anchor layers) reaches the same 1e-6 at every size, within one check of the
+  oracle's layer count and 1e-5 of its x.
 """
 import numpy as np
 import pytest
@@ -149,3 +152,32 @@ def test_fp64_degenerate_shapes(rq):
     one = s.solve(eps_abs=EPS, max_iter=1)
     s.close()
     assert one["iters"] == 1 and one["status"] == rq.MAX_ITER
+
+
+@pytest.mark.parametrize("n", R.SIZES)
+def test_fp64_anchored_converges_at_1e6(rq, n):
+    P, q, A, l, u = R.random_dense_qp(0, n)
+    s = rq.ReluQP(P, A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, single_precision=rq.PREC_FP64R)
+    out = s.solve(eps_abs=EPS, max_iter=4000)
+    warm = s.solve(x_warm=out["x"], lam_warm=out["lam"], rho_index=out["rho_index"], eps_abs=EPS)
+    s.close()
+    orc = O.solve(P, q, A, l, u, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS, max_iter=4000)
+    res = O.residuals(P, q, A, out["x"], out["z"], out["lam"])
+    assert out["status"] == rq.SOLVED, n
+    assert res["r_prim"] <= EPS and res["r_dual"] <= EPS, (n, res)
+    assert abs(out["iters"] - orc.iters) <= 25, (n, out["iters"], orc.iters)
+    assert np.max(np.abs(out["x"] - orc.x)) <= 1e-5, n
+    assert warm["status"] == rq.SOLVED and warm["iters"] == 25
+
+
+def test_fp64_anchored_first_layers_match_fp64(rq):
+    """Within one anchor period the anchored layers are the FP64 layers up to the FP32
+    rounding of the increment products (1e-6 relative over 24 layers)."""
+    P, q, A, l, u = R.random_dense_qp(1, 342)
+    outs = []
+    for prec in (rq.PREC_FP64, rq.PREC_FP64R):
+        s = rq.ReluQP(P, A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, check_interval=25, single_precision=prec)
+        outs.append(s.solve(rho_index=1, max_iter=24, eps_abs=0.0))
+        s.close()
+    assert rel(outs[1]["x"], outs[0]["x"]) <= 1e-6
+    assert rel(outs[1]["z"], outs[0]["z"]) <= 1e-6
