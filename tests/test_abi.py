@@ -100,3 +100,24 @@ def test_new_options_are_validated_without_gpu(libpath):
     with pytest.raises(rq.ReluQPError) as e:
         rq.condense_mpc(np.array([[np.inf, 0], [0, 1]]), np.ones((2, 1)), np.eye(2), np.eye(1), 3)
     assert e.value.kind == "INVALID"
+
+
+def test_product_path_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: without librelu_qp.so every entry point raises before any work."""
+    import numpy as np
+    import paper_2311_18056_gb300 as rq
+    monkeypatch.setattr(rq, "library_path", str(tmp_path / "librelu_qp.so"))
+    monkeypatch.setattr(rq, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        rq.ReluQP(np.eye(2), np.eye(2), -np.ones(2), np.ones(2))
+    with pytest.raises(RuntimeError, match="missing"):
+        rq.condense_mpc(np.eye(2), np.ones((2, 1)), np.eye(2), np.eye(1), 3)
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The binding, the package and the workload generators load without `oracle`."""
+    import subprocess
+    import sys
+    code = ("import sys, paper_2311_18056_gb300, paper_2311_18056_gb300.build, workloads.mpc, "
+            "workloads.random_qp; assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
+    subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
