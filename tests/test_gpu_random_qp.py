@@ -181,3 +181,17 @@ def test_fp64_anchored_first_layers_match_fp64(rq):
         s.close()
     assert rel(outs[1]["x"], outs[0]["x"]) <= 1e-6
     assert rel(outs[1]["z"], outs[0]["z"]) <= 1e-6
+
+
+def test_fp64_anchored_with_scaling(rq):
+    """The anchored form on a scaled problem: residuals of the original problem within 1e-6."""
+    P, q, A, l, u = R.random_dense_qp(0, 105)
+    s = rq.ReluQP(P, A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, scaling_iters=10, single_precision=rq.PREC_FP64R)
+    out = s.solve(eps_abs=EPS, max_iter=4000)
+    s.close()
+    orc = O.solve_scaled(P, q, A, l, u, scaling_iters=10, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS, max_iter=4000)
+    res = O.residuals(P, q, A, out["x"], out["z"], out["lam"])
+    assert out["status"] == rq.SOLVED
+    assert res["r_prim"] <= EPS * (1 + 1e-6) and res["r_dual"] <= EPS * (1 + 1e-6)
+    assert abs(out["iters"] - orc.iters) <= 25
+    assert np.max(np.abs(out["x"] - orc.x)) <= 1e-5
