@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--random-qp", action="store_true",
                     help="random dense QPs of Sec. V-A: FP64 single solves to 1e-6 per size")
     ap.add_argument("--rqp-count", type=int, default=10, help="random QPs per size")
+    ap.add_argument("--rqp-sizes", type=str, default="", help="comma-separated subset of the ten sizes")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -521,7 +522,8 @@ def run_random_qp(args):
     eps = 1e-6
     per_size = []
     cores = blas_threads()
-    for n in R.SIZES:
+    sizes = [int(v) for v in args.rqp_sizes.split(",")] if args.rqp_sizes else list(R.SIZES)
+    for n in sizes:
         ms, iters, solved, wall = [], [], 0, []
         ms_r, iters_r, solved_r = [], [], 0
         for seed in range(args.rqp_count):
