@@ -81,6 +81,7 @@ struct SingleWork64 {
     double *Py = nullptr, *Axf = nullptr, *lstd = nullptr;
     double *xin = nullptr, *lin = nullptr;
     double *c = nullptr, *sref = nullptr;   // refined form: anchor layer product and its operand
+    float* d32 = nullptr;                   // refined form: FP32 increment of the next layer (ldw)
     unsigned long long* red = nullptr;   // 3 slots x 8 reduction words (bits of non-negative doubles)
     unsigned* bar = nullptr;             // grid barrier [count, generation]
     int* out_i = nullptr;                // status, iters, rho_index, switches, err

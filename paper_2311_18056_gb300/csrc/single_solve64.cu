@@ -47,6 +47,7 @@ struct SP64 {
     const float* Wt32[RQ_MAX_RHO];   // refined form: FP32 bank, rows of ldw floats (zero padded)
     int ldw, anchor_every;
     double *c, *sref;                // refined form: anchor product and operand (R each)
+    float* d32;                      // refined form: (float)(s - s_ref) of the next layer (ldw, zero padded)
     const double* bias[RQ_MAX_RHO];
     double rho[RQ_MAX_RHO];
     const double *P, *A, *At, *q, *l, *u;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, 1) single64_kernel(SP64 p) {
             load_shared_cg(sv, scur, R);
         } else {
             for (int k = threadIdx.x; k < p.ldw; k += blockDim.x)
-                dv[k] = k < R ? (float)(__ldcg(scur + k) - __ldcg(p.sref + k)) : 0.f;
+                dv[k] = __ldcg(p.d32 + k);   // written by the owners of the rows in the last layer
         }
         __syncthreads();
         const double* Wg = p.Wt[ri];
@@ -173,6 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1) single64_kernel(SP64 p) {
                 if (r < n) {
                     p.y[r] = t;
                     snext[r] = t;
+                    if (REFINED) p.d32[r] = (float)(t - p.sref[r]);
                 } else {
                     const int i = r - n;
                     const double rho_i = rho * (double)__ldg(p.rs + i);
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1) single64_kernel(SP64 p) {
                     p.z[i] = zn;
                     p.lam[i] = ln;
                     snext[r] = 2.0 * rho_i * zn - ln;
+                    if (REFINED) p.d32[r] = (float)(snext[r] - p.sref[r]);
                 }
             }
         }
@@ -348,6 +351,7 @@ void fill_params(relu_qp_t h, SP64& p, int grid) {
     p.anchor_every = h->opts.check_interval > 0 ? h->opts.check_interval : 25;
     p.c = h->sw64.c;
     p.sref = h->sw64.sref;
+    p.d32 = h->sw64.d32;
     for (int r = 0; r < h->nr; ++r) {
         p.Wt32[r] = h->be[r].Wt;
         p.Wt[r] = h->be[r].Wt64;
@@ -430,6 +434,7 @@ int single64_alloc(relu_qp_t h, const double* P, const double* A) {
     SingleWork64& w = h->sw64;
     for (double** v : {&w.y, &w.z, &w.lam, &w.Ay, &w.s0, &w.s1, &w.Py, &w.Axf, &w.lstd, &w.xin, &w.lin, &w.c, &w.sref})
         RQ_TRY(alloc(h, v, (size_t)R));
+    RQ_TRY(alloc(h, &w.d32, (size_t)h->ldw));   // zero beyond R (set once here)
     RQ_TRY(alloc(h, &w.red, 3 * RED_WORDS));
     RQ_TRY(alloc(h, &w.bar, 2));
     RQ_TRY(alloc(h, &w.out_i, OUT_WORDS));
