@@ -330,45 +330,59 @@ template <int NB, int BN, int STAGES, int KSTAGE, int KA>
 __device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtensorMap* tmA32, const CUtensorMap* tmB,
                                            uint32_t sbase, uint32_t bar0, int nkb, int koff, int g0, int a0, int a1,
                                            int b0, int b1, unsigned gmask, const unsigned* sync, unsigned target,
-                                           int& issued, bool& sync_failed) {
+                                           int own_lo, int own_n, uint32_t own_bar, uint32_t own_par, int& issued,
+                                           bool& sync_failed) {
     const int brow[2] = {b0, b1}, arow[3] = {a0, a1, 0};
     const uint32_t tx = (uint32_t)(KSTAGE - KA) + operand_bytes<2>(gmask);
     const int pre = nkb < STAGES ? nkb : STAGES;
-    for (int kb = 0; kb < pre; ++kb) {
-        const int gk = g0 + kb, s = gk % STAGES;
+    // k blocks in the order own_lo, own_lo + 1, ... (wrapping): the first own_n of them hold only
+    // rows this CTA's own epilogue wrote
+    auto kb_at = [&](int i) { return (i + own_lo) % nkb; };
+    for (int i = 0; i < pre; ++i) {
+        const int gk = g0 + i, s = gk % STAGES;
         if (!mbar_wait(bar0 + 8 * (STAGES + s), ((gk / STAGES) & 1) ^ 1)) return false;
         const uint32_t full = bar0 + 8 * s;
         mbar_expect_tx(full, tx);
 #pragma unroll
         for (int b = 0; b < NB; ++b)
-            tma_load_2d(sbase + s * KSTAGE + KA + b * BN * 128, tmB, kb * kBK + koff, brow[b], full);
+            tma_load_2d(sbase + s * KSTAGE + KA + b * BN * 128, tmB, kb_at(i) * kBK + koff, brow[b], full);
     }
-    if (sync) {
-        const long long t0 = gtime();
-        while (true) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sync) : "memory");
-            if (v >= target) break;
-            if (gtime() - t0 > kWaitNs) {
-                sync_failed = true;
-                return false;
-            }
-        }
-        // the operand was written by generic stores of other CTAs; order them before the TMA reads
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-    } else {
-        griddep_wait();
-    }
-    for (int kb = 0; kb < nkb; ++kb) {
-        const int gk = g0 + kb, s = gk % STAGES;
+    if (!sync) griddep_wait();
+    bool own_ready = !sync || own_n == 0, tile_ready = !sync;
+    for (int i = 0; i < nkb; ++i) {
+        const int gk = g0 + i, s = gk % STAGES;
         const uint32_t full = bar0 + 8 * s;
         const uint32_t st = sbase + s * KSTAGE;
-        const int k0 = kb * kBK + koff;
-        if (kb >= pre) {
+        const int k0 = kb_at(i) * kBK + koff;
+        if (i >= pre) {
             if (!mbar_wait(bar0 + 8 * (STAGES + s), ((gk / STAGES) & 1) ^ 1)) return false;
             mbar_expect_tx(full, tx);
 #pragma unroll
             for (int b = 0; b < NB; ++b) tma_load_2d(st + KA + b * BN * 128, tmB, k0, brow[b], full);
+        }
+        if (i < own_n && !own_ready) {
+            // rows this CTA wrote itself: its epilogue warps have stored them and fenced
+            // them for the async proxy before arriving on own_bar
+            if (!mbar_wait(own_bar, own_par)) {
+                sync_failed = true;
+                return false;
+            }
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            own_ready = true;
+        } else if (i >= own_n && !tile_ready) {
+            const long long t0 = gtime();
+            while (true) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sync) : "memory");
+                if (v >= target) break;
+                if (gtime() - t0 > kWaitNs) {
+                    sync_failed = true;
+                    return false;
+                }
+            }
+            // the operand was written by generic stores of other CTAs; order them before the TMA reads
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            tile_ready = true;
         }
         load_operand<2>(tmA, tmA32, st, k0, arow, gmask, full);
         issued = gk + 1;
@@ -919,8 +933,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     float* recv = reinterpret_cast<float*>(smem + STAGES * L::kStage + L::kXpose);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * L::kStage + L::kXpose + L::kRecv);
     // bars[2S] accumulator ready, bars[2S+1] partners' partial sums received,
-    // bars[2S+2] accumulator consumed (the epilogue warps read all of a layer's TMEM)
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
+    // bars[2S+2] accumulator consumed (the epilogue warps read all of a layer's TMEM),
+    // bars[2S+3] this CTA's rows of the layer stored (for its producer's own k blocks)
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
     int& s_fail = *reinterpret_cast<int*>(tmem_holder + 1);   // in the dynamic area: no static shared memory
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -932,6 +947,7 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
         mbar_init(smem_u32(&bars[2 * STAGES]), 1);
         mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * HALVES);
         mbar_init(smem_u32(&bars[2 * STAGES + 2]), 4 * HALVES);   // one arrival per epilogue warp
+        mbar_init(smem_u32(&bars[2 * STAGES + 3]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
@@ -958,6 +974,13 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             for (int gr = 0; gr < 4; ++gr)
                 if (p.perm[slot0 + 32 * gr] >= 0) gmask |= 1u << gr;
             const int b0 = g.b_row[0] + ri * g.b_rho_stride + row0, b1 = g.b_row[1] + ri * g.b_rho_stride + row0;
+            // without a K split, the k blocks made only of this CTA's own rows are loaded first,
+            // after its own epilogue and before the tile's counter; every other k block
+            // still waits for the whole tile (which also keeps each layer's epilogue from
+            // overwriting an operand buffer another CTA may still read)
+            const int own_lo = KS == 1 ? (row0 + kBK - 1) / kBK : 0;
+            const int own_hi = KS == 1 ? min(row0 + BN, g.rows) / kBK : 0;
+            const int own_n = (KS == 1 && own_hi > own_lo && own_hi - own_lo < kb_count) ? own_hi - own_lo : 0;
             int issued = 0;
             bool sync_failed = false;
             for (int j = 1; j <= c.nl; ++j) {
@@ -966,7 +989,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 const bool ok = produce_layer<2, BN, STAGES, L::kStage, L::kA>(
                     &tmA, &tmA32, &tmB, smem_u32(smem), smem_u32(bars), kb_count, g.k_off + kb_begin * kBK,
                     (j - 1) * kb_count, a0, a0 + c.slots, b0, b1, gmask, j == 1 ? nullptr : c.sync + tile,
-                    (unsigned)(j - 1) * nct, issued, sync_failed);
+                    (unsigned)(j - 1) * nct, own_n ? own_lo : 0, own_n, smem_u32(&bars[2 * STAGES + 3]),
+                    (uint32_t)((j - 2) & 1), issued, sync_failed);
                 if (!ok) {
                     wait_failed(g.err, sync_failed ? WS_PROD_SYNC : WS_PROD_EMPTY);
                     s_fail = 1;
@@ -1043,6 +1067,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
                 : "memory");
             if (any) break;
             if (warp == 2 && lane == 0) {
+                // this CTA's rows of layer j are stored (each epilogue thread fenced them for the
+                // async proxy before the barrier above): its producer may load them
+                if (j < c.nl) mbar_arrive(smem_u32(&bars[2 * STAGES + 3]));
                 if (j < c.nl) {
                     // a release at GPU scope: it orders this CTA's stores of layer j (those of the
                     // other epilogue warps through the barrier above) before the counter's increment
