@@ -153,7 +153,14 @@ def _stream_handle(stream):
 
 
 class ReluQP:
-    """One QP  min 1/2 x'Px + q'x  s.t.  l <= Ax <= u  with its bank of layers on the GPU."""
+    """One QP  min 1/2 x'Px + q'x  s.t.  l <= Ax <= u  with its bank of layers on the GPU.
+
+    Keyword options mirror relu_qp_opts (include/relu_qp.h): check_interval,
+    adaptive_rho, rho0, eq_scale, keep_fp64, max_batch (> 0 enables the batched
+    entry points), precision (batched: PREC_FP32 or PREC_BF16X3), stream (a CUDA
+    stream or its handle), scaling_iters (Algorithm 1's scaling step: modified
+    Ruiz iterations at setup, 0 = off) and single_precision (single solves:
+    PREC_FP32, PREC_FP64 or PREC_FP64R, the FP64-anchored form)."""
 
     def __init__(self, P, A, l, u, q=None, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), *, check_interval=25,
                  adaptive_rho=True, rho0=0.1, eq_scale=1e3, keep_fp64=False, max_batch=0,
