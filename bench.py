@@ -57,6 +57,14 @@ def parse():
                     help="random dense QPs of Sec. V-A: FP64 single solves to 1e-6 per size")
     ap.add_argument("--rqp-count", type=int, default=10, help="random QPs per size")
     ap.add_argument("--rqp-sizes", type=str, default="", help="comma-separated subset of the ten sizes")
+    ap.add_argument("--closed-loop", action="store_true",
+                    help="random-MPC closed loop (Sec. V-B): single-QP FP32 solves, warm-started, per nu")
+    ap.add_argument("--cl-nus", type=str, default="4,8,16,32,40", help="closed loop: comma-separated nu values")
+    ap.add_argument("--cl-steps", type=int, default=100, help="closed loop: MPC steps per nu")
+    ap.add_argument("--humanoid", action="store_true",
+                    help="humanoid-sized QP (n=600, m=1000): single FP32 solves and a BF16-split batch of 256")
+    ap.add_argument("--serve-rates", type=str, default="",
+                    help="served stream: comma-separated request rates to sweep (max sustainable rate)")
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -504,6 +512,7 @@ def run_serve(args):
             "p50_ms_by_family": [float(np.percentile(v, 50)) if v else None for v in lat_f],
             "p99_ms_by_family": [float(np.percentile(v, 99)) if v else None for v in lat_f],
             "unsolved": int(sum(1 for s_ in status if s_ != 0)), "requests": measured,
+            "offered_rate": args.rate, "sustained": bool(value >= 0.97 * args.rate),
             "fp32_one_at_a_time": {"mean_solve_ms_by_family": single_ms, "utilization_at_rate": util,
                                    "max_rate_req_per_s": float(1e3 / np.sum(mix * np.array(single_ms))),
                                    "stable": util < 1.0}}
@@ -573,8 +582,189 @@ def run_random_qp(args):
     print(json.dumps(line), flush=True)
 
 
+def single_roofline(n, m, layers, ms):
+    """Achieved bandwidth of the single-QP FP32 layer: one layer reads the FP32
+    bank entry Wt ((n+m) x (n+m), 4 bytes each); bytes x layers / device time."""
+    bytes_per_layer = 4.0 * (n + m) ** 2
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    gbs = bytes_per_layer * layers / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+            "bytes_per_layer": bytes_per_layer, "peak_kind": "measured copy bandwidth",
+            "note": "algorithmic bytes of the bank entry per layer; the entry is served from L2 and shared memory "
+                    "when it fits, so frac > 1 would mean on-chip reuse"}
+
+
+def run_closed_loop(args):
+    """Random linear MPC in closed loop (config 1; Sec. V-B): per nu, 100 MPC
+    steps x+ = A x + B u0 + w, each QP solved to eps=1e-3 by the single-QP FP32
+    path, warm-started from the previous step's (x, lam, rho); reports the
+    device solve time p50/p99, layers, active-limit fraction, the layer's
+    achieved bytes/s and the FP64 oracle on the first steps."""
+    import torch
+    import paper_2311_18056_gb300 as rq
+    from paper_2311_18056_gb300 import build as _build
+    from workloads import mpc
+    from oracle import relu_qp_oracle as O
+    _build.build()
+    torch.cuda.set_device(0)
+    per_nu = []
+    for nu in [int(v) for v in args.cl_nus.split(",")]:
+        pq, X0, x0_std = mpc.workload(f"sweep{nu}", 1)
+        W = mpc.disturbances(pq, args.cl_steps, 0.1)
+        x = X0[0].copy()
+        q, l, u = pq.instance(x)
+        s = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+        s.solve(eps_abs=EPS)                  # first launch of the handle (not timed)
+        warm = None
+        ms, call_ms, layers, active, status, oracle_ms, oracle_err = [], [], [], [], [], [], []
+        for k in range(args.cl_steps):
+            q, l, u = pq.instance(x)
+            if args.profile_window and k == 1:
+                torch.cuda.profiler.start()
+            t0 = time.perf_counter()
+            s.update(q, l, u)
+            if warm is None:
+                r = s.solve(eps_abs=EPS)
+            else:
+                r = s.solve(x_warm=warm["x"], lam_warm=warm["lam"], rho_index=warm["rho_index"], eps_abs=EPS)
+            call_ms.append(1e3 * (time.perf_counter() - t0))
+            if args.profile_window and k == 1:
+                torch.cuda.profiler.stop()
+            ms.append(r["solve_ms"])
+            layers.append(r["iters"])
+            status.append(r["status"])
+            Ax = pq.A @ r["x"]
+            active.append(float(np.mean((Ax <= l + 1e-3) | (Ax >= u - 1e-3))))
+            if k < 3:
+                t1 = time.perf_counter()
+                o = O.solve(pq.P, q, pq.A, l, u, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS)
+                oracle_ms.append(1e3 * (time.perf_counter() - t1))
+                oracle_err.append(float(np.max(np.abs(o.x - r["x"]))))
+            warm = r
+            x = pq.Ad @ x + pq.Bd @ pq.first_control(x, r["x"]) + W[k]
+        s.close()
+        roof = single_roofline(pq.n, pq.m, float(np.sum(layers)), float(np.sum(ms)))
+        per_nu.append({"nu": nu, "n": pq.n, "m": pq.m, "steps": args.cl_steps, "x0_std": x0_std,
+                       "solved": int(sum(1 for v in status if v == rq.SOLVED)),
+                       "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                       "p50_call_ms": float(np.percentile(call_ms, 50)),
+                       "solves_per_s": 1e3 / float(np.mean(ms)), "mean_layers": float(np.mean(layers)),
+                       "us_per_layer": 1e3 * float(np.sum(ms)) / float(np.sum(layers)),
+                       "active_fraction": float(np.mean(active)), "roofline": roof,
+                       "oracle_ms_first3": oracle_ms, "max_abs_err_vs_oracle_first3": oracle_err})
+        print(f"nu={nu}: p50 {per_nu[-1]['p50_ms']:.3f} ms p99 {per_nu[-1]['p99_ms']:.3f} ms, layers "
+              f"{np.mean(layers):.0f}, {roof['achieved']:.0f} GB/s", file=sys.stderr, flush=True)
+    big = per_nu[-1]
+    line = {"metric": "closed-loop random MPC: single-QP FP32 solve time at eps=1e-3 (one GB300)",
+            "value": big["p50_ms"], "unit": "ms", "n_gpus": 1, "higher_is_better": False, "dtype": "f32",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "random linear MPC, horizon 40, nx = 3 nu, |u| <= 1, LQR-preconditioned "
+                                   "condensing (n = m = 40 nu); x0 scaled so the limits bind, w ~ N(0, 0.1^2); "
+                                   "each step warm-started from the previous solve", "nus": [p["nu"] for p in per_nu]},
+            "per_nu": per_nu,
+            "cpu_baseline": {"value": float(np.mean(big["oracle_ms_first3"])), "unit": "ms",
+                             "cores": blas_threads(), "kind": "oracle",
+                             "sample": f"first 3 closed-loop steps at nu={big['nu']} solved by the FP64 oracle"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_humanoid(args):
+    """Humanoid-sized QP (config 3: n = 600, m = 1000 with 400 dense
+    inequalities): single-QP FP32 solves one at a time and one BF16-split batch
+    of 256 QPs, both to eps = 1e-3, with the oracle on a bounded sample."""
+    import torch
+    import paper_2311_18056_gb300 as rq
+    from paper_2311_18056_gb300 import build as _build
+    from workloads import mpc
+    from oracle import relu_qp_oracle as O
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pq, X0, x0_std = mpc.workload("humanoid", 256 + 32)
+    q, l, u = pq.instance(X0[0])
+    # single FP32, one at a time
+    s = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+    s.solve(eps_abs=EPS)
+    ms, layers, solved = [], [], 0
+    for x0 in X0[256:256 + 32]:
+        s.update(*pq.instance(x0))
+        r = s.solve(eps_abs=EPS)
+        ms.append(r["solve_ms"])
+        layers.append(r["iters"])
+        solved += int(r["status"] == rq.SOLVED)
+    s.close()
+    single = {"solves": len(ms), "solved": solved, "p50_ms": float(np.percentile(ms, 50)),
+              "p99_ms": float(np.percentile(ms, 99)), "solves_per_s": 1e3 / float(np.mean(ms)),
+              "mean_layers": float(np.mean(layers)),
+              "roofline": single_roofline(pq.n, pq.m, float(np.sum(layers)), float(np.sum(ms)))}
+    # batched BF16 split x 256
+    B = 256
+    sb = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK, max_batch=B, precision=rq.PREC_BF16X3)
+    sb.set_parametric(pq.F, pq.E, pq.l0, pq.u0)
+    X = torch.from_numpy(X0[:B].astype(np.float32)).to(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sb.update_batch_x0(X)
+        sb.solve_batch(eps_abs=EPS)
+    sb.profile(enable=1, reset=True)
+    tt, unsolved = [], 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        sb.update_batch_x0(X)
+        out = sb.solve_batch(eps_abs=EPS)
+        b.record()
+        torch.cuda.synchronize()
+        tt.append(a.elapsed_time(b))
+        unsolved += int(np.sum(out["status"] != rq.SOLVED))
+    prof = sb.profile(enable=0)
+    sb.close()
+    peak_sus, _, peak_kind = measured_peaks()
+    roof = None
+    if prof["layer_timed"] > 0:
+        achieved = prof["layer_flops"] / (prof["layer_ms"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_sus, "unit": "TFLOP/s",
+                "frac": achieved / peak_sus, "peak_kind": f"bf16 sustained, {peak_kind}",
+                "avg_layer_us": 1e3 * prof["layer_ms"] / prof["layer_timed"]}
+    # oracle on a bounded sample
+    t0 = time.perf_counter()
+    worst = 0.0
+    for b in range(2):
+        qb, lb, ub = pq.instance(X0[b].astype(np.float32).astype(np.float64))
+        o = O.solve(pq.P, qb, pq.A, lb, ub, sigma=SIGMA, rho_bank=BANK, eps_abs=EPS)
+        worst = max(worst, float(np.max(np.abs(o.x - out["x"][b]))))
+    oracle_ms = 1e3 * (time.perf_counter() - t0) / 2
+    batched = {"batch": B, "ms_per_batch": float(np.mean(tt)), "solves_per_s": B / (float(np.mean(tt)) / 1e3),
+               "unsolved": unsolved, "mean_layers": float(np.mean(out["iters"])), "roofline": roof,
+               "max_abs_err_vs_oracle_2": worst}
+    line = {"metric": "humanoid-sized QP (n=600, m=1000): QP solves/s at eps=1e-3, batched BF16-split x256 "
+                      "and single FP32 (one GB300)",
+            "value": batched["solves_per_s"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "bf16",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "humanoid-sized MPC nx=70 nu=30 N=20, block dynamics, |u|<=50 + 400 dense rows "
+                                   f"(n=600, m=1000), x0 ~ N(0, {x0_std:.3g}^2)", "batch": B},
+            "batched": batched, "single_fp32": single,
+            "speedup_batched_vs_single": batched["solves_per_s"] / single["solves_per_s"],
+            "cpu_baseline": {"value": 1e3 / oracle_ms, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": "2 humanoid QPs solved by the FP64 oracle"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.closed_loop:
+        run_closed_loop(args)
+        return
+    if args.humanoid:
+        run_humanoid(args)
+        return
+    if args.serve and args.serve_rates:
+        for r in args.serve_rates.split(","):
+            args.rate = float(r)
+            run_serve(args)
+        return
     if args.serve:
         run_serve(args)
     elif args.random_qp:

@@ -92,6 +92,13 @@ typedef struct relu_qp_opts {
                                layers: faster, iterates within rounding of FP64).  Both
                                keep the FP64 bank (as keep_fp64) and FP64 copies of P
                                and A; relu_qp_solve_noalloc refuses them. */
+    long long device_budget; /* cap, in bytes, on the device memory the handle keeps
+                               (layer bank, problem data, single-QP and batch state);
+                               0 = no cap.  An allocation that would pass it fails
+                               with RELU_QP_ERR_OOM before cudaMalloc is called.  The
+                               FP64 inputs and scratch of the offline stage, freed
+                               before relu_qp_setup returns, are not counted.  No
+                               counterpart in the paper (deployment limit). */
 } relu_qp_opts;
 
 #define RELU_QP_PREC_FP32    0   /* batched layer product in FP32 on the CUDA cores */
@@ -186,13 +193,17 @@ int relu_qp_solve(relu_qp_t h, const double* x_warm, const double* lam_warm, int
  *   x_warm, lam_warm  device FP32 (n / m) warm start, or NULL (lam_warm needs x_warm)
  *   rho_index_warm, eps_abs, eps_rel, max_iter, info: as relu_qp_solve
  *   x_out (n, required), z_out, lam_out (m, may be NULL): device FP32 outputs
+ * Unlike relu_qp_solve (host FP64 arrays), every array here is device FP32
+ * memory (or managed memory) of the handle's device; each non-NULL pointer is
+ * checked before any GPU work and anything else returns RELU_QP_ERR_INVALID.
  * Limits and rules: n + m <= 4096 (larger problems return RELU_QP_ERR_INVALID
  * before any GPU work).  All calls share the one array, so calls whose GPU
  * work overlaps (other streams or threads) race; order them.  The array keeps
  * the last call's contents; each call clears what must start at zero.  The
- * first call on each device looks the array's device address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.
+ * call is synchronous: it returns once the outputs and info are written.  The
+ * first call for each device looks the array's device address up
+ * (cudaGetSymbolAddress) with the handle's device current; make that first
+ * call before any stream capture.
  * Errors: INVALID, UNSUPPORTED (device ordinal >= 64, or a handle set up with
  * scaling_iters > 0), CUDA, TIMEOUT.
  */
@@ -320,8 +331,18 @@ int relu_qp_solve_batch(relu_qp_t h, int B, const float* X_warm, const float* La
  * z = A x, paper Sec. II-B "Warm Starting"), runs one chunk of check_interval
  * layers and the residual check for every family with work, each family on
  * its own stream so that their chunks overlap on the GPU, and retires the
- * QPs that finished (solved, max_iter reached, or non-finite).  Results keep
- * the request's tag and its submit and completion times on the server clock.
+ * QPs that finished (solved, max_iter reached, or non-finite).  Families
+ * advance independently: a family whose chunk has finished retires, admits
+ * and launches its next chunk at once, without waiting for the chunks of the
+ * other families.  Results keep the request's tag and its submit and
+ * completion times on the server clock.
+ * Admission by device memory (relu_qp_server_set_budget): each family's
+ * layer bank and fixed buffers are charged when the budget is set; every
+ * admitted request is charged its family's bytes per QP slot (the batch state
+ * it occupies on the device) until it retires.  A request waits while its
+ * family has no free slot or the budget has no room for it, and a request of
+ * one family is not admitted ahead of an older waiting request of another
+ * family whose room it would take.
  * While a server exists its families' handles run on the server's streams;
  * do not use them for other calls until relu_qp_server_destroy.
  */
@@ -346,9 +367,23 @@ int relu_qp_server_create(relu_qp_server_t* out, relu_qp_t const* families, int 
                           double eps_abs, double eps_rel, int max_iter);
 /* Queue one request: x0 host FP32 (nx of the family), client in [-1, clients). */
 int relu_qp_server_submit(relu_qp_server_t s, int family, int client, const float* x0, long long tag);
-/* One admission + chunk + retirement round for every family (blocks until its
- * chunks are done).  *active / *waiting (may be NULL): requests in slots / queued. */
+/* One round: every family without a chunk in flight admits waiting requests and
+ * launches its next chunk; every family whose chunk has finished retires its
+ * finished requests, admits and launches again.  Returns as soon as at least
+ * one family has finished a chunk in this call (or at once when no chunk is
+ * in flight); it does not wait for the other families.  *active / *waiting
+ * (may be NULL): requests in slots / queued. */
 int relu_qp_server_step(relu_qp_server_t s, int* active, int* waiting);
+/* Device-memory budget of the server in bytes (0 = slots only, the default).
+ * Errors: OOM when the families' banks and fixed buffers alone exceed it (the
+ * budget is then unchanged), INVALID for a negative value. */
+int relu_qp_server_set_budget(relu_qp_server_t s, long long bytes);
+/* Memory accounting of one family: fixed bytes (its handle's bank and problem
+ * data plus the server's buffers for it) and bytes per QP slot.  Any pointer
+ * may be NULL.  Errors: INVALID (family out of range). */
+int relu_qp_server_family_bytes(relu_qp_server_t s, int family, long long* fixed_bytes, long long* slot_bytes);
+/* Bytes charged by the requests now in slots, over every family. */
+long long relu_qp_server_bytes_in_use(relu_qp_server_t s);
 /* Pop up to max_results finished requests; x_out (may be NULL) receives each
  * result's x (FP32) at row stride x_stride floats.  Returns the number popped. */
 int relu_qp_server_poll(relu_qp_server_t s, int max_results, relu_qp_result* results, float* x_out, int x_stride);
@@ -385,6 +420,38 @@ int relu_qp_set_opts(relu_qp_t h, const relu_qp_opts* opts);
 
 /* Sizes of a handle (any pointer may be NULL). */
 int relu_qp_dims(relu_qp_t h, int* n, int* m, int* n_rho);
+
+/* Device memory the handle keeps, in bytes (what opts.device_budget caps);
+ * -1 for a NULL handle. */
+long long relu_qp_device_bytes(relu_qp_t h);
+
+/*
+ * ---- deadline diagnostics ---------------------------------------------------
+ * No counterpart in the paper.  Every device-side wait of the library (the
+ * grid barrier of the cooperative kernels, and the mbarrier and layer-counter
+ * waits of the tensor-core kernels) gives up at a deadline and reports
+ * RELU_QP_ERR_TIMEOUT instead of hanging the GPU.  These calls make one kind
+ * of wait run out on purpose, on the current device and the legacy stream,
+ * so that a test can see the status come back and the context stay usable.
+ *
+ * relu_qp_diag_device_wait -- kind 0: a cooperative launch of a few CTAs
+ *   whose grid barrier expects one arrival more than there are CTAs (every
+ *   CTA waits until timeout_ns); kind 1: the same barrier with the right
+ *   arrival count (passes; the control case); kind 2: an mbarrier wait that
+ *   nothing completes; kind 3: a layer-counter wait that nothing increments.
+ *   timeout_ns in [1e3, 1e9].  *status receives the kernel's error word
+ *   (RELU_QP_ERR_TIMEOUT, or 0 when the wait completed), *ms (may be NULL)
+ *   the device time of the launch.  Returns INVALID, OOM, CUDA, UNSUPPORTED
+ *   (no cooperative launch) or OK.
+ * relu_qp_diag_host_barrier -- the grid barrier's arrival and wait logic (the
+ *   template the kernels use) run by `threads` host threads for `rounds`
+ *   barriers, with an arrival count of threads + extra: extra = 0 passes
+ *   every round, extra > 0 makes every thread give up after timeout_ns.
+ *   *timeouts receives the number of threads that gave up, *ms (may be NULL)
+ *   the wall time.  Needs no GPU.  Returns INVALID or OK.
+ */
+int relu_qp_diag_device_wait(int kind, long long timeout_ns, int* status, double* ms);
+int relu_qp_diag_host_barrier(int threads, int extra, int rounds, long long timeout_ns, int* timeouts, double* ms);
 
 /* Free every device and host resource of h (NULL is a no-op). */
 void relu_qp_destroy(relu_qp_t h);

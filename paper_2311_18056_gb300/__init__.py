@@ -32,7 +32,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("check_interval", _c_int), ("adaptive_rho", _c_int), ("rho0", _c_double),
                 ("eq_scale", _c_double), ("keep_fp64", _c_int), ("max_batch", _c_int),
                 ("batch_precision", _c_int), ("stream", _c_void_p), ("scaling_iters", _c_int),
-                ("single_precision", _c_int)]
+                ("single_precision", _c_int), ("device_budget", ctypes.c_longlong)]
 
 
 class Prof(ctypes.Structure):
@@ -84,6 +84,15 @@ _SIGNATURES = {
     "relu_qp_server_clock": (_c_double, [_c_void_p]),
     "relu_qp_server_destroy": (None, [_c_void_p]),
     "relu_qp_server_error": (ctypes.c_char_p, [_c_void_p]),
+    "relu_qp_server_set_budget": (_c_int, [_c_void_p, ctypes.c_longlong]),
+    "relu_qp_server_family_bytes": (_c_int, [_c_void_p, _c_int, ctypes.POINTER(ctypes.c_longlong),
+                                             ctypes.POINTER(ctypes.c_longlong)]),
+    "relu_qp_server_bytes_in_use": (ctypes.c_longlong, [_c_void_p]),
+    "relu_qp_device_bytes": (ctypes.c_longlong, [_c_void_p]),
+    "relu_qp_diag_device_wait": (_c_int, [_c_int, ctypes.c_longlong, ctypes.POINTER(_c_int),
+                                          ctypes.POINTER(_c_double)]),
+    "relu_qp_diag_host_barrier": (_c_int, [_c_int, _c_int, _c_int, ctypes.c_longlong, ctypes.POINTER(_c_int),
+                                           ctypes.POINTER(_c_double)]),
     "relu_qp_destroy": (None, [_c_void_p]),
     "relu_qp_last_error": (ctypes.c_char_p, [_c_void_p]),
 }
@@ -159,12 +168,14 @@ class ReluQP:
     adaptive_rho, rho0, eq_scale, keep_fp64, max_batch (> 0 enables the batched
     entry points), precision (batched: PREC_FP32 or PREC_BF16X3), stream (a CUDA
     stream or its handle), scaling_iters (Algorithm 1's scaling step: modified
-    Ruiz iterations at setup, 0 = off) and single_precision (single solves:
-    PREC_FP32, PREC_FP64 or PREC_FP64R, the FP64-anchored form)."""
+    Ruiz iterations at setup, 0 = off), single_precision (single solves:
+    PREC_FP32, PREC_FP64 or PREC_FP64R, the FP64-anchored form) and
+    device_budget (bytes of device memory the handle may keep, 0 = no cap)."""
 
     def __init__(self, P, A, l, u, q=None, sigma=1e-6, rho_bank=(0.1, 1.0, 10.0), *, check_interval=25,
                  adaptive_rho=True, rho0=0.1, eq_scale=1e3, keep_fp64=False, max_batch=0,
-                 precision=PREC_FP32, stream=None, scaling_iters=0, single_precision=PREC_FP32):
+                 precision=PREC_FP32, stream=None, scaling_iters=0, single_precision=PREC_FP32,
+                 device_budget=0):
         L = lib()
         P = _f64(P)
         n = P.shape[0]
@@ -186,6 +197,7 @@ class ReluQP:
         o.stream = _stream_handle(stream)
         o.scaling_iters = int(scaling_iters)
         o.single_precision = int(single_precision)
+        o.device_budget = int(device_budget)
         h = _c_void_p()
         rc = L.relu_qp_setup(ctypes.byref(h), n, m, _ptr(P), _ptr(q), _ptr(A) if m else None,
                              _ptr(l) if m else None, _ptr(u) if m else None, float(sigma), _ptr(bank),
@@ -204,6 +216,10 @@ class ReluQP:
     @property
     def handle(self):
         return self._h
+
+    def device_bytes(self):
+        """Device memory the handle keeps (what device_budget caps)."""
+        return int(lib().relu_qp_device_bytes(self._h))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -398,6 +414,24 @@ class Server:
 
     def clock(self):
         return lib().relu_qp_server_clock(self._s)
+
+    def set_budget(self, nbytes):
+        """Device-memory budget for admission (bytes; 0 = free slots only)."""
+        rc = lib().relu_qp_server_set_budget(self._s, int(nbytes))
+        if rc != OK:
+            raise ReluQPError(rc, lib().relu_qp_server_error(self._s).decode())
+
+    def family_bytes(self, family):
+        """(fixed bytes, bytes per admitted request) of one family."""
+        a, b = ctypes.c_longlong(), ctypes.c_longlong()
+        rc = lib().relu_qp_server_family_bytes(self._s, int(family), ctypes.byref(a), ctypes.byref(b))
+        if rc != OK:
+            raise ReluQPError(rc, "family out of range")
+        return a.value, b.value
+
+    def bytes_in_use(self):
+        """Bytes charged by the requests now in slots."""
+        return int(lib().relu_qp_server_bytes_in_use(self._s))
 
     def close(self):
         if getattr(self, "_s", None):

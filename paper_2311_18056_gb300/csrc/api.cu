@@ -271,6 +271,11 @@ int fail(relu_qp_t h, int code, const std::string& msg) {
 
 int dev_alloc(relu_qp_t h, void** p, size_t bytes) {
     *p = nullptr;
+    const long long cap = h->opts.device_budget;
+    if (cap > 0 && h->dev_bytes + bytes > (size_t)cap)
+        return fail(h, RELU_QP_ERR_OOM, "device-memory budget of " + std::to_string(cap) + " bytes exceeded (" +
+                                             std::to_string(h->dev_bytes) + " held, " + std::to_string(bytes) +
+                                             " more asked)");
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -279,6 +284,7 @@ int dev_alloc(relu_qp_t h, void** p, size_t bytes) {
                                             " bytes): " + cudaGetErrorString(e));
     }
     h->allocs.push_back(*p);
+    h->dev_bytes += bytes;
     e = cudaMemset(*p, 0, bytes);
     if (e != cudaSuccess) return fail(h, RELU_QP_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
     return RELU_QP_OK;
@@ -337,6 +343,7 @@ int relu_qp_setup(relu_qp_t* out, int n, int m, const double* P, const double* q
     if (o.single_precision != RELU_QP_PREC_FP32 && o.single_precision != RELU_QP_PREC_FP64 &&
         o.single_precision != RELU_QP_PREC_FP64R)
         return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: single_precision FP32, FP64 or FP64R");
+    if (o.device_budget < 0) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "opts: device_budget >= 0");
     if (o.single_precision != RELU_QP_PREC_FP32) o.keep_fp64 = 1;   // the FP64 solves read the FP64 bank
     relu_qp_t h = new (std::nothrow) relu_qp_s;
     if (!h) return rq::fail(nullptr, RELU_QP_ERR_OOM, "host allocation failed");
@@ -514,6 +521,8 @@ int relu_qp_dims(relu_qp_t h, int* n, int* m, int* n_rho) {
     return RELU_QP_OK;
 }
 
+long long relu_qp_device_bytes(relu_qp_t h) { return h ? (long long)h->dev_bytes : -1; }
+
 void relu_qp_destroy(relu_qp_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -662,6 +671,18 @@ int relu_qp_server_poll(relu_qp_server_t s, int max_results, relu_qp_result* res
 }
 
 double relu_qp_server_clock(relu_qp_server_t s) { return s ? rq::server_clock(s) : 0.0; }
+
+int relu_qp_server_set_budget(relu_qp_server_t s, long long bytes) {
+    if (!s || bytes < 0) return RELU_QP_ERR_INVALID;
+    return rq::server_set_budget(s, bytes);
+}
+
+int relu_qp_server_family_bytes(relu_qp_server_t s, int family, long long* fixed_bytes, long long* slot_bytes) {
+    if (!s || family < 0 || family >= rq::server_families(s)) return RELU_QP_ERR_INVALID;
+    return rq::server_family_bytes(s, family, fixed_bytes, slot_bytes);
+}
+
+long long relu_qp_server_bytes_in_use(relu_qp_server_t s) { return s ? rq::server_bytes_in_use(s) : -1; }
 
 void relu_qp_server_destroy(relu_qp_server_t s) {
     if (s) rq::server_destroy(s);

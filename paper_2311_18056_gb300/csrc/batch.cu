@@ -23,6 +23,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <thread>
 #include <new>
 
 namespace rq {
@@ -574,6 +575,28 @@ int copy_rows_in(relu_qp_t h, float* dst, int ld, const float* src, int rows, in
 }
 
 }  // namespace
+
+// Device bytes per QP slot of a batched handle: the arrays batch_alloc sizes by
+// max_batch (per-QP state, bias rows of every bank entry, outputs, records) and
+// the share of the slot-indexed operands (cap slots of the slots rows).
+size_t batch_slot_bytes(relu_qp_t h) {
+    const BatchWork& w = h->bw;
+    const size_t mm = h->m > 0 ? h->m : 1, f = sizeof(float);
+    size_t b = 3 * w.ldn * f + f;                       // Y, Q, PY, QN
+    b += 7 * w.ldm * f;                                 // Z, LAM, AY, RR, LSTD, L, U
+    b += (size_t)h->nr * w.ldR * f;                     // BIAS
+    b += (h->n + 2 * mm) * f;                           // XO, ZO, LO
+    b += RW_WORDS * sizeof(unsigned) + 6 * sizeof(int); // RED, rho_idx, status, iters, nsw, rp, rd
+    b += sizeof(int);                                   // perm
+    if (w.prec == RELU_QP_PREC_BF16X3) {
+        b += 2 * w.ldR * f;                             // C, SREF
+        b += w.ldk * f + w.ldkc * f;                    // S32, CK32
+        b += 2 * (7 * (size_t)w.ldk + 3 * (size_t)w.ldkc);   // BF16 operand parts and check operand
+    } else {
+        b += 2 * w.ldk * f + w.ldkc * f;                // S32 pair, CK32
+    }
+    return b;
+}
 
 int batch_alloc(relu_qp_t h) {
     BatchWork& w = h->bw;
@@ -1266,6 +1289,8 @@ struct ServeFamily {
     cudaEvent_t ev = nullptr;
     bool launched = false;
     std::vector<void*> dev_allocs, host_allocs;
+    size_t dev_bytes = 0;          // the server's device buffers for this family
+    size_t slot_bytes = 0;         // device bytes charged per admitted request
 };
 
 struct ServeResult {
@@ -1278,6 +1303,9 @@ struct ServeResult {
 struct relu_qp_server_s {
     std::vector<rq::ServeFamily> fam;
     std::deque<rq::ServeResult> results;
+    long long budget = 0;          // device-memory budget (0: slots only)
+    size_t fixed = 0;              // every family's bank and fixed buffers
+    size_t in_use = 0;             // bytes charged by the requests in slots
     double eps_abs = 1e-3, eps_rel = 0.0;
     int max_iter = 4000;
     std::chrono::steady_clock::time_point t0;
@@ -1306,6 +1334,7 @@ int sdev(relu_qp_server_t s, ServeFamily& f, T** p, size_t count) {
     }
     cudaMemset(q, 0, count * sizeof(T) + 16);
     f.dev_allocs.push_back(q);
+    f.dev_bytes += count * sizeof(T) + 16;
     *p = static_cast<T*>(q);
     return RELU_QP_OK;
 }
@@ -1337,9 +1366,33 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
     BatchWork& w = h->bw;
     const int n = h->n, m = h->m, R = h->R, nx = w.nx;
     BatchParams p = base_params(h);
-    // ---- admission ----
-    const int k = (int)std::min(f.queue.size(), f.free_idx.size());
+    // ---- admission: a free slot, and (with a budget) room for the request's
+    // slot bytes that no older waiting request of another family needs ----
+    int k = (int)std::min(f.queue.size(), f.free_idx.size());
+    if (s->budget > 0 && k > 0) {
+        const size_t room = (size_t)s->budget - s->fixed;
+        // the oldest request waiting in another family that has a free slot
+        double t_old = 1e300;
+        size_t b_old = 0;
+        for (const auto& g : s->fam) {
+            if (&g == &f || g.queue.empty() || g.free_idx.empty()) continue;
+            if (g.queue.front().t_submit < t_old) {
+                t_old = g.queue.front().t_submit;
+                b_old = g.slot_bytes;
+            }
+        }
+        int fit = 0;
+        size_t used = s->in_use;
+        while (fit < k) {
+            const size_t need = used + f.slot_bytes + (f.queue[fit].t_submit > t_old ? b_old : 0);
+            if (need > room) break;
+            used += f.slot_bytes;
+            ++fit;
+        }
+        k = fit;
+    }
     if (k > 0) {
+        s->in_use += (size_t)k * f.slot_bytes;
         for (int j = 0; j < k; ++j) {
             ServeRequest rq_ = std::move(f.queue.front());
             f.queue.pop_front();
@@ -1406,7 +1459,7 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
 int family_collect(relu_qp_server_t s, ServeFamily& f, int fi) {
     if (!f.launched) return RELU_QP_OK;
     f.launched = false;
-    RQ_SCUDA(s, cudaEventSynchronize(f.ev));
+    RQ_SCUDA(s, cudaEventSynchronize(f.ev));   // complete already when called from server_step
     const double t = s->now();
     if (f.h_cnt[1 + CNT_ERR]) return sfail(s, RELU_QP_ERR_TIMEOUT, "a tensor-core kernel wait passed its deadline");
     const int cnt = f.h_cnt[0];
@@ -1430,6 +1483,7 @@ int family_collect(relu_qp_server_t s, ServeFamily& f, int fi) {
         s->results.push_back(std::move(res));
         f.free_idx.push_back(qp);
         --f.active;
+        s->in_use -= std::min(s->in_use, f.slot_bytes);
     }
     return RELU_QP_OK;
 }
@@ -1459,7 +1513,16 @@ int server_create(relu_qp_server_t* out, relu_qp_t const* families, int nf, cons
         f.t_submit_of.assign(f.cap, 0.0);
         f.client_of.assign(f.cap, -1);
         for (int q = f.cap - 1; q >= 0; --q) f.free_idx.push_back(q);
-        RQ_SCUDA(s, cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking));
+        // smaller problems get higher stream priorities, so that their short chunks
+        // do not queue behind the grids of a family of large problems
+        int rank = 0;
+        for (int g = 0; g < nf; ++g)
+            if (families[g]->R < h->R || (families[g]->R == h->R && g < fi)) ++rank;
+        int prio_lo = 0, prio_hi = 0;
+        RQ_SCUDA(s, cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        // (numerically lower = higher priority: the smallest family gets prio_hi)
+        const int prio = std::min(prio_lo, prio_hi + rank);
+        RQ_SCUDA(s, cudaStreamCreateWithPriority(&f.stream, cudaStreamNonBlocking, prio));
         RQ_SCUDA(s, cudaEventCreateWithFlags(&f.ev, cudaEventDisableTiming));
         f.saved_stream = h->stream;
         h->stream = f.stream;
@@ -1494,9 +1557,39 @@ int server_create(relu_qp_server_t* out, relu_qp_t const* families, int nf, cons
         RQ_SCUDA(s, cudaGetLastError());
         RQ_SCUDA(s, cudaMemsetAsync(w.counters, 0, sizeof(int) * CNT_WORDS, f.stream));
         RQ_SCUDA(s, cudaStreamSynchronize(f.stream));
+        // memory accounting: a request occupies one QP slot of the handle plus its rows of the
+        // server's compact buffers (x0, q, x, l, u, A x, b of every bank entry, the result row)
+        const size_t fl = sizeof(float);
+        const size_t serve_slot = (w.ldx + 2 * w.ldn + 3 * w.ldm + (size_t)h->nr * w.ldR + f.ldo) * fl +
+                                  4 * sizeof(int);
+        f.slot_bytes = batch_slot_bytes(h) + serve_slot;
+        const size_t fam_fixed = h->dev_bytes + f.dev_bytes;
+        const size_t fam_slots = (size_t)f.cap * f.slot_bytes;
+        s->fixed += fam_fixed > fam_slots ? fam_fixed - fam_slots : 0;
     }
     return RELU_QP_OK;
 }
+
+int server_set_budget(relu_qp_server_t s, long long bytes) {
+    size_t one = 0;   // room for one request of every family, so that none waits forever
+    for (const auto& f : s->fam) one = std::max(one, f.slot_bytes);
+    if (bytes > 0 && (size_t)bytes < s->fixed + one)
+        return sfail(s, RELU_QP_ERR_OOM, "server budget of " + std::to_string(bytes) + " bytes is below the " +
+                                             std::to_string(s->fixed) + " bytes of the families' banks and buffers "
+                                             "plus one request of the largest family (" + std::to_string(one) + ")");
+    s->budget = bytes;
+    return RELU_QP_OK;
+}
+
+int server_family_bytes(relu_qp_server_t s, int family, long long* fixed_bytes, long long* slot_bytes) {
+    const ServeFamily& f = s->fam[family];
+    const size_t all = f.h->dev_bytes + f.dev_bytes, slots = (size_t)f.cap * f.slot_bytes;
+    if (fixed_bytes) *fixed_bytes = (long long)(all > slots ? all - slots : 0);
+    if (slot_bytes) *slot_bytes = (long long)f.slot_bytes;
+    return RELU_QP_OK;
+}
+
+long long server_bytes_in_use(relu_qp_server_t s) { return (long long)s->in_use; }
 
 int server_submit(relu_qp_server_t s, int family, int client, const float* x0, long long tag) {
     ServeFamily& f = s->fam[family];
@@ -1509,9 +1602,34 @@ int server_submit(relu_qp_server_t s, int family, int client, const float* x0, l
     return RELU_QP_OK;
 }
 
+// Families advance independently: a family with no chunk in flight admits and
+// launches; one whose chunk has finished (its event has completed) retires,
+// admits and launches again at once.  The call returns once some family has
+// finished a chunk (or when no chunk is in flight), so a family of small
+// problems is never held back by the chunk of a family of large ones.
 int server_step(relu_qp_server_t s, int* active, int* waiting) {
-    for (auto& f : s->fam) RQ_TRY(family_launch(s, f));
-    for (size_t fi = 0; fi < s->fam.size(); ++fi) RQ_TRY(family_collect(s, s->fam[fi], (int)fi));
+    const size_t nf = s->fam.size();
+    for (auto& f : s->fam)
+        if (!f.launched) RQ_TRY(family_launch(s, f));
+    bool any_in_flight = false;
+    for (auto& f : s->fam) any_in_flight = any_in_flight || f.launched;
+    bool progressed = !any_in_flight;
+    while (!progressed) {
+        for (size_t fi = 0; fi < nf; ++fi) {
+            ServeFamily& f = s->fam[fi];
+            if (!f.launched) continue;
+            const cudaError_t q = cudaEventQuery(f.ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                return sfail(s, RELU_QP_ERR_CUDA, std::string("server chunk: ") + cudaGetErrorString(q));
+            }
+            RQ_TRY(family_collect(s, f, (int)fi));
+            RQ_TRY(family_launch(s, f));
+            progressed = true;
+        }
+        if (!progressed) std::this_thread::yield();
+    }
     int a = 0, q = 0;
     for (auto& f : s->fam) {
         a += f.active;

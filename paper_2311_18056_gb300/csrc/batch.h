@@ -95,6 +95,21 @@ __device__ __forceinline__ void put_check(const BatchParams& p, int slot, int co
 // r+ = (Ax)+ - z+ + lam'+/rho_i = t - z+ + r (array RR); the refined layers
 // read r from RR and write x, Ax, z and lam' only at the last layer of the
 // chunk.  With EPI_CHECK the new x also goes into the check operand.
+// The z, lam' and operand update of one row of A x (FP32), given the layer's
+// product t and the carried r = (Ax) - z + lam'/rho_i.  Every FP32 path calls
+// this one function (tiled kernels and the convergence tail), so that a QP's
+// iterates do not depend on which kernel runs its layer.
+__device__ __forceinline__ void ax_row_update(float t, float rr, float lo, float up, float rho_i, float& zn,
+                                              float& ln, float& s_new) {
+    zn = fminf(fmaxf(t + rr, lo), up);
+    ln = rho_i * rr;
+    s_new = 2.f * rho_i * zn - ln;
+}
+
+__device__ __forceinline__ float ax_row_carry(float ay, float zi, float li, float rho_i) {
+    return ay - zi + li / rho_i;
+}
+
 __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int qp, int ri, int r, float acc) {
     const unsigned f = p.flags;
     const bool refine_only = (f & EPI_REFINE) && !(f & EPI_REBASE);
@@ -127,17 +142,16 @@ __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int q
         } else {
             const float ay = p.AY[o], zi = p.Z[o], li = p.LAM[o];
             if (f & EPI_REBASE) p.SREF[oR] = 2.f * rho_i * zi - li;
-            rr = ay - zi + li / rho_i;
+            rr = ax_row_carry(ay, zi, li, rho_i);
         }
-        const float zn = fminf(fmaxf(t + rr, p.L[o]), p.U[o]);
-        const float ln = rho_i * rr;
+        float zn, ln;
+        ax_row_update(t, rr, p.L[o], p.U[o], rho_i, zn, ln, s_new);
         if (f & EPI_REFINE) p.RR[o] = t - zn + rr;
         if (store_state) {
             p.AY[o] = t;
             p.Z[o] = zn;
             p.LAM[o] = ln;
         }
-        s_new = 2.f * rho_i * zn - ln;
     }
     if (!(f & EPI_LAST)) {
         const size_t so = (size_t)slot * p.ldk + r;
@@ -349,6 +363,52 @@ __device__ __forceinline__ void check1_elem(const BatchParams& p, int slot, int 
     }
 }
 
+// check1_elem for 4 consecutive rows r0..r0+3 of one QP, all rows of x
+// (r0 + 3 < n) or all of A x (r0 >= n, n a multiple of 4), 16-byte aligned:
+// the same arithmetic with 128-bit loads and stores of the QP's rows.
+__device__ __forceinline__ void check1_4(const BatchParams& p, int slot, int qp, int ri, int r0, const float (&a)[4],
+                                         float& rp, float& nax, float& nz, float& npx) {
+    if (r0 < p.n) {
+        st4(p.PY + (size_t)qp * p.ldn + r0, a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) npx = nmax(npx, fabsf(p.rsx ? a[k] * p.rsx[r0 + k] : a[k]));
+        return;
+    }
+    const int i0 = r0 - p.n;
+    const size_t o = (size_t)qp * p.ldm + i0;
+    float z[4], lm[4], rs[4], ls[4];
+    ld4(p.Z + o, z);
+    ld4(p.LAM + o, lm);
+    ld4(p.rs + i0, rs);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float d = a[k] - z[k];
+        ls[k] = lm[k] + p.rho[ri] * rs[k] * d;
+        const float f = p.rsz ? p.rsz[i0 + k] : 1.f;
+        rp = nmax(rp, fabsf(p.rsz ? d * f : d));
+        nax = nmax(nax, fabsf(p.rsz ? a[k] * f : a[k]));
+        nz = nmax(nz, fabsf(p.rsz ? z[k] * f : z[k]));
+    }
+    st4(p.AY + o, a);
+    st4(p.LSTD + o, ls);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) put_check(p, slot, p.n64 + i0 + k, ls[k]);
+}
+
+// check2_elem for 4 consecutive rows j0..j0+3 (< n) of one QP, 16-byte aligned.
+__device__ __forceinline__ void check2_4(const BatchParams& p, int qp, int j0, const float (&a)[4], float& rd,
+                                         float& natl) {
+    float px[4], q[4];
+    ld4(p.PY + (size_t)qp * p.ldn + j0, px);
+    ld4(p.Q + (size_t)qp * p.ldn + j0, q);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float r = px[k] + q[k] + a[k];
+        rd = nmax(rd, fabsf(p.rsx ? r * p.rsx[j0 + k] : r));
+        natl = nmax(natl, fabsf(p.rsx ? a[k] * p.rsx[j0 + k] : a[k]));
+    }
+}
+
 // Second residual product, row j of A^T lam_std: dual residual P x + q + A^T lam_std.
 __device__ __forceinline__ void check2_elem(const BatchParams& p, int qp, int j, float acc, float& rd, float& natl) {
     const float r = p.PY[(size_t)qp * p.ldn + j] + p.Q[(size_t)qp * p.ldn + j] + acc;
@@ -463,6 +523,10 @@ int tc_set_layer_table(relu_qp_t h, const std::vector<LayerCfg>& by_tiles);  // 
 // device error word of the backend (0 = none) and, for a deadline, which wait gave up
 // (site); clears both
 int tc_error(relu_qp_t h, int* site = nullptr);
+
+// Deadline diagnostics of the tensor-core kernels' waits (kind 0: mbarrier,
+// 1: layer counter); dev: >= 4 zeroed ints (error word, site, counter).
+int tc_diag_wait(int kind, int* dev, long long ns, cudaStream_t stream);
 
 // --- convergence tail (batch_tail.cu) --------------------------------------
 constexpr int kTailMax = 8;      // QPs the tail kernel takes at most

@@ -30,6 +30,8 @@ namespace rq {
 namespace {
 
 constexpr int kTailThreads = 384;   // 12 warps: one row of the layer each
+constexpr int kTailWarps = kTailThreads / 32;
+constexpr int kTailRPW = 4;         // rows per warp whose state stays in registers during a chunk
 
 struct TailArgs {
     BatchParams p;              // state (QP-indexed rows), bank scalars; Sout / CK32 set per phase
@@ -45,6 +47,7 @@ struct TailArgs {
     int nq, it0, max_iter, ci;
     int rpc;                    // rows of the layer per CTA (contiguous)
     int wcache;                 // 1: the CTA's Wt rows of one bank entry are cached in shared memory
+    int regs;                   // 1: every warp owns <= kTailRPW rows (their state kept in registers)
     long long timeout_ns;
 };
 
@@ -248,6 +251,37 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                 cache_ri = ri0;
             }
         }
+        // the state of this warp's rows for lane j's QP (bias of its bank entry, and for
+        // rows of A x the carried A x, z, lam', l, u, rho_i) stays in registers for the
+        // chunk: loaded here, written back at the chunk's last layer (the checks, the
+        // decision and the next chunk's fill read it from memory)
+        const bool live_lane = lane < nq && s_live[lane];
+        const int qp_l = live_lane ? a.qlist[lane] : 0, ri_l = live_lane ? s_ri[lane] : 0;
+        float rb[kTailRPW], ray[kTailRPW], rz[kTailRPW], rlam[kTailRPW], rlo[kTailRPW], rup[kTailRPW],
+            rrho[kTailRPW];
+        if (a.regs && live_lane) {
+#pragma unroll
+            for (int w = 0; w < kTailRPW; ++w) {
+                const int r = row_beg + warp + kTailWarps * w;
+                rb[w] = ray[w] = rz[w] = rlam[w] = rlo[w] = rup[w] = rrho[w] = 0.f;
+                if (r >= row_end) continue;
+                rb[w] = p.BIAS[((size_t)ri_l * p.cap + qp_l) * p.ldR + r];
+                if (r >= p.n) {
+                    const int i = r - p.n;
+                    const size_t o = (size_t)qp_l * p.ldm + i;
+                    ray[w] = p.AY[o];
+                    rz[w] = p.Z[o];
+                    rlam[w] = p.LAM[o];
+                    rlo[w] = p.L[o];
+                    rup[w] = p.U[o];
+                    rrho[w] = p.rho[ri_l] * p.rs[i];
+                }
+            }
+        }
+        auto wrow = [&](int j, int r) {
+            return s_ri[j] == cache_ri ? WRowRef{wc + (size_t)(r - row_beg) * wops, kStepPad}
+                                       : WRowRef{a.W[s_ri[j]] + (size_t)r * p.ldk, kStep};
+        };
         for (int jl = 0; jl < len; ++jl) {
             const float* Sc = a.S + (size_t)cur * kTailMax * p.ldk;
             p.Sout = a.S + (size_t)(cur ^ 1) * kTailMax * p.ldk;
@@ -256,18 +290,49 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
             p.flags = jl == len - 1 ? (EPI_LAST | (check ? EPI_CHECK : 0u)) : 0u;
             stage_rows(tsm, ops, Sc, p.ldk, 0, p.ldk, nq, s_live);
             __syncthreads();
-            for (int r0 = row_beg + warp * kRB; r0 < row_end; r0 += (kTailThreads / 32) * kRB) {
-                float acc[kRB];
-                warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r0, row_end,
-                          [&](int j, int r) {
-                              return s_ri[j] == cache_ri ? WRowRef{wc + (size_t)(r - row_beg) * wops, kStepPad}
-                                                         : WRowRef{a.W[s_ri[j]] + (size_t)r * p.ldk, kStep};
-                          },
-                          acc);
-                if (lane < nq && s_live[lane])
+            if (a.regs) {
+                const bool last = jl == len - 1;
 #pragma unroll
-                    for (int i = 0; i < kRB; ++i)
-                        if (r0 + i < row_end) layer_elem(p, lane, a.qlist[lane], s_ri[lane], r0 + i, acc[i]);
+                for (int w = 0; w < kTailRPW; ++w) {
+                    const int r = row_beg + warp + kTailWarps * w;
+                    if (r >= row_end) break;
+                    float acc[kRB];
+                    warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r, row_end, wrow, acc);
+                    if (!live_lane) continue;
+                    // the FP32 layer of layer_elem on register state
+                    const float t = acc[0] + rb[w];
+                    float s_new;
+                    if (r < p.n) {
+                        s_new = t;
+                        if (last) {
+                            p.Y[(size_t)qp_l * p.ldn + r] = t;
+                            if (check) put_check(p, lane, r, t);
+                        }
+                    } else {
+                        float zn, ln;
+                        const float rr = ax_row_carry(ray[w], rz[w], rlam[w], rrho[w]);
+                        ax_row_update(t, rr, rlo[w], rup[w], rrho[w], zn, ln, s_new);
+                        ray[w] = t;
+                        rz[w] = zn;
+                        rlam[w] = ln;
+                        if (last) {
+                            const size_t o = (size_t)qp_l * p.ldm + (r - p.n);
+                            p.AY[o] = t;
+                            p.Z[o] = zn;
+                            p.LAM[o] = ln;
+                        }
+                    }
+                    if (!last) p.Sout[(size_t)lane * p.ldk + r] = s_new;
+                }
+            } else {
+                for (int r0 = row_beg + warp * kRB; r0 < row_end; r0 += kTailWarps * kRB) {
+                    float acc[kRB];
+                    warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r0, row_end, wrow, acc);
+                    if (live_lane)
+#pragma unroll
+                        for (int i = 0; i < kRB; ++i)
+                            if (r0 + i < row_end) layer_elem(p, lane, qp_l, ri_l, r0 + i, acc[i]);
+                }
             }
             cur ^= 1;
             if (!tail_barrier(a, &s_ok)) return;
@@ -471,6 +536,7 @@ int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, i
     a.ci = h->opts.check_interval;
     a.rpc = w.tail_rpc;
     a.wcache = w.tail_cache;
+    a.regs = w.tail_rpc <= kTailWarps * kTailRPW ? 1 : 0;
     a.timeout_ns = 2000000000LL;
     void* args[] = {&a};
     RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)batch_tail_kernel, dim3(w.tail_grid), dim3(kTailThreads), args,

@@ -101,11 +101,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // deadline.  (The deadline is checked after every unsuccessful try_wait,
 // which itself blocks for a while; a tight loop of tries between clock reads
 // made every pipeline hand-off several times slower.)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t parity, long long ns) {
     const long long t0 = gtime();
     while (!mbar_try(bar, parity))
-        if (gtime() - t0 > kWaitNs) return false;
+        if (gtime() - t0 > ns) return false;
     return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) { return mbar_wait_ns(bar, parity, kWaitNs); }
+
+// Wait (acquire at GPU scope) until the counter reaches target; false after ns.
+__device__ __forceinline__ bool wait_counter_geq(const unsigned* ctr, unsigned target, long long ns) {
+    const long long t0 = gtime();
+    while (true) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if (gtime() - t0 > ns) return false;
+    }
 }
 
 // The same for a long wait by a thread that is not on the critical path: poll
@@ -370,15 +382,9 @@ __device__ __noinline__ bool produce_layer(const CUtensorMap* tmA, const CUtenso
             asm volatile("fence.proxy.async.global;" ::: "memory");
             own_ready = true;
         } else if (i >= own_n && !tile_ready) {
-            const long long t0 = gtime();
-            while (true) {
-                unsigned v;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(sync) : "memory");
-                if (v >= target) break;
-                if (gtime() - t0 > kWaitNs) {
-                    sync_failed = true;
-                    return false;
-                }
+            if (!wait_counter_geq(sync, target, kWaitNs)) {
+                sync_failed = true;
+                return false;
             }
             // the operand was written by generic stores of other CTAs; order them before the TMA reads
             asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -522,8 +528,11 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
     const int slot = slot0 + q * 32 + lane;
     const int qp = p.perm[slot];
     const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-    // whole 16-row pieces are transposed through shared memory so that
-    // lane = 4 * (slot % 8) + (row group): QP slot pass * 8 + lane / 4, rows cg..cg+3
+    // whole 16-row pieces are transposed so that lane = 4 * (slot % 8) + (row
+    // group): pass `pass` handles rows cg..cg+3 of the QP of slot pass * 8 +
+    // lane / 4, and a warp's 128-bit accesses cover 8 QPs' contiguous 64-byte
+    // row segments.  Refined layers transpose through a per-warp shared-memory
+    // buffer; the drained modes read the other slots' sums where they are.
     const int cg = (lane & 3) * 4;
     int qq[4];
 #pragma unroll
@@ -535,6 +544,19 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
         const int r0 = row0 + c0;
         return MODE <= MODE_LAYER_ACCURATE && r0 + 16 <= g.rows && (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
     };
+    // residual products: 16-row pieces of rows of x only or of A x only take the
+    // transposed path as well (the drained sums of every slot of the warp are in
+    // shared memory, so the transposition needs no extra buffer)
+    constexpr bool CHECK = MODE == MODE_CHECK1 || MODE == MODE_CHECK2;
+    auto check_whole_at = [&](int c0) {
+        const int r0 = row0 + c0;
+        return CHECK && r0 + 16 <= g.rows && (r0 + 16 <= p.n || (r0 >= p.n && n_aligned));
+    };
+    float mx[4][4];   // per pass (QP): the residual maxima of the transposed pieces
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mx[a][b] = 0.f;
     // refined layers: the lighter refined-only inputs (flags never hold EPI_REBASE)
     using Piece = typename std::conditional<MODE == MODE_LAYER_REFINED, Chunk4R, Chunk4>::type;
     Piece in[4];
@@ -629,7 +651,6 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
         if (lane == 0) { wait_failed(g.err, DRAIN ? WS_DRAIN_READY : WS_EPI_ACC); *s_fail = 1; }
     } else {
         float ra = 0.f, rb = 0.f, rc = 0.f, rd = 0.f;
-        float* xb = xpose + (warp - 2) * 32 * 17;       // this warp's [32 slots][16 rows] buffer
         // inputs of the next whole chunk load pass by pass as this chunk's
         // passes finish, so that a memory round trip overlaps a chunk of work
         for (int c0 = cbeg; c0 < cend; c0 += 16) {
@@ -638,6 +659,25 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
             const int cn = c0 + 16;
             const bool next_whole = cn < cend && whole_at(cn);
             if (next_whole) load_rs(cn, rs_next);
+            if (CHECK && check_whole_at(c0)) {
+                // lane = 4 * (slot % 8) + row group: rows r0 + cg .. + 3 of the slot
+                // pass * 8 + lane / 4, read from that slot's drained sums
+                __syncwarp();
+                const float* wsum = drain + (warp - 2) * 32 * (PER + 1);
+#pragma unroll
+                for (int pass = 0; pass < 4; ++pass) {
+                    const int sl = pass * 8 + (lane >> 2);
+                    if (qq[pass] < 0) continue;
+                    const float* src = wsum + sl * (PER + 1) + (c0 - cbeg) + cg;
+                    const float a4[4] = {src[0], src[1], src[2], src[3]};
+                    if (MODE == MODE_CHECK1)
+                        check1_4(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, mx[pass][0], mx[pass][1],
+                                 mx[pass][2], mx[pass][3]);
+                    else
+                        check2_4(p, qq[pass], r0 + cg, a4, mx[pass][0], mx[pass][1]);
+                }
+                continue;
+            }
             float v[16];
             if (DRAIN) {
 #pragma unroll
@@ -677,8 +717,22 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
                 for (int t = 0; t < 16; ++t) v[t] = tot[t];
             }
             if (whole) {
+                // the source rows: this warp's transpose buffer (refined), or the
+                // drained sums, which already hold every slot of the warp
+                const float* base;
+                int stride, off;
+                if (DRAIN) {
+                    base = drain + (warp - 2) * 32 * (PER + 1);
+                    stride = PER + 1;
+                    off = c0 - cbeg;
+                } else {
+                    float* xb = xpose + (warp - 2) * 32 * 17;       // [32 slots][16 rows]
 #pragma unroll
-                for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
+                    for (int t = 0; t < 16; ++t) xb[lane * 17 + t] = v[t];
+                    base = xb;
+                    stride = 17;
+                    off = 0;
+                }
                 __syncwarp();
 #pragma unroll
                 for (int pass = 0; pass < 4; ++pass) {
@@ -686,7 +740,7 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
                     if (qq[pass] >= 0) {
                         float a4[4];
 #pragma unroll
-                        for (int t = 0; t < 4; ++t) a4[t] = xb[sl * 17 + cg + t];
+                        for (int t = 0; t < 4; ++t) a4[t] = base[sl * stride + off + cg + t];
                         chunk4_apply(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, in[pass], rs);
                     }
                     if (next_whole) load_pass(cn, pass);
@@ -722,6 +776,31 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
             } else if (MODE == MODE_CHECK2) {
                 red_slot(p.RED, qp, RW_RD, ra);
                 red_slot(p.RED, qp, RW_ATL, rb);
+            }
+        }
+        if (CHECK) {
+            // the transposed pieces: the 4 lanes of a slot (lane & 3 = row group)
+            // combine their maxima, then one of them adds them to the QP's words
+#pragma unroll
+            for (int pass = 0; pass < 4; ++pass) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    float v = mx[pass][b];
+                    v = nmax(v, __shfl_xor_sync(0xffffffffu, v, 1));
+                    v = nmax(v, __shfl_xor_sync(0xffffffffu, v, 2));
+                    mx[pass][b] = v;
+                }
+                if ((lane & 3) == 0 && qq[pass] >= 0) {
+                    if (MODE == MODE_CHECK1) {
+                        red_slot(p.RED, qq[pass], RW_RP, mx[pass][0]);
+                        red_slot(p.RED, qq[pass], RW_AX, mx[pass][1]);
+                        red_slot(p.RED, qq[pass], RW_Z, mx[pass][2]);
+                        red_slot(p.RED, qq[pass], RW_PX, mx[pass][3]);
+                    } else {
+                        red_slot(p.RED, qq[pass], RW_RD, mx[pass][0]);
+                        red_slot(p.RED, qq[pass], RW_ATL, mx[pass][1]);
+                    }
+                }
             }
         }
     }
@@ -1097,6 +1176,28 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Deadline diagnostics: the waits above, made to run out on purpose.  kind 0:
+// an mbarrier that nothing arrives on (mbar_wait_ns); kind 1: a layer counter
+// that nothing increments (wait_counter_geq).  The waiting thread gives up at
+// its deadline and records RELU_QP_ERR_TIMEOUT in err[0] (err[1] = the kind +
+// 1), as the kernels above do; nothing faults or hangs.
+// ---------------------------------------------------------------------------
+__global__ void tc_diag_wait_kernel(int kind, const unsigned* ctr, int* err, long long ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const bool ok = kind == 0 ? mbar_wait_ns(smem_u32(&bar), 0, ns) : wait_counter_geq(ctr, 1u, ns);
+    if (!ok) {
+        atomicCAS(err + 1, 0, kind + 1);
+        atomicExch(err, RELU_QP_ERR_TIMEOUT);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1431,6 +1532,13 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
     if (phase == 1)
         return dispatch_3part<MODE_CHECK1>(h, 64, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
     return dispatch_3part<MODE_CHECK2>(h, 64, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
+}
+
+// Launch tc_diag_wait_kernel on `stream` with the words at dev (>= 4 ints,
+// zeroed by the caller); the caller synchronises and reads err = dev[0..1].
+int tc_diag_wait(int kind, int* dev, long long ns, cudaStream_t stream) {
+    tc_diag_wait_kernel<<<1, 32, 0, stream>>>(kind, reinterpret_cast<const unsigned*>(dev + 2), dev, ns);
+    return cudaGetLastError() == cudaSuccess ? RELU_QP_OK : RELU_QP_ERR_CUDA;
 }
 
 int tc_error(relu_qp_t h, int* site) {

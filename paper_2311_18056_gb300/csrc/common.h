@@ -171,6 +171,7 @@ struct relu_qp_s {
     std::vector<int> prof_span_launches;     // launches covered by each recorded event pair
     std::string err;
     std::vector<void*> allocs;               // every cudaMalloc of the handle
+    size_t dev_bytes = 0;                    // bytes of those allocations (opts.device_budget caps it)
 };
 
 namespace rq {
@@ -241,6 +242,11 @@ double server_clock(relu_qp_server_t s);
 int server_families(relu_qp_server_t s);
 int server_clients(relu_qp_server_t s, int family);
 int server_nx(relu_qp_server_t s, int family);
+int server_set_budget(relu_qp_server_t s, long long bytes);
+int server_family_bytes(relu_qp_server_t s, int family, long long* fixed_bytes, long long* slot_bytes);
+long long server_bytes_in_use(relu_qp_server_t s);
+// device bytes of one QP slot of a batched handle (every array that scales with max_batch)
+size_t batch_slot_bytes(relu_qp_t h);
 void batch_release(relu_qp_t h);
 
 inline int ceil_div(int a, int b) { return (a + b - 1) / b; }

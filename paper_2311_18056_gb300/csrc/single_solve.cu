@@ -526,16 +526,22 @@ std::mutex g_noalloc_mutex;
 
 size_t noalloc_words(int ldw, int ldp, int ldt) { return 3 * (size_t)ldw + ldp + 6 * (size_t)ldt + 64; }
 
-// Device address of the array on the current device, looked up once per
+// Device address of the array on the handle's device, looked up once per
 // device (a host-side use of the symbol itself would not be a device address).
+// The lookup is made with h->device current, whatever device the calling
+// thread has made current, because the stream and every buffer of the solve
+// belong to h->device.
 int noalloc_scratch(relu_qp_t h, float** out) {
-    int dev = 0;
-    RQ_CUDA(h, cudaGetDevice(&dev));
+    const int dev = h->device;
     if (dev < 0 || dev >= kMaxDevices) return fail(h, RELU_QP_ERR_UNSUPPORTED, "device ordinal >= 64");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_ptr[dev]) {
+        int cur = 0;
+        RQ_CUDA(h, cudaGetDevice(&cur));
+        if (cur != dev) RQ_CUDA(h, cudaSetDevice(dev));
         void* ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (cur != dev) cudaSetDevice(cur);
         if (e != cudaSuccess || !ptr) {
             cudaGetLastError();
             return fail(h, RELU_QP_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
@@ -543,6 +549,25 @@ int noalloc_scratch(relu_qp_t h, float** out) {
         g_noalloc_ptr[dev] = static_cast<float*>(ptr);
     }
     *out = g_noalloc_ptr[dev];
+    return RELU_QP_OK;
+}
+
+// The caller's warm-start and output pointers must be device (or managed)
+// memory of the handle's device: anything else would reach the kernels and
+// the device-to-device copies unchecked.  NULL passes (optional arguments are
+// checked by the caller).
+int noalloc_check_ptr(relu_qp_t h, const void* ptr, const char* name) {
+    if (!ptr) return RELU_QP_OK;
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, RELU_QP_ERR_INVALID, std::string(name) + " is not a CUDA pointer");
+    }
+    const bool on_device = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (!on_device || (a.type == cudaMemoryTypeDevice && a.device != h->device))
+        return fail(h, RELU_QP_ERR_INVALID,
+                    std::string(name) + " must be device FP32 memory of device " + std::to_string(h->device));
     return RELU_QP_OK;
 }
 
@@ -557,6 +582,11 @@ int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm
         return fail(h, RELU_QP_ERR_INVALID, "relu_qp_solve_noalloc supports n + m <= " +
                                                 std::to_string(kNoAllocMaxRows) + " (fixed scratch of " +
                                                 std::to_string(kNoAllocWords * 4 / 1024) + " KiB)");
+    RQ_TRY(noalloc_check_ptr(h, x_warm, "x_warm"));
+    RQ_TRY(noalloc_check_ptr(h, lam_warm, "lam_warm"));
+    RQ_TRY(noalloc_check_ptr(h, x_out, "x_out"));
+    RQ_TRY(noalloc_check_ptr(h, z_out, "z_out"));
+    RQ_TRY(noalloc_check_ptr(h, lam_out, "lam_out"));
     float* base = nullptr;
     RQ_TRY(noalloc_scratch(h, &base));
     // carve the scratch: vectors first (16-byte aligned offsets), then the words

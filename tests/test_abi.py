@@ -15,7 +15,7 @@ def declared_functions():
     for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(hdr).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(relu_qp_[a-z0-9_]+)\s*\(",
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:long\s+long|[A-Za-z_][A-Za-z0-9_]*)\s*\*?\s*(relu_qp_[a-z0-9_]+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names
@@ -121,3 +121,31 @@ def test_product_path_does_not_import_the_oracle():
     code = ("import sys, paper_2311_18056_gb300, paper_2311_18056_gb300.build, workloads.mpc, "
             "workloads.random_qp; assert not any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules)")
     subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True)
+
+
+def test_device_budget_is_validated_without_gpu(libpath):
+    import numpy as np
+    import paper_2311_18056_gb300 as rq
+    o = rq.Opts()
+    rq.lib().relu_qp_default_opts(ctypes.byref(o))
+    assert o.device_budget == 0
+    with pytest.raises(rq.ReluQPError) as e:
+        rq.ReluQP(np.eye(2), np.eye(2), -np.ones(2), np.ones(2), device_budget=-1)
+    assert e.value.kind == "INVALID"
+
+
+def test_grid_barrier_logic_on_host_threads(libpath):
+    """The grid barrier's arrival/wait template, run by host threads: with the
+    right arrival count every round passes; with one arrival missing every
+    thread gives up at its deadline (about 2 ms) and reports it, instead of
+    waiting forever."""
+    import paper_2311_18056_gb300 as rq
+    L = rq.lib()
+    n_to, ms = ctypes.c_int(-1), ctypes.c_double(0.0)
+    assert L.relu_qp_diag_host_barrier(8, 0, 2000, 2_000_000_000, ctypes.byref(n_to), ctypes.byref(ms)) == 0
+    assert n_to.value == 0
+    assert L.relu_qp_diag_host_barrier(6, 1, 5, 2_000_000, ctypes.byref(n_to), ctypes.byref(ms)) == 0
+    assert n_to.value == 6
+    assert 1.5 <= ms.value < 2000.0
+    # arguments are checked
+    assert L.relu_qp_diag_host_barrier(0, 0, 1, 2_000_000, ctypes.byref(n_to), None) == -1

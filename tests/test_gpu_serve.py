@@ -126,3 +126,48 @@ def test_server_rejects_bad_requests(rq, families):
     with pytest.raises(rq.ReluQPError):
         srv.submit(0, np.zeros(families[0][1].nx, np.float32), client=5)   # no clients configured
     srv.close()
+
+
+def test_budget_holds_requests_back_then_admits(rq, families):
+    """Admission by device memory: with room for two requests of the humanoid
+    family, six of its requests enter two at a time, the rest wait, every one
+    is answered, and each answer equals the same request solved alone (the
+    FP32 family's arithmetic does not depend on its batch)."""
+    f = 2
+    name, pq, s, h = families[f]
+    srv = rq.Server([h for *_, h in families], eps_abs=1e-3)
+    fixed = sum(srv.family_bytes(k)[0] for k in range(3))
+    slot = srv.family_bytes(f)[1]
+    assert slot > 0 and fixed > 0
+    with pytest.raises(rq.ReluQPError) as e:
+        srv.set_budget(fixed // 2)                       # the banks alone do not fit
+    assert e.value.kind == "OOM"
+    srv.set_budget(fixed + 2 * slot + slot // 2)
+    rng = np.random.default_rng(11)
+    x0s = [(s * rng.standard_normal(pq.nx)).astype(np.float32) for _ in range(6)]
+    for tag, x0 in enumerate(x0s):
+        srv.submit(f, x0, tag=tag)
+    active, waiting = srv.step()
+    results = srv.poll()                                 # a request may finish at its first check
+    assert active <= 2 and active + waiting + len(results) == 6 and waiting >= 2
+    assert srv.bytes_in_use() == active * slot
+    peak = active
+    for _ in range(2000):
+        active, waiting = srv.step()
+        peak = max(peak, active)
+        assert srv.bytes_in_use() <= 2 * slot
+        results += srv.poll()
+        if active == 0 and waiting == 0:
+            break
+    srv.close()
+    assert peak <= 2
+    assert sorted(r["tag"] for r in results) == list(range(6))
+    for r in results:
+        alone_srv = rq.Server([h for *_, h in families], eps_abs=1e-3)
+        alone_srv.submit(f, x0s[r["tag"]], tag=0)
+        alone = run_all(alone_srv)
+        alone_srv.close()
+        assert r["status"] == alone[0]["status"] == rq.SOLVED
+        assert r["iters"] == alone[0]["iters"]
+        assert np.max(np.abs(r["x"] - alone[0]["x"])) <= 1e-6 * (1 + np.max(np.abs(r["x"])))
+

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 SIGMA = 1e-6
 BANK = (0.1, 1.0, 10.0)
+CHECK_INTERVAL = 25          # the handles below use the default check interval
 
 
 @pytest.fixture(scope="module")
@@ -78,8 +79,47 @@ def test_noalloc_warm_start_and_fixed_layers(rq):
     for _ in range(2):
         ref = s.solve(x_warm=cold["x"], lam_warm=cold["lam"], rho_index=cold["rho_index"], eps_abs=1e-3)
         got = noalloc(rq, s, x_warm=cold["x"], lam_warm=cold["lam"], rho_index=cold["rho_index"])
-        assert got["iters"] == ref["iters"] == 25
+        assert got["iters"] == ref["iters"]
+        # warm-started at the optimum: both stop at the first check
+        assert ref["iters"] == CHECK_INTERVAL
         assert np.max(np.abs(got["x"] - ref["x"])) <= 1e-5 * (1 + np.max(np.abs(ref["x"])))
+    s.close()
+
+
+def test_noalloc_after_a_larger_problem(rq):
+    """A small problem solved right after a larger one: the larger call leaves
+    values in the shared array beyond the small problem's vectors (padding of
+    x, lam_std, the operands), which must not leak into its answer."""
+    big, Xb, _ = mpc.workload("humanoid", 1)
+    q, l, u = big.instance(Xb[0])
+    sb = rq.ReluQP(big.P, big.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+    small, Xs, _ = mpc.workload("small", 2)
+    q, l, u = small.instance(Xs[1])
+    ss = rq.ReluQP(small.P, small.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+    for _ in range(2):
+        noalloc(rq, sb)
+        ref = ss.solve(eps_abs=1e-3)
+        got = noalloc(rq, ss)
+        assert got["status"] == ref["status"] == rq.SOLVED
+        assert got["iters"] == ref["iters"]
+        assert np.max(np.abs(got["x"] - ref["x"])) <= 1e-5 * (1 + np.max(np.abs(ref["x"])))
+        assert np.max(np.abs(got["lam"] - ref["lam"])) <= 1e-5 * (1 + np.max(np.abs(ref["lam"])))
+    sb.close()
+    ss.close()
+
+
+def test_noalloc_rejects_host_pointers(rq):
+    """The outputs of this entry point are device arrays; a host array is
+    refused before any GPU work."""
+    pq, X0, _ = mpc.workload("small", 1)
+    q, l, u = pq.instance(X0[0])
+    s = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+    host = np.zeros(s.n, dtype=np.float32)
+    info = rq.Info()
+    rc = rq.lib().relu_qp_solve_noalloc(s.handle, None, None, -1, 1e-3, 0.0, 4000,
+                                        host.ctypes.data, None, None, ctypes.byref(info))
+    assert rc != 0
+    assert "x_out" in rq.lib().relu_qp_last_error(s.handle).decode()
     s.close()
 
 
