@@ -401,6 +401,11 @@ const char* relu_qp_server_error(relu_qp_server_t s);
  * their device time from CUDA events recorded on the handle's stream around
  * each chunk's run of consecutive layer launches (layer_timed counts the
  * launches those spans cover; up to 8192 spans per solve are timed).
+ * `host_checks` / `host_gap_ms` (batched solves, while profiling): the checks
+ * after which the host read the active-QP count back (one stream synchronise
+ * each) and the summed device time between the last kernel before each of
+ * those reads and the first event the host enqueued after it returned, i.e.
+ * how long the GPU waited on the host round trip.
  */
 typedef struct relu_qp_prof {
     long long launches;
@@ -408,6 +413,8 @@ typedef struct relu_qp_prof {
     long long layer_timed;
     double layer_ms;
     double layer_flops;
+    long long host_checks;
+    double host_gap_ms;
 } relu_qp_prof;
 
 /* Read the counters into *out (may be NULL), then reset them if `reset`, then

@@ -530,6 +530,8 @@ void relu_qp_destroy(relu_qp_t h) {
     rq::batch_release(h);
     for (cudaEvent_t e : h->prof_ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->gap_ev)
+        if (e) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
@@ -698,15 +700,21 @@ int relu_qp_profile(relu_qp_t h, int enable, int reset, relu_qp_prof* out) {
         out->layer_timed = h->layer_timed;
         out->layer_ms = h->layer_ms;
         out->layer_flops = h->layer_flops;
+        out->host_checks = h->host_checks;
+        out->host_gap_ms = h->host_gap_ms;
     }
     if (reset) {
         h->launches = h->layer_launches = h->layer_timed = 0;
         h->layer_ms = h->layer_flops = 0.0;
+        h->host_checks = 0;
+        h->host_gap_ms = 0.0;
     }
     if (enable >= 0) {
         if (enable && h->prof_ev.empty()) {
             h->prof_ev.resize(2 * 8192, nullptr);
             for (auto& e : h->prof_ev) RQ_CUDA(h, cudaEventCreate(&e));
+            h->gap_ev.resize(2 * 256, nullptr);
+            for (auto& e : h->gap_ev) RQ_CUDA(h, cudaEventCreate(&e));
         }
         h->prof_on = enable ? 1 : 0;
     }

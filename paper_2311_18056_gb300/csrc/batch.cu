@@ -960,7 +960,7 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
                 // operand set read by this layer: 4..6 = s (3-way), else pair ((j-1)&1)
                 if (timed && j == 1) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
                 RQ_TRY(tc_layer(h, q, j == 0 ? -1 : ((j - 1) & 1), tiles_max,
-                                ceil_div(active, kSlotTile) + h->nr - 1, j > 0));
+                                tiles_now > 0 ? tiles_now : ceil_div(active, kSlotTile) + h->nr - 1, j > 0));
                 ++h->launches;
                 if (j > 0) {
                     ++h->layer_launches;
@@ -994,14 +994,18 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
 }
 
 // Residual products of a check: [P; A] x, then A^T lam_std (Eqs. primal, dual).
-int run_check(relu_qp_t h, const BatchParams& p, int active) {
+// tiles_now: slot tiles in use when the host knows them (> 0), else a bound
+// from the active QP count is used.
+int run_check(relu_qp_t h, const BatchParams& p, int active, int tiles_now) {
     BatchWork& w = h->bw;
     const int tiles_max = w.slots / kSlotTile;
     BatchParams q = p;
     if (w.prec == RELU_QP_PREC_BF16X3 && w.check_tc) {
         q.CK = static_cast<__nv_bfloat16*>(w.CK);
-        RQ_TRY(tc_check(h, q, 1, tiles_max));
-        RQ_TRY(tc_check(h, q, 2, tiles_max));
+        const int active_tiles =
+            tiles_now > 0 ? tiles_now : std::min(tiles_max, ceil_div(active, kSlotTile) + h->nr - 1);
+        RQ_TRY(tc_check(h, q, 1, tiles_max, active_tiles));
+        RQ_TRY(tc_check(h, q, 2, tiles_max, active_tiles));
     } else {
         q.CK32 = w.CK32;
         RQ_TRY(check32(h, q, w.Wc32, tiles_max, active, 1));
@@ -1061,7 +1065,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     // slot tiles in use: exact at a cold start (every QP in the starting bank entry's
     // group) and after each check, an upper bound after a warm start
     int tiles_now = rw ? std::min(tiles_max, ceil_div(B, kSlotTile) + h->nr - 1) : ceil_div(B, kSlotTile);
-    size_t prof_used = 0;
+    size_t prof_used = 0, gap_used = 0;
     bool tail_used = false;
     while (it < max_iter) {
         const int len = std::min(chunk, max_iter - it);
@@ -1070,7 +1074,7 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         RQ_TRY(run_layers(h, p, len, check, active, tiles_now, prof_used));
         it += len;
         if (check) {
-            RQ_TRY(run_check(h, p, active));
+            RQ_TRY(run_check(h, p, active, tiles_now));
             DecideArgs d{B, it, last_chunk ? 1 : 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO,
                          w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, 0, max_iter, nullptr, nullptr};
             batch_decide_kernel<<<B, kDecideThreads, 0, h->stream>>>(p, d);
@@ -1081,8 +1085,15 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         RQ_TRY(regroup_slots(h, p, B, check));
         if (check) {
             int cnt[CNT_WORDS] = {0, 0, 0, 0};
+            // profiling: how long the GPU waits for this host round trip
+            const bool gap = h->prof_on && gap_used + 2 <= h->gap_ev.size();
+            if (gap) RQ_CUDA(h, cudaEventRecord(h->gap_ev[gap_used], h->stream));
             RQ_CUDA(h, cudaMemcpyAsync(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
             RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+            if (gap) {
+                RQ_CUDA(h, cudaEventRecord(h->gap_ev[gap_used + 1], h->stream));
+                gap_used += 2;
+            }
             if (cnt[CNT_ERR]) break;     // reported below
             if (cnt[CNT_ACTIVE] == 0) break;
             active = cnt[CNT_ACTIVE];
@@ -1113,6 +1124,12 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         h->layer_timed += h->prof_span_launches[e / 2];
     }
     h->prof_span_launches.clear();
+    for (size_t e = 0; e + 1 < gap_used; e += 2) {
+        float ms = 0.f;
+        RQ_CUDA(h, cudaEventElapsedTime(&ms, h->gap_ev[e], h->gap_ev[e + 1]));
+        h->host_gap_ms += ms;
+        ++h->host_checks;
+    }
     // ---- outputs (scaled handles: x = D xb, z = zb / E, lam = E lamb / c) ----
     RQ_TRY(scale_rows(h, w.XO, B, n, n, h->sc_x));
     if (Zo && m > 0) RQ_TRY(scale_rows(h, w.ZO, B, m, m, h->sc_z));
@@ -1436,7 +1453,7 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
     h->prof_span_launches.clear();    // the server does not read the layer events
     RQ_TRY(regroup_slots(h, p, w.cap, true));
     RQ_TRY(run_layers(h, p, ci, true, f.active, 0, prof_used));
-    RQ_TRY(run_check(h, p, f.active));
+    RQ_TRY(run_check(h, p, f.active, 0));
     RQ_SCUDA(s, cudaMemsetAsync(f.d.cnt, 0, sizeof(int), f.stream));
     DecideArgs dd{w.cap, 0, 0, h->opts.adaptive_rho, s->eps_abs, s->eps_rel, w.XO, w.ZO, w.LO,
                   w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, ci, s->max_iter, f.d.done, f.d.cnt};

@@ -504,7 +504,8 @@ int tc_prepare(relu_qp_t h);                     // BF16 splits of every W_rho a
 // operand_set < 0: accurate (3-way) layer; pdl: programmatic dependent launch on the
 // previous kernel of the stream (refined layers only)
 int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int active_tiles, bool pdl = false);
-int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles);   // phase 1: [P; A] x, 2: A^T lam
+// phase 1: [P; A] x, 2: A^T lam; active_tiles: slot tiles in use (an upper bound)
+int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles, int active_tiles);
 // Refined layers 1 .. nl of a chunk in one persistent launch (flags of layer nl
 // get last_flags); active_tiles = slot tiles in use (an upper bound).
 // RELU_QP_ERR_UNSUPPORTED: not possible here (too many CTAs for one wave, or the

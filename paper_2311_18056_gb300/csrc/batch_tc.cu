@@ -256,7 +256,9 @@ struct TcSmem {
     static constexpr int kA = NA * kTileBytesA;
     static constexpr int kB = NB * BN * 128;
     static constexpr int kStage = kA + kB;
-    static constexpr int kXpose = 8 * 32 * 17 * 4;      // epilogue transpose buffers (8 warps)
+    // epilogue transpose buffers (8 warps); the drained (3-part) modes read their
+    // sums transposed from the drain buffer and need none
+    static constexpr int kXpose = NA == 3 ? 0 : 8 * 32 * 17 * 4;
     // the partners' partial sums of this CTA's columns: KS - 1 buffers of [128 slots][BN / KS
     // columns], 16-byte chunks swizzled by slot
     static constexpr int kRecv = KS > 1 ? (KS - 1) * kSlotTile * (BN / KS) * 4 : 0;
@@ -1223,7 +1225,7 @@ struct TcState {
     // encoded maps, keyed by box rows
     CUtensorMap opnd_map[2], ck_map[2];  // operand tensors, boxes of 128 and of 32 slot rows
     CUtensorMap wb_map[kNumLayerBN];     // weights, box rows kLayerBN[i]
-    CUtensorMap wcb_map[2];              // check matrix, box rows 64 and 128
+    CUtensorMap wcb_map[3];              // check matrix, box rows 64, 128 and 96
 };
 
 int encode_2d(relu_qp_t h, TcState* st, CUtensorMap* map, void* base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
@@ -1383,14 +1385,18 @@ int dispatch_refined(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, cons
     }
 }
 
-// 3-part modes: b64 / b128 are the maps with 64- and 128-row boxes
+// 3-part modes: b64 / b96 are the weight maps with 64- and 96-row boxes.  The
+// drained accumulation keeps FP32 sums of BN / 2 columns per epilogue warp in
+// shared memory, which leaves room for two pipeline stages at BN = 64 or 96.
+// BN = 96 when it turns two waves of CTAs over the active slot tiles into one
+// (the full batch: 25 row blocks of 64 x 8 tiles = 200 CTAs, of 96: 136); the
+// tile width does not change any output's arithmetic (the k order is fixed).
 template <int MODE>
-int dispatch_3part(relu_qp_t h, int bn, const CUtensorMap& b64, const CUtensorMap& b128, const BatchParams& p,
-                   const TcArgs& g, const CUtensorMap* a, int tiles) {
-    // the drained accumulation keeps FP32 sums of BN / 2 columns per epilogue warp in
-    // shared memory: BN = 64 leaves room for two pipeline stages
-    (void)bn;
-    (void)b128;
+int dispatch_3part(relu_qp_t h, int active_tiles, const CUtensorMap& b64, const CUtensorMap& b96,
+                   const BatchParams& p, const TcArgs& g, const CUtensorMap* a, int tiles) {
+    const long long w64 = (long long)ceil_div(g.rows, 64) * active_tiles;
+    const long long w96 = (long long)ceil_div(g.rows, 96) * active_tiles;
+    if (w64 > h->num_sms && w96 <= h->num_sms) return launch_tc<MODE, 96, 1>(h, a, b96, p, g, tiles, false);
     return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles, false);
 }
 
@@ -1415,8 +1421,8 @@ int tc_prepare(relu_qp_t h) {
     }
     for (int i = 0; i < kNumLayerBN; ++i)
         RQ_TRY(encode_2d(h, st, &st->wb_map[i], w.WB, (uint64_t)h->nr * 3 * w.Rpad, w.ldk, kLayerBN[i]));
-    for (int i = 0; i < 2; ++i)
-        RQ_TRY(encode_2d(h, st, &st->wcb_map[i], w.WCB, 3ull * w.npad, w.ldkc, 64 << i));
+    for (int i = 0; i < 3; ++i)
+        RQ_TRY(encode_2d(h, st, &st->wcb_map[i], w.WCB, 3ull * w.npad, w.ldkc, i == 2 ? 96 : 64 << i));
     return RELU_QP_OK;
 }
 
@@ -1476,7 +1482,8 @@ int tc_layer(relu_qp_t h, const BatchParams& p, int operand_set, int tiles, int 
     for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
     if (operand_set < 0) {   // accurate: s1, s2, s3 are parts 4..6
         for (int a = 0; a < 3; ++a) g.a_row[a] = (4 + a) * w.slots;
-        return dispatch_3part<MODE_LAYER_ACCURATE>(h, 64, st->wb_map[2], st->wb_map[4], p, g, st->opnd_map, tiles);
+        return dispatch_3part<MODE_LAYER_ACCURATE>(h, active_tiles, st->wb_map[2], st->wb_map[3], p, g,
+                                                   st->opnd_map, tiles);
     }
     // the configuration tuned for this many active slot tiles
     const LayerCfg c = cfg_for(st, active_tiles);
@@ -1516,7 +1523,7 @@ int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int
 
 void tc_disable_chunk(relu_qp_t h) { static_cast<TcState*>(h->bw.tc)->chunk_ok = false; }
 
-int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
+int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles, int active_tiles) {
     BatchWork& w = h->bw;
     TcState* st = static_cast<TcState*>(w.tc);
     TcArgs g{};
@@ -1530,8 +1537,8 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles) {
         g.b_row[a] = a * w.npad;
     }
     if (phase == 1)
-        return dispatch_3part<MODE_CHECK1>(h, 64, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
-    return dispatch_3part<MODE_CHECK2>(h, 64, st->wcb_map[0], st->wcb_map[1], p, g, st->ck_map, tiles);
+        return dispatch_3part<MODE_CHECK1>(h, active_tiles, st->wcb_map[0], st->wcb_map[2], p, g, st->ck_map, tiles);
+    return dispatch_3part<MODE_CHECK2>(h, active_tiles, st->wcb_map[0], st->wcb_map[2], p, g, st->ck_map, tiles);
 }
 
 // Launch tc_diag_wait_kernel on `stream` with the words at dev (>= 4 ints,

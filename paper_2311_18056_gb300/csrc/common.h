@@ -169,6 +169,10 @@ struct relu_qp_s {
     int prof_on = 0;
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_span_launches;     // launches covered by each recorded event pair
+    // host round trips of a batched solve (profiling): event pairs around each read-back
+    std::vector<cudaEvent_t> gap_ev;
+    long long host_checks = 0;
+    double host_gap_ms = 0.0;
     std::string err;
     std::vector<void*> allocs;               // every cudaMalloc of the handle
     size_t dev_bytes = 0;                    // bytes of those allocations (opts.device_budget caps it)
