@@ -405,7 +405,8 @@ const char* relu_qp_server_error(relu_qp_server_t s);
  * after which the host read the active-QP count back (one stream synchronise
  * each) and the summed device time between the last kernel before each of
  * those reads and the first event the host enqueued after it returned, i.e.
- * how long the GPU waited on the host round trip.
+ * how long the GPU waited on the host round trip.  `resident_launches`: chunk
+ * launches that ran the resident-weight kernel (one slot tile of few QPs).
  */
 typedef struct relu_qp_prof {
     long long launches;
@@ -415,6 +416,7 @@ typedef struct relu_qp_prof {
     double layer_flops;
     long long host_checks;
     double host_gap_ms;
+    long long resident_launches;
 } relu_qp_prof;
 
 /* Read the counters into *out (may be NULL), then reset them if `reset`, then

@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
 class Prof(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("layer_launches", ctypes.c_longlong),
                 ("layer_timed", ctypes.c_longlong), ("layer_ms", _c_double), ("layer_flops", _c_double),
-                ("host_checks", ctypes.c_longlong), ("host_gap_ms", _c_double)]
+                ("host_checks", ctypes.c_longlong), ("host_gap_ms", _c_double),
+                ("resident_launches", ctypes.c_longlong)]
 
 
 class Info(ctypes.Structure):

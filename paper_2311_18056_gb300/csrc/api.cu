@@ -702,11 +702,12 @@ int relu_qp_profile(relu_qp_t h, int enable, int reset, relu_qp_prof* out) {
         out->layer_flops = h->layer_flops;
         out->host_checks = h->host_checks;
         out->host_gap_ms = h->host_gap_ms;
+        out->resident_launches = h->resident_launches;
     }
     if (reset) {
         h->launches = h->layer_launches = h->layer_timed = 0;
         h->layer_ms = h->layer_flops = 0.0;
-        h->host_checks = 0;
+        h->host_checks = h->resident_launches = 0;
         h->host_gap_ms = 0.0;
     }
     if (enable >= 0) {

@@ -754,6 +754,31 @@ int tc_tune(relu_qp_t h) {
             }
         }
         for (int u = t; u <= tiles; ++u) table[u] = best_c;   // until the next measured count
+        if (t == 1 && tc_small_eligible(h, per_tile, 1)) {
+            // the resident-weight kernel for one tile of few QPs against the best tiled one
+            RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * 2 * tiles, h->stream));
+            int rc = tc_small(h, p, 2, 0u, per_tile, 1);
+            if (rc == RELU_QP_OK) {
+                RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * 2 * tiles, h->stream));
+                RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+                RQ_TRY(tc_small(h, p, 8, 0u, per_tile, 1));
+                RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+                RQ_CUDA(h, cudaEventSynchronize(h->ev1));
+                int site = 0;
+                if (tc_error(h, &site))
+                    return fail(h, RELU_QP_ERR_TIMEOUT, "tensor-core wait " + std::to_string(site) +
+                                                            " passed its deadline while tuning (resident-weight kernel)");
+                float ms = 0.f;
+                RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+                ms /= 8;
+                if (log)
+                    std::fprintf(stderr, "relu_qp tune: n=%d m=%d tiles=1 qps/tile=%d resident-weight us=%.2f\n", h->n,
+                                 h->m, per_tile, 1e3f * ms);
+                tc_small_set(h, ms < best);
+            } else if (rc != RELU_QP_ERR_UNSUPPORTED) {
+                return rc;
+            }
+        }
     }
     tune_perm_kernel<<<ceil_div(w.slots, 256), 256, 0, h->stream>>>(w.slots, w.cap, tiles, kSlotTile, w.perm,
                                                                      w.tile_rho, w.counters);
@@ -930,11 +955,19 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
             if (w.check_tc) q.CK = static_cast<__nv_bfloat16*>(w.CK);
             else q.CK32 = w.CK32;
             if (j == 1 && w.chunk_sync) {
-                // layers 1 .. len-1 in one persistent launch when the tile's CTAs fit in one wave
+                // layers 1 .. len-1 in one persistent launch when the tile's CTAs fit in one wave:
+                // the resident-weight kernel for one tile of few QPs (when the tuner chose it),
+                // else the tiled chunk kernel
                 BatchParams qc = q;
                 qc.flags = 0;
                 if (timed) RQ_CUDA(h, cudaEventRecord(h->prof_ev[prof_used], h->stream));
-                const int rc = tc_chunk(h, qc, len - 1, EPI_LAST | (check ? EPI_CHECK : 0u), tiles_now);
+                int rc = RELU_QP_ERR_UNSUPPORTED;
+                if (tc_small_chosen(h) && tc_small_eligible(h, active, tiles_now)) {
+                    rc = tc_small(h, qc, len - 1, EPI_LAST | (check ? EPI_CHECK : 0u), active, tiles_now);
+                    if (rc != RELU_QP_OK && rc != RELU_QP_ERR_UNSUPPORTED) return rc;
+                    if (rc == RELU_QP_OK) ++h->resident_launches;
+                }
+                if (rc != RELU_QP_OK) rc = tc_chunk(h, qc, len - 1, EPI_LAST | (check ? EPI_CHECK : 0u), tiles_now);
                 if (rc == RELU_QP_OK) {
                     h->launches += 1;
                     h->layer_launches += len - 1;

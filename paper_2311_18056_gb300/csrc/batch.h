@@ -513,6 +513,15 @@ int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles, int active
 // layers one by one.
 int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active_tiles);
 void tc_disable_chunk(relu_qp_t h);
+// Resident-weight chunk kernel (one slot tile of at most 64 active QPs, the
+// layer's rows of Wt kept in shared memory over a cluster of 8 CTAs that
+// split k): refined layers 1 .. nl of a chunk, as tc_chunk.
+// RELU_QP_ERR_UNSUPPORTED: not possible here (more tiles or QPs, too large a
+// problem for one wave, or a refused launch, which disables it for the handle).
+bool tc_small_eligible(relu_qp_t h, int active, int active_tiles);
+int tc_small(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active, int active_tiles);
+void tc_small_set(relu_qp_t h, bool use);   // use it where eligible (set by the tuner)
+bool tc_small_chosen(relu_qp_t h);
 void tc_release(relu_qp_t h);
 // refined-layer configuration: K split over a cluster of ks CTAs, tile width bn
 struct LayerCfg {

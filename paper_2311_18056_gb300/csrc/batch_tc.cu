@@ -1178,6 +1178,311 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Resident-weight chunk kernel: the refined layers 1 .. nl of a chunk when a
+// single slot tile holds at most NS active QPs (the middle and end of a
+// batched solve, when few QPs are left).
+//
+// The roles of the operands are swapped: the MMA's M = 128 rows are rows of
+// the layer Wt and its N = NS columns are the QP slots, so that a CTA's rows
+// of Wt, over its k range, stay in shared memory for the whole chunk and each
+// layer only loads the (small) operand of the slots.  A cluster of 8 CTAs
+// shares a block of 128 rows and splits k into 8 ranges (<= 4 k-blocks each:
+// w1 and w2 of 128 rows x 256 k are 128 KB); every CTA sends its partial sums
+// of rows 16 r .. 16 r + 15 to rank r through distributed shared memory, and
+// rank r adds the 8 partials in rank order and applies the element-wise layer
+// (chunk4_apply) to its 16 rows x NS slots.  Layers are ordered by the tile's
+// counter as in tc_chunk_kernel (release after the epilogue, acquire before
+// the next operand load); every wait has a deadline.
+// Warps: 0 TMA, 1 MMA (one lane), 2-5 epilogue (warp w reads TMEM lanes of
+// quadrant w % 4).
+// ---------------------------------------------------------------------------
+constexpr int kSmallKS = 8;                          // K split over a cluster of 8 CTAs
+constexpr int kSmallRows = 128;                      // rows of Wt per CTA (the MMA M dimension)
+constexpr int kSmallMaxKb = 4;                       // k-blocks per CTA at most
+constexpr int kSmallOwn = kSmallRows / kSmallKS;     // rows each CTA finalises
+constexpr int kSmallThreads = 192;
+
+template <int NS>
+struct SmallSmem {
+    static constexpr int kWPart = kSmallRows * 128;                 // one k-block of one weight part
+    static constexpr int kOpPart = NS * 128;                        // one k-block of one operand part
+    static constexpr int kW = 2 * kSmallMaxKb * kWPart;
+    static constexpr int kOp = 2 * kSmallMaxKb * kOpPart;
+    static constexpr int kRecv = kSmallKS * kSmallOwn * NS * 4;      // [sender][16 rows][NS slots] FP32
+    static constexpr int kBytes = kW + kOp + kRecv + 1024 /* align */ + 256 /* barriers */;
+};
+
+template <int NS>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+    tc_small_kernel(const __grid_constant__ CUtensorMap tmA32, const __grid_constant__ CUtensorMap tmW,
+                    BatchParams p, TcArgs g, ChunkArgs c) {
+    static_assert(NS == 32 || NS == 64, "32 or 64 slots");
+    using L = SmallSmem<NS>;
+    constexpr int TCOLS = tmem_cols(2 * NS);
+    if (cluster_size() != (uint32_t)kSmallKS) {
+        if (threadIdx.x == 0) atomicExch(g.err, RELU_QP_ERR_CUDA);
+        return;
+    }
+    const int tile = 0;                                 // the single active slot tile
+    const int slot0 = 0;
+    const int rank = (int)cluster_rank();
+    const int row0 = (blockIdx.x / kSmallKS) * kSmallRows;
+    const int ri = p.tile_rho[tile];
+    const int kb_begin = rank * g.num_kb / kSmallKS;
+    const int kb_count = (rank + 1) * g.num_kb / kSmallKS - kb_begin;
+    const unsigned nct = gridDim.x;
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sW = smem;
+    uint8_t* sOp = smem + L::kW;
+    float* recv = reinterpret_cast<float*>(smem + L::kW + L::kOp);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::kW + L::kOp + L::kRecv);
+    // bars: 0 weights loaded, 1 operand loaded, 2 accumulators ready, 3 accumulators
+    // consumed, 4 partials received; then the TMEM address and the failure flag
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
+    int& s_fail = *reinterpret_cast<int*>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        mbar_init(smem_u32(&bars[2]), 1);
+        mbar_init(smem_u32(&bars[3]), 4);             // one arrival per epilogue warp
+        mbar_init(smem_u32(&bars[4]), kSmallKS);      // one arrival per sender CTA
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    cluster_sync();        // every partner's barriers are initialised before anything is sent
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------- TMA producer -------------------------
+        if (lane == 0) {
+            prefetch_map(&tmA32);
+            prefetch_map(&tmW);
+            // the weight slice, once: parts w1, w2 of rows row0 .. row0 + 127, this CTA's k-blocks
+            const uint32_t wfull = smem_u32(&bars[0]);
+            mbar_expect_tx(wfull, (uint32_t)(2 * kb_count * L::kWPart));
+            for (int b = 0; b < kb_count; ++b)
+                for (int part = 0; part < 2; ++part)
+                    tma_load_2d(smem_u32(sW + (part * kSmallMaxKb + b) * L::kWPart), &tmW,
+                                (kb_begin + b) * kBK, g.b_row[part] + ri * g.b_rho_stride + row0, wfull);
+            const uint32_t opfull = smem_u32(&bars[1]);
+            int loads = 0;
+            for (int j = 1; j <= c.nl; ++j) {
+                if (*(volatile int*)&s_fail) break;
+                if (j > 1) {
+                    // every CTA of the tile is done with layer j - 1 (which also means this
+                    // CTA's MMAs of layer j - 1 have read the operand buffer)
+                    if (!wait_counter_geq(c.sync + tile, (unsigned)(j - 1) * nct, kWaitNs)) {
+                        wait_failed(g.err, WS_PROD_SYNC);
+                        s_fail = 1;
+                        break;
+                    }
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+                const int a0 = 2 * ((j - 1) & 1) * c.slots + slot0;
+                mbar_expect_tx(opfull, (uint32_t)(2 * kb_count * L::kOpPart));
+                for (int b = 0; b < kb_count; ++b)
+                    for (int part = 0; part < 2; ++part)
+                        for (int gr = 0; gr < NS / 32; ++gr)
+                            tma_load_2d(smem_u32(sOp + (part * kSmallMaxKb + b) * L::kOpPart + gr * 4096), &tmA32,
+                                        (kb_begin + b) * kBK, a0 + part * c.slots + 32 * gr, opfull);
+                ++loads;
+            }
+            // the copies in flight land before the CTA may exit (bounded waits)
+            if (loads > 0) mbar_wait(opfull, (uint32_t)((loads - 1) & 1));
+            mbar_wait(wfull, 0);
+        }
+    } else if (warp == 1) {
+        // ------------------------- MMA issuer -------------------------
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(NS);
+            int commits = 0;
+            bool ok = mbar_wait(smem_u32(&bars[0]), 0);
+            if (!ok) {
+                wait_failed(g.err, WS_MMA_FULL);
+                s_fail = 1;
+            }
+            for (int j = 1; ok && j <= c.nl; ++j) {
+                if (*(volatile int*)&s_fail) break;
+                if (j > 1 && !mbar_wait(smem_u32(&bars[3]), (uint32_t)((j - 2) & 1))) {
+                    wait_failed(g.err, WS_MMA_ACC);
+                    s_fail = 1;
+                    break;
+                }
+                if (!mbar_wait(smem_u32(&bars[1]), (uint32_t)((j - 1) & 1))) {
+                    wait_failed(g.err, WS_MMA_FULL);
+                    s_fail = 1;
+                    break;
+                }
+                fence_after();
+                const uint64_t dw = sdesc(smem_u32(sW)), dop = sdesc(smem_u32(sOp));
+                for (int b = 0; b < kb_count; ++b) {
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+#pragma unroll
+                        for (int pr = 0; pr < 3; ++pr) {
+                            // (w1, d_hi) -> accumulator 0; (w2, d_hi), (w1, d_lo) -> accumulator 1
+                            const int iw = pr == 1 ? 1 : 0, io = pr == 2 ? 1 : 0;
+                            const uint64_t ad = dw + (uint64_t)(((iw * kSmallMaxKb + b) * L::kWPart + kk * 32) >> 4);
+                            const uint64_t bd = dop + (uint64_t)(((io * kSmallMaxKb + b) * L::kOpPart + kk * 32) >> 4);
+                            const bool first = b == 0 && kk == 0 && pr <= 1;
+                            mma_bf16(tmem + (pr == 0 ? 0 : NS), ad, bd, IDESC, first ? 0u : 1u);
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&bars[2]));
+                ++commits;
+            }
+            if (commits > 0 && !mbar_wait(smem_u32(&bars[2]), (uint32_t)((commits - 1) & 1))) {
+                wait_failed(g.err, WS_MMA_ACC);
+                s_fail = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------- epilogue (warps 2-5) -------------------------
+        const int q = warp & 3;                       // TMEM lane quadrant: rows 32 q .. 32 q + 31
+        const int et = (warp - 2) * 32 + lane;        // 0 .. 127
+        // the element this thread finalises: slot es, rows fr0 .. fr0 + 7 of the block
+        const int es = et >> 1;
+        const int fr = rank * kSmallOwn + (et & 1) * 8;          // row within the 128-row block
+        const int fr0 = row0 + fr;
+        const bool mine = es < NS;
+        const int eqp = mine ? p.perm[slot0 + es] : -1;
+        const bool n_aligned = (p.n & 3) == 0;
+        auto whole4 = [&](int r0) { return r0 + 4 <= g.rows && (r0 + 4 <= p.n || (r0 >= p.n && n_aligned)); };
+        // sender side: lane = row 32 q + lane of the block; rows 16 o .. 16 o + 15 go to rank o
+        const int srow = q * 32 + lane;
+        const int owner = srow / kSmallOwn;
+        const uint32_t recv_remote = mapa(smem_u32(recv), (uint32_t)owner);
+        for (int j = 1; j <= c.nl; ++j) {
+            BatchParams pj = p;
+            pj.flags = EPI_REFINE | (j == c.nl ? c.last_flags : 0u);
+            pj.Dhi = c.OP + (size_t)(2 * (j & 1)) * c.opart;
+            pj.Dlo = pj.Dhi + c.opart;
+            // this thread's inputs load while the MMAs run
+            Chunk4R in[2];
+            if (eqp >= 0) {
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2)
+                    if (whole4(fr0 + 4 * h2)) chunk4_load(pj, eqp, ri, fr0 + 4 * h2, in[h2]);
+            }
+            // the accumulators of layer j
+            bool ready = true;
+            if (lane == 0) ready = mbar_wait_sleep(smem_u32(&bars[2]), (uint32_t)((j - 1) & 1), 128);
+            ready = __shfl_sync(0xffffffffu, ready, 0);
+            if (ready) ready = mbar_wait(smem_u32(&bars[2]), (uint32_t)((j - 1) & 1));
+            ready = __all_sync(0xffffffffu, ready);
+            if (ready) {
+                fence_after();
+                const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+                // partial sums of this CTA's k range for row srow, all NS slots -> rank owner,
+                // into its receive slot `rank` at row srow % 16
+                const uint32_t dst = recv_remote + 4u * (uint32_t)((rank * kSmallOwn + srow % kSmallOwn) * NS);
+#pragma unroll
+                for (int c0 = 0; c0 < NS; c0 += 16) {
+                    float v[16], w[16];
+                    tmem_ld16(tl + c0, v);
+                    tmem_ld16(tl + NS + c0, w);
+#pragma unroll
+                    for (int t = 0; t < 16; t += 4)
+                        st_cluster4(dst + 4u * (uint32_t)(c0 + t), v[t] + w[t], v[t + 1] + w[t + 1], v[t + 2] + w[t + 2],
+                                    v[t + 3] + w[t + 3]);
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars[3]));          // this warp's TMEM reads are done
+            // lanes 0 and 16 announce their half-warp's rows to the two owners
+            if ((lane & 15) == 0) mbar_arrive_cluster(mapa(smem_u32(&bars[4]), (uint32_t)owner));
+            bool got = ready;
+            if (got) {
+                if (lane == 0) got = mbar_wait_cluster(smem_u32(&bars[4]), (uint32_t)((j - 1) & 1), 64);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (got) got = mbar_wait_cluster(smem_u32(&bars[4]), (uint32_t)((j - 1) & 1), 0);
+                got = __all_sync(0xffffffffu, got);
+            }
+            if (!ready || !got) {
+                if (lane == 0) {
+                    wait_failed(g.err, ready ? WS_EPI_RECV : WS_EPI_ACC);
+                    s_fail = 1;
+                }
+            } else if (eqp >= 0) {
+                // the 8 partials of rows fr .. fr + 7, slot es, added in rank order
+                float acc[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float tsum = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kSmallKS; ++k) {
+                        const float v = recv[(k * kSmallOwn + (fr - rank * kSmallOwn) + i) * NS + es];
+                        tsum = k == 0 ? v : tsum + v;
+                    }
+                    acc[i] = tsum;
+                }
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int r0 = fr0 + 4 * h2;
+                    if (whole4(r0)) {
+                        float rs4[4] = {1.f, 1.f, 1.f, 1.f};
+                        if (r0 >= p.n) ld4(p.rs + (r0 - p.n), rs4);
+                        const float a4[4] = {acc[4 * h2], acc[4 * h2 + 1], acc[4 * h2 + 2], acc[4 * h2 + 3]};
+                        chunk4_apply(pj, slot0 + es, eqp, ri, r0, a4, in[h2], rs4);
+                    } else {
+                        for (int t = 0; t < 4; ++t)
+                            if (r0 + t < g.rows) layer_elem(pj, slot0 + es, eqp, ri, r0 + t, acc[4 * h2 + t]);
+                    }
+                }
+            }
+            // release this CTA's part of layer j (operand and state stores) before the
+            // tile's counter moves on; the epilogue warps leave the loop together
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            fence_before();
+            const int mine_fail = *(volatile int*)&s_fail;
+            int any;
+            asm volatile(
+                "{\n .reg .pred pi, po;\n setp.ne.s32 pi, %1, 0;\n"
+                " bar.red.or.pred po, 1, %2, pi;\n selp.s32 %0, 1, 0, po;\n}\n"
+                : "=r"(any)
+                : "r"(mine_fail), "r"(128)
+                : "memory");
+            if (any) break;
+            if (warp == 2 && lane == 0) {
+                if (j < c.nl) {
+                    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c.sync + tile) : "memory");
+                } else {
+                    __threadfence();
+                    const unsigned done = atomicAdd(c.sync + c.done_off + tile, 1u) + 1u;
+                    if (done == nct) {
+                        atomicExch(c.sync + tile, 0u);
+                        atomicExch(c.sync + c.done_off + tile, 0u);
+                    }
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync();        // no CTA leaves while a partner may still write into its shared memory
+    if (warp == 1) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Deadline diagnostics: the waits above, made to run out on purpose.  kind 0:
 // an mbarrier that nothing arrives on (mbar_wait_ns); kind 1: a layer counter
 // that nothing increments (wait_counter_geq).  The waiting thread gives up at
@@ -1221,6 +1526,9 @@ struct TcState {
     LayerCfg cfg{1, 128};                // refined layer: K split and width when no table is set
     std::vector<LayerCfg> cfg_by_tiles;  // [t] = the tuned configuration for t active slot tiles
     bool chunk_ok = true;                // persistent chunk kernel usable (cleared after a refused launch)
+    bool small_ok = true;                // resident-weight chunk kernel usable (cleared after a refused launch)
+    bool small_use = false;              // the tuner found it faster for one slot tile of few QPs
+    int small_clusters = -1;             // clusters of it that fit co-resident (-1: not asked yet)
     int* err = nullptr;                  // = counters + CNT_ERR
     // encoded maps, keyed by box rows
     CUtensorMap opnd_map[2], ck_map[2];  // operand tensors, boxes of 128 and of 32 slot rows
@@ -1348,6 +1656,32 @@ int dispatch_chunk(relu_qp_t h, int bn, int ks, const CUtensorMap* wmaps, const 
         }
     }
     return RELU_QP_ERR_UNSUPPORTED;
+}
+
+template <int NS>
+int launch_small(relu_qp_t h, const CUtensorMap& a32, const CUtensorMap& w128, const BatchParams& p,
+                 const TcArgs& g, const ChunkArgs& c) {
+    using L = SmallSmem<NS>;
+    auto kern = tc_small_kernel<NS>;
+    RQ_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kSmallKS * ceil_div(g.rows, kSmallRows), 1);
+    cfg.blockDim = dim3(kSmallThreads);
+    cfg.dynamicSmemBytes = L::kBytes;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSmallKS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a32, w128, p, g, c);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RELU_QP_ERR_UNSUPPORTED;     // the caller uses the other chunk kernel
+    }
+    return RELU_QP_OK;
 }
 
 // Refined layer widths by K split: KS = 4 takes 64 and 128 (each CTA
@@ -1522,6 +1856,74 @@ int tc_chunk(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int
 }
 
 void tc_disable_chunk(relu_qp_t h) { static_cast<TcState*>(h->bw.tc)->chunk_ok = false; }
+
+// Clusters of the resident-weight kernel (its larger instantiation) that the
+// GPU can hold at once; every CTA of a launch must be co-resident, since the
+// layers are ordered by a counter the CTAs wait on.
+int small_clusters_fit(relu_qp_t h) {
+    auto kern = tc_small_kernel<64>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SmallSmem<64>::kBytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kSmallKS * ceil_div(h->R, kSmallRows), 1);
+    cfg.blockDim = dim3(kSmallThreads);
+    cfg.dynamicSmemBytes = SmallSmem<64>::kBytes;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSmallKS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void*)kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+bool tc_small_eligible(relu_qp_t h, int active, int active_tiles) {
+    const BatchWork& w = h->bw;
+    TcState* st = static_cast<TcState*>(w.tc);
+    if (!st || !st->small_ok || !w.chunk_sync || active_tiles != 1 || active < 1 || active > 64) return false;
+    const int nkb = w.ldk / kBK;
+    if (ceil_div(nkb, kSmallKS) > kSmallMaxKb || nkb < kSmallKS) return false;
+    if ((long long)kSmallKS * ceil_div(h->R, kSmallRows) > h->num_sms) return false;
+    if (st->small_clusters < 0) st->small_clusters = small_clusters_fit(h);
+    return st->small_clusters >= ceil_div(h->R, kSmallRows);
+}
+
+void tc_small_set(relu_qp_t h, bool use) { static_cast<TcState*>(h->bw.tc)->small_use = use; }
+bool tc_small_chosen(relu_qp_t h) { return static_cast<const TcState*>(h->bw.tc)->small_use; }
+
+int tc_small(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int active, int active_tiles) {
+    BatchWork& w = h->bw;
+    TcState* st = static_cast<TcState*>(w.tc);
+    if (nl < 1 || !tc_small_eligible(h, active, active_tiles)) return RELU_QP_ERR_UNSUPPORTED;
+    TcArgs g{};
+    g.num_kb = w.ldk / kBK;
+    g.rows = h->R;
+    g.err = st->err;
+    g.b_rho_stride = 3 * w.Rpad;
+    for (int b = 0; b < 3; ++b) g.b_row[b] = b * w.Rpad;
+    ChunkArgs c{};
+    c.nl = nl;
+    c.last_flags = last_flags;
+    c.OP = static_cast<__nv_bfloat16*>(w.OPND);
+    c.opart = (size_t)w.slots * w.ldk;
+    c.slots = w.slots;
+    c.sync = w.chunk_sync;
+    c.done_off = w.slots / kSlotTile;
+    const int rc = active <= 32 ? launch_small<32>(h, st->opnd_map[1], st->wb_map[4], p, g, c)
+                                : launch_small<64>(h, st->opnd_map[1], st->wb_map[4], p, g, c);
+    if (rc == RELU_QP_ERR_UNSUPPORTED) st->small_ok = false;   // launch refused: not again for this handle
+    return rc;
+}
 
 int tc_check(relu_qp_t h, const BatchParams& p, int phase, int tiles, int active_tiles) {
     BatchWork& w = h->bw;

@@ -171,7 +171,7 @@ struct relu_qp_s {
     std::vector<int> prof_span_launches;     // launches covered by each recorded event pair
     // host round trips of a batched solve (profiling): event pairs around each read-back
     std::vector<cudaEvent_t> gap_ev;
-    long long host_checks = 0;
+    long long host_checks = 0, resident_launches = 0;
     double host_gap_ms = 0.0;
     std::string err;
     std::vector<void*> allocs;               // every cudaMalloc of the handle

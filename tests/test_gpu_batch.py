@@ -222,3 +222,42 @@ def test_batch_unconstrained_m0(rq):
         X = -np.linalg.solve(P, Q.T).T
         assert np.all(out["status"] == rq.SOLVED)
         assert np.max(np.abs(out["x"] - X)) <= 1e-4
+
+
+@pytest.mark.parametrize("B", [20, 48])
+def test_one_tile_resident_weight_kernel(rq, B):
+    """One slot tile of few QPs (n = m = 800): the tuner times the
+    resident-weight chunk kernel (rows of the layer kept in shared memory over a
+    cluster of 8 CTAs) against the tiled one and uses it where faster.  The
+    iterates after 50 fixed-rho layers match the oracle's within the split
+    form's 1e-4, and a converged solve matches the oracle within 1e-3 with
+    FP64-recomputed residuals within eps."""
+    pq, X0, Q, L, U = mpc_batch("batched", B)
+    s = rq.ReluQP(pq.P, pq.A, L[0], U[0], q=Q[0], sigma=SIGMA, rho_bank=BANK, check_interval=0,
+                  max_batch=B, precision=rq.PREC_BF16X3)
+    s.update_batch(Q, L, U)
+    s.profile(enable=1, reset=True)
+    out = s.solve_batch(max_iter=50)
+    used = s.profile(enable=0)["resident_launches"]
+    s.close()
+    n, m = pq.n, pq.m
+    worst = 0.0
+    for b in range(0, B, 7):
+        v = O.layer_iterates(pq.P, Q[b], pq.A, L[b], U[b], SIGMA, BANK[0], 50)[-1]
+        x, z, lam_l = v[:n], v[n:n + m], v[n + m:]
+        lam = O.std_multiplier(pq.A, x, z, lam_l, O.rho_vector(L[b], U[b], BANK[0]))
+        ref = np.concatenate([x, z, lam])
+        got = np.concatenate([out["x"][b], out["z"][b], out["lam"][b]]).astype(np.float64)
+        worst = max(worst, rel(got, ref))
+    assert worst <= TOL_ITER[1], worst
+    # converged, adaptive rho, checks every 25 layers
+    s = rq.ReluQP(pq.P, pq.A, L[0], U[0], q=Q[0], sigma=SIGMA, rho_bank=BANK, max_batch=B,
+                  precision=rq.PREC_BF16X3)
+    s.update_batch(Q, L, U)
+    s.profile(enable=1, reset=True)
+    conv = s.solve_batch(eps_abs=1e-3, max_iter=4000)
+    used += s.profile(enable=0)["resident_launches"]
+    s.close()
+    assert np.all(conv["status"] == rq.SOLVED)
+    check_converged(rq, pq, Q, L, U, conv, range(0, B, 9))
+    print(f"B={B}: resident-weight chunk launches {used}, iterate error {worst:.2e}")
