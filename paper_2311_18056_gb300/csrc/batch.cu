@@ -320,9 +320,11 @@ int check32(relu_qp_t h, const BatchParams& q, const float* Wc, int tiles_max, i
 // bank switch).
 constexpr int kDecideThreads = 128;
 
-__global__ void __launch_bounds__(kDecideThreads) batch_decide_kernel(BatchParams p, DecideArgs d) {
-    const int qp = blockIdx.x;
-    if (qp >= d.B) return;
+// by_slot: one block per slot of the tiles in use (QP = perm[slot], padding
+// slots return), which covers every active QP; else one block per QP id.
+__global__ void __launch_bounds__(kDecideThreads) batch_decide_kernel(BatchParams p, DecideArgs d, int by_slot) {
+    const int qp = by_slot ? p.perm[blockIdx.x] : (int)blockIdx.x;
+    if (qp < 0 || qp >= d.B) return;
     __shared__ int s_act, s_nri;    // s_act: -1 not active, 0 continue, 1 finished, 2 bank switch
     unsigned* red = p.RED + (size_t)qp * RW_WORDS;
     if (threadIdx.x == 0) {
@@ -547,6 +549,7 @@ BatchParams base_params(relu_qp_t h) {
     for (int r = 0; r < h->nr; ++r) {
         p.rho[r] = (float)h->be[r].rho;
         p.rhod[r] = h->be[r].rho;
+        p.logrho[r] = std::log(h->be[r].rho);
     }
     p.rs = h->rs32;
     p.rsx = h->sc_rx;
@@ -1110,7 +1113,10 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
             RQ_TRY(run_check(h, p, active, tiles_now));
             DecideArgs d{B, it, last_chunk ? 1 : 0, h->opts.adaptive_rho, eps_abs, eps_rel, w.XO, w.ZO, w.LO,
                          w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, 0, max_iter, nullptr, nullptr};
-            batch_decide_kernel<<<B, kDecideThreads, 0, h->stream>>>(p, d);
+            // the active QPs are the ones in the slots of the last regroup: one block per slot
+            const bool by_slot = tiles_now > 0 && tiles_now * kSlotTile < B;
+            batch_decide_kernel<<<by_slot ? tiles_now * kSlotTile : B, kDecideThreads, 0, h->stream>>>(
+                p, d, by_slot ? 1 : 0);
             RQ_CUDA(h, cudaGetLastError());
             ++h->launches;
         }
@@ -1490,7 +1496,7 @@ int family_launch(relu_qp_server_t s, ServeFamily& f) {
     RQ_SCUDA(s, cudaMemsetAsync(f.d.cnt, 0, sizeof(int), f.stream));
     DecideArgs dd{w.cap, 0, 0, h->opts.adaptive_rho, s->eps_abs, s->eps_rel, w.XO, w.ZO, w.LO,
                   w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, ci, s->max_iter, f.d.done, f.d.cnt};
-    batch_decide_kernel<<<w.cap, kDecideThreads, 0, f.stream>>>(p, dd);
+    batch_decide_kernel<<<w.cap, kDecideThreads, 0, f.stream>>>(p, dd, 0);
     RQ_SCUDA(s, cudaGetLastError());
     serve_gather_kernel<<<ceil_div(w.cap * 32, 256), 256, 0, f.stream>>>(
         p, f.d.done, f.d.cnt, f.d.client_of, w.status, w.iters, w.rho_idx, w.nsw, w.rp, w.rd, w.XO, h->sc_x, f.d.Wx,

@@ -37,6 +37,7 @@ struct BatchParams {
     int n, m, R, ldn, ldm, ldR, ldk, n64, ldkc, cap, slots, nr;
     float rho[RQ_MAX_RHO];
     double rhod[RQ_MAX_RHO];
+    double logrho[RQ_MAX_RHO];              // log of each bank entry (the penalty rule's distance)
     const float* rs;                         // per-row penalty scale (1 or eq_scale)
     // scaled problems: the residual and norm factors back to the original problem,
     // 1/(c D) for rows of x and 1/E for constraint rows (nullptr without scaling)
@@ -466,7 +467,7 @@ __device__ __forceinline__ Decision decide_eval(const BatchParams& p, const Deci
                 const double le = log(est);
                 double best = 1e300;
                 for (int k = 0; k < p.nr; ++k) {
-                    const double dd = fabs(le - log(p.rhod[k]));
+                    const double dd = fabs(le - p.logrho[k]);
                     if (dd < best) { best = dd; x.nri = k; }
                 }
             }

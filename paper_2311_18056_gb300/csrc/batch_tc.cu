@@ -179,6 +179,27 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
+// two 16-column loads (the two significance accumulators) behind one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&v)[16], float (&w)[16]) {
+    uint32_t r[16], s[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(s[0]), "=r"(s[1]), "=r"(s[2]), "=r"(s[3]), "=r"(s[4]), "=r"(s[5]), "=r"(s[6]), "=r"(s[7]),
+          "=r"(s[8]), "=r"(s[9]), "=r"(s[10]), "=r"(s[11]), "=r"(s[12]), "=r"(s[13]), "=r"(s[14]), "=r"(s[15])
+        : "r"(tb));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        v[i] = __uint_as_float(r[i]);
+        w[i] = __uint_as_float(s[i]);
+    }
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -599,8 +620,7 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
 #pragma unroll
             for (int c = 0; c < PER; c += 16) {
                 float v[16], w[16];
-                tmem_ld16(tb + cbeg + c, v);
-                tmem_ld16(tb + BN + cbeg + c, w);
+                tmem_ld16x2(tb + cbeg + c, tb + BN + cbeg + c, v, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) dsum[c + t] += v[t] + w[t];
             }
@@ -629,8 +649,7 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
 #pragma unroll
                 for (int c = 0; c < PER; c += 16) {
                     float v[16], w[16];
-                    tmem_ld16(tl + pc0 + c, v);
-                    tmem_ld16(tl + BN + pc0 + c, w);
+                    tmem_ld16x2(tl + pc0 + c, tl + BN + pc0 + c, v, w);
 #pragma unroll
                     for (int t = 0; t < 16; t += 4)
                         st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, half * PER + c + t), v[t] + w[t],
@@ -686,8 +705,7 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
                 for (int t = 0; t < 16; ++t) v[t] = dsum[c0 - cbeg + t];
             } else {
                 float w[16];
-                tmem_ld16(tl + c0, v);
-                tmem_ld16(tl + BN + c0, w);
+                tmem_ld16x2(tl + c0, tl + BN + c0, v, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
             }
@@ -980,6 +998,7 @@ struct ChunkArgs {
     unsigned* sync;            // per slot tile: CTAs done with layers so far (zero at launch), then
                                // at sync + done_off the CTAs done with the whole launch
     int done_off;
+    int ncols;                 // resident-weight kernel: slots in the MMA's N (a multiple of 16)
 };
 
 template <int BN, int STAGES, int KS>
@@ -1212,6 +1231,15 @@ struct SmallSmem {
     static constexpr int kBytes = kW + kOp + kRecv + 1024 /* align */ + 256 /* barriers */;
 };
 
+// float offset of (row, slot) in one sender's [16 rows][NS] block of the
+// receive buffer: the 16-byte chunk index is XORed with the row, so that the
+// 16 rows a half-warp writes at one slot land in different banks
+template <int NS>
+__device__ __forceinline__ int small_off(int row, int slot) {
+    constexpr int MASK = NS / 4 - 1;
+    return row * NS + ((((slot >> 2) ^ (row & MASK))) << 2) + (slot & 3);
+}
+
 template <int NS>
 __global__ void __launch_bounds__(kSmallThreads, 1)
     tc_small_kernel(const __grid_constant__ CUtensorMap tmA32, const __grid_constant__ CUtensorMap tmW,
@@ -1292,10 +1320,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
                     asm volatile("fence.proxy.async.global;" ::: "memory");
                 }
                 const int a0 = 2 * ((j - 1) & 1) * c.slots + slot0;
-                mbar_expect_tx(opfull, (uint32_t)(2 * kb_count * L::kOpPart));
+                mbar_expect_tx(opfull, (uint32_t)(2 * kb_count * ((c.ncols + 31) / 32) * 4096));
                 for (int b = 0; b < kb_count; ++b)
                     for (int part = 0; part < 2; ++part)
-                        for (int gr = 0; gr < NS / 32; ++gr)
+                        for (int gr = 0; gr < (c.ncols + 31) / 32; ++gr)
                             tma_load_2d(smem_u32(sOp + (part * kSmallMaxKb + b) * L::kOpPart + gr * 4096), &tmA32,
                                         (kb_begin + b) * kBK, a0 + part * c.slots + 32 * gr, opfull);
                 ++loads;
@@ -1307,7 +1335,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
     } else if (warp == 1) {
         // ------------------------- MMA issuer -------------------------
         if (lane == 0) {
-            constexpr uint32_t IDESC = idesc_bf16(NS);
+            const uint32_t IDESC = idesc_bf16(c.ncols);
             int commits = 0;
             bool ok = mbar_wait(smem_u32(&bars[0]), 0);
             if (!ok) {
@@ -1359,7 +1387,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
         const int es = et >> 1;
         const int fr = rank * kSmallOwn + (et & 1) * 8;          // row within the 128-row block
         const int fr0 = row0 + fr;
-        const bool mine = es < NS;
+        const bool mine = es < c.ncols;
         const int eqp = mine ? p.perm[slot0 + es] : -1;
         const bool n_aligned = (p.n & 3) == 0;
         auto whole4 = [&](int r0) { return r0 + 4 <= g.rows && (r0 + 4 <= p.n || (r0 >= p.n && n_aligned)); };
@@ -1390,16 +1418,15 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
                 const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
                 // partial sums of this CTA's k range for row srow, all NS slots -> rank owner,
                 // into its receive slot `rank` at row srow % 16
-                const uint32_t dst = recv_remote + 4u * (uint32_t)((rank * kSmallOwn + srow % kSmallOwn) * NS);
-#pragma unroll
-                for (int c0 = 0; c0 < NS; c0 += 16) {
+                const uint32_t dst = recv_remote + 4u * (uint32_t)(rank * kSmallOwn * NS);
+                const int rw = srow % kSmallOwn;
+                for (int c0 = 0; c0 < c.ncols; c0 += 16) {
                     float v[16], w[16];
-                    tmem_ld16(tl + c0, v);
-                    tmem_ld16(tl + NS + c0, w);
+                    tmem_ld16x2(tl + c0, tl + NS + c0, v, w);
 #pragma unroll
                     for (int t = 0; t < 16; t += 4)
-                        st_cluster4(dst + 4u * (uint32_t)(c0 + t), v[t] + w[t], v[t + 1] + w[t + 1], v[t + 2] + w[t + 2],
-                                    v[t + 3] + w[t + 3]);
+                        st_cluster4(dst + 4u * (uint32_t)small_off<NS>(rw, c0 + t), v[t] + w[t], v[t + 1] + w[t + 1],
+                                    v[t + 2] + w[t + 2], v[t + 3] + w[t + 3]);
                 }
             }
             fence_before();
@@ -1427,7 +1454,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1)
                     float tsum = 0.f;
 #pragma unroll
                     for (int k = 0; k < kSmallKS; ++k) {
-                        const float v = recv[(k * kSmallOwn + (fr - rank * kSmallOwn) + i) * NS + es];
+                        const float v = recv[k * kSmallOwn * NS + small_off<NS>((fr - rank * kSmallOwn) + i, es)];
                         tsum = k == 0 ? v : tsum + v;
                     }
                     acc[i] = tsum;
@@ -1919,6 +1946,7 @@ int tc_small(relu_qp_t h, const BatchParams& p, int nl, unsigned last_flags, int
     c.slots = w.slots;
     c.sync = w.chunk_sync;
     c.done_off = w.slots / kSlotTile;
+    c.ncols = std::max(16, (active + 15) / 16 * 16);   // the MMA's N covers the active slots
     const int rc = active <= 32 ? launch_small<32>(h, st->opnd_map[1], st->wb_map[4], p, g, c)
                                 : launch_small<64>(h, st->opnd_map[1], st->wb_map[4], p, g, c);
     if (rc == RELU_QP_ERR_UNSUPPORTED) st->small_ok = false;   // launch refused: not again for this handle
