@@ -661,6 +661,8 @@ int batch_alloc(relu_qp_t h) {
         RQ_TRY(alloc(h, &w.Wc32, (size_t)(n + m) * w.ldkc));
     }
     RQ_TRY(batch_tail_alloc(h));
+    RQ_CUDA(h, cudaMallocHost(reinterpret_cast<void**>(&w.cnt_host), sizeof(int) * CNT_WORDS));
+    RQ_CUDA(h, cudaEventCreateWithFlags(&w.ev_cnt, cudaEventDisableTiming));
     return RELU_QP_OK;
 }
 
@@ -801,6 +803,10 @@ int tc_tune(relu_qp_t h) {
 
 void batch_release(relu_qp_t h) {
     if (h->bw.tc) tc_release(h);
+    if (h->bw.cnt_host) cudaFreeHost(h->bw.cnt_host);
+    if (h->bw.ev_cnt) cudaEventDestroy(h->bw.ev_cnt);
+    h->bw.cnt_host = nullptr;
+    h->bw.ev_cnt = nullptr;
 }
 
 // After the FP64 stage: FP32 check matrix (FP32 backend) or tensor maps and
@@ -932,7 +938,7 @@ int regroup_slots(relu_qp_t h, const BatchParams& p, int nqp, bool assign) {
 // the last layer also writes x into the check operand.  `active` is the
 // number of QPs in the batch (for the tile-width choice and the FLOP count).
 int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int active, int tiles_now,
-               size_t& prof_used) {
+               size_t& prof_used, int j_begin = 0, int j_end = 1 << 30) {
     BatchWork& w = h->bw;
     const int R = h->R;
     const bool bf16 = w.prec == RELU_QP_PREC_BF16X3;
@@ -945,9 +951,9 @@ int run_layers(relu_qp_t h, const BatchParams& p, int len, bool check, int activ
     // between them would break the programmatic overlap of consecutive layers)
     const bool timed = h->prof_on && bf16 && len > 1 && prof_used + 2 <= h->prof_ev.size();
     // layer counters of the persistent chunk kernel start at zero
-    if (bf16 && w.chunk_sync && len > 1)
+    if (bf16 && w.chunk_sync && len > 1 && j_end > 1)
         RQ_CUDA(h, cudaMemsetAsync(w.chunk_sync, 0, sizeof(unsigned) * 2 * tiles_max, h->stream));
-    for (int j = 0; j < len; ++j) {
+    for (int j = j_begin; j < std::min(len, j_end); ++j) {
         BatchParams q = p;
         q.flags = 0;
         if (j == len - 1) q.flags |= EPI_LAST | (check ? EPI_CHECK : 0u);
@@ -1103,11 +1109,13 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
     int tiles_now = rw ? std::min(tiles_max, ceil_div(B, kSlotTile) + h->nr - 1) : ceil_div(B, kSlotTile);
     size_t prof_used = 0, gap_used = 0;
     bool tail_used = false;
+    bool first_done = false;     // the chunk's first layer was enqueued before the host's read-back
     while (it < max_iter) {
         const int len = std::min(chunk, max_iter - it);
         const bool last_chunk = it + len == max_iter;
         const bool check = (ci > 0 && (it + len) % ci == 0) || last_chunk;
-        RQ_TRY(run_layers(h, p, len, check, active, tiles_now, prof_used));
+        RQ_TRY(run_layers(h, p, len, check, active, tiles_now, prof_used, first_done ? 1 : 0));
+        first_done = false;
         it += len;
         if (check) {
             RQ_TRY(run_check(h, p, active, tiles_now));
@@ -1123,16 +1131,31 @@ int batch_solve(relu_qp_t h, int B, const float* Xw, const float* Lw, const int*
         if (last_chunk) break;
         RQ_TRY(regroup_slots(h, p, B, check));
         if (check) {
-            int cnt[CNT_WORDS] = {0, 0, 0, 0};
-            // profiling: how long the GPU waits for this host round trip
+            // the host needs the active QP and slot-tile counts of the regroup (they choose
+            // the next chunk's kernel); the copy is waited for through an event, and in the
+            // split form the next chunk's first (accurate) layer is enqueued before the
+            // wait, so that the GPU works during the round trip.  That layer stores only
+            // chunk-local data (c, s_ref, r, the operand), never x, Ax, z or lam', so nothing
+            // depends on it if the host then stops or hands the last QPs to the tail kernel.
+            RQ_CUDA(h, cudaMemcpyAsync(w.cnt_host, w.counters, sizeof(int) * CNT_WORDS, cudaMemcpyDeviceToHost,
+                                       h->stream));
+            RQ_CUDA(h, cudaEventRecord(w.ev_cnt, h->stream));
+            const int nlen = std::min(chunk, max_iter - it);
+            if (bf16 && nlen > 1) {
+                const bool ncheck = (ci > 0 && (it + nlen) % ci == 0) || it + nlen == max_iter;
+                RQ_TRY(run_layers(h, p, nlen, ncheck, active, tiles_now, prof_used, 0, 1));
+                first_done = true;
+            }
+            // profiling: how long the GPU then waits for the host
             const bool gap = h->prof_on && gap_used + 2 <= h->gap_ev.size();
             if (gap) RQ_CUDA(h, cudaEventRecord(h->gap_ev[gap_used], h->stream));
-            RQ_CUDA(h, cudaMemcpyAsync(cnt, w.counters, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
-            RQ_CUDA(h, cudaStreamSynchronize(h->stream));
+            RQ_CUDA(h, cudaEventSynchronize(w.ev_cnt));
             if (gap) {
                 RQ_CUDA(h, cudaEventRecord(h->gap_ev[gap_used + 1], h->stream));
                 gap_used += 2;
             }
+            int cnt[CNT_WORDS];
+            std::memcpy(cnt, w.cnt_host, sizeof(cnt));
             if (cnt[CNT_ERR]) break;     // reported below
             if (cnt[CNT_ACTIVE] == 0) break;
             active = cnt[CNT_ACTIVE];

@@ -114,7 +114,9 @@ __device__ __forceinline__ float ax_row_carry(float ay, float zi, float li, floa
 __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int qp, int ri, int r, float acc) {
     const unsigned f = p.flags;
     const bool refine_only = (f & EPI_REFINE) && !(f & EPI_REBASE);
-    const bool store_state = !refine_only || (f & EPI_LAST);
+    // the split form writes x, Ax, z, lam' only at a chunk's last layer (its other layers,
+    // the accurate first one included, keep chunk-local data: c, s_ref, r and the operand)
+    const bool store_state = !(f & EPI_REFINE) || (f & EPI_LAST);
     const size_t oR = (size_t)qp * p.ldR + r;
     const float* bias = p.BIAS + (size_t)ri * p.cap * p.ldR;
     float t;
@@ -213,6 +215,7 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
                                              const float (&acc)[4], Chunk4& c, const float (&rs)[4]) {
     const unsigned f = p.flags;
     const size_t oR = (size_t)qp * p.ldR + r0;
+    const bool store_state = !(f & EPI_REFINE) || (f & EPI_LAST);   // as layer_elem
     float s_new[4];
     if (r0 < p.n) {
 #pragma unroll
@@ -220,7 +223,7 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
             c.t[k] += acc[k];
             s_new[k] = c.t[k];
         }
-        st4(p.Y + (size_t)qp * p.ldn + r0, c.t);
+        if (store_state) st4(p.Y + (size_t)qp * p.ldn + r0, c.t);
         if (f & EPI_CHECK)
             for (int k = 0; k < 4; ++k) put_check(p, slot, r0 + k, c.t[k]);
     } else {
@@ -239,9 +242,11 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
             c.lm[k] = ln;
             s_new[k] = 2.f * rho_i * zn - ln;
         }
-        st4(p.AY + o, c.t);
-        st4(p.Z + o, c.zz);
-        st4(p.LAM + o, c.lm);
+        if (store_state) {
+            st4(p.AY + o, c.t);
+            st4(p.Z + o, c.zz);
+            st4(p.LAM + o, c.lm);
+        }
         if (f & EPI_REFINE) st4(p.RR + o, rn);
     }
     if (f & EPI_REBASE) {

@@ -127,6 +127,8 @@ struct BatchWork {
     int tail_rpc = 0, tail_cache = 0;      // rows per CTA; 1 = those rows of Wt cached in shared memory
     size_t tail_smem = 0;                  // its dynamic shared memory
     unsigned* chunk_sync = nullptr;        // per slot tile: layer counters of the persistent chunk kernel
+    int* cnt_host = nullptr;               // pinned host copy of the counters read back after a check
+    cudaEvent_t ev_cnt = nullptr;          // recorded after that copy
 };
 
 }  // namespace rq
