@@ -273,6 +273,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "value_is": f"the FP64 oracle's QP solves/s on the host ({per_step} QPs of the batched workload per step)",
             "config": workload_config(per_step, x0_std, "fp64 oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} QPs per step of the batched workload (n=m=800), FP64 NumPy"},
