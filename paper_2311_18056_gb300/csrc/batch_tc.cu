@@ -545,7 +545,12 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
     constexpr int HALVES = OWN >= 32 ? 2 : 1;
     constexpr int PER = OWN / HALVES;
     constexpr bool DRAIN = MODE != MODE_LAYER_REFINED;
-    static_assert(!DRAIN || KS == 1, "drained modes run without a K split");
+    // drained modes with a K split: every epilogue warp drains its share of all BN
+    // columns over this CTA's k range (DW columns from dbeg), sends the partners
+    // their columns' partial sums, and the warps that hold this CTA's own columns
+    // add the KS partials in rank order in place
+    constexpr bool DSPLIT = DRAIN && KS > 1;
+    constexpr int DW = DSPLIT ? BN / HALVES : PER;
     const int q = warp & 3;                         // TMEM lane quadrant of this warp
     const int half = (warp - 2) >> 2;               // which half of this CTA's columns
     const int slot = slot0 + q * 32 + lane;
@@ -561,7 +566,11 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
 #pragma unroll
     for (int pass = 0; pass < 4; ++pass) qq[pass] = __shfl_sync(0xffffffffu, qp, pass * 8 + (lane >> 2));
     const int own0 = rank * OWN;
-    const int cbeg = own0 + half * PER, cend = cbeg + PER;
+    const int dbeg = DSPLIT ? half * DW : own0 + half * PER;   // first drained column of this warp
+    const bool holds_own = !DSPLIT || (own0 >= dbeg && own0 < dbeg + DW);
+    // the columns this warp finalises (none for a split warp that only sends)
+    const int cbeg = DSPLIT ? own0 : own0 + half * PER;
+    const int cend = holds_own ? cbeg + (DSPLIT ? OWN : PER) : cbeg;
     const bool n_aligned = (p.n & 3) == 0;
     auto whole_at = [&](int c0) {
         const int r0 = row0 + c0;
@@ -593,7 +602,7 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
         if (r0 >= p.n) ld4(p.rs + (r0 - p.n), dst);
     };
     // the inputs of the first chunk load while the MMAs run
-    if (whole_at(cbeg)) {
+    if (cend > cbeg && whole_at(cbeg)) {
         load_rs(cbeg, rs);
 #pragma unroll
         for (int pass = 0; pass < 4; ++pass) load_pass(cbeg, pass);
@@ -602,11 +611,11 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
     // polls) for the whole main loop; then every lane observes the
     // completed phase itself
     bool ready = true;
-    // this warp's running sums [lane][PER] (drained modes)
-    float* dsum = DRAIN ? drain + (warp - 2) * 32 * (PER + 1) + lane * (PER + 1) : nullptr;
+    // this warp's running sums [lane][DW] (drained modes)
+    float* dsum = DRAIN ? drain + (warp - 2) * 32 * (DW + 1) + lane * (DW + 1) : nullptr;
     if (DRAIN) {
 #pragma unroll
-        for (int c = 0; c < PER; ++c) dsum[c] = 0.f;
+        for (int c = 0; c < DW; ++c) dsum[c] = 0.f;
         for (int kb = 0; kb < nkb && ready; ++kb) {
             const int b = kb & 1;
             const uint32_t par = (kb >> 1) & 1;
@@ -618,9 +627,9 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
             fence_after();
             const uint32_t tb = tl + (uint32_t)(2 * BN * b);
 #pragma unroll
-            for (int c = 0; c < PER; c += 16) {
+            for (int c = 0; c < DW; c += 16) {
                 float v[16], w[16];
-                tmem_ld16x2(tb + cbeg + c, tb + BN + cbeg + c, v, w);
+                tmem_ld16x2(tb + dbeg + c, tb + BN + dbeg + c, v, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) dsum[c + t] += v[t] + w[t];
             }
@@ -635,7 +644,62 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
         ready = __all_sync(0xffffffffu, ready);
         if (ready) fence_after();
     }
-    if (KS > 1) {
+    if (DSPLIT) {
+        // partial sums of the partners' columns (those this warp drained) go to row
+        // (q * 32 + lane) of buffer j of each partner's receive area
+        const int srow = q * 32 + lane;
+        for (int pk = 0; pk < KS; ++pk) {
+            if (pk == rank) continue;
+            const int pc0 = pk * OWN;
+            if (pc0 < dbeg || pc0 >= dbeg + DW) continue;   // not drained here
+            const int j = rank < pk ? rank : rank - 1;
+            const uint32_t dst = mapa(smem_u32(recv + j * kSlotTile * OWN), (uint32_t)pk);
+            if (ready) {
+#pragma unroll
+                for (int c = 0; c < OWN; c += 4)
+                    st_cluster4(dst + 4u * (uint32_t)recv_off<OWN>(srow, c), dsum[pc0 - dbeg + c],
+                                dsum[pc0 - dbeg + c + 1], dsum[pc0 - dbeg + c + 2], dsum[pc0 - dbeg + c + 3]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa(bar_recv, (uint32_t)pk));
+        }
+        bool got = true;
+        if (holds_own) {
+            if (lane == 0) got = mbar_wait_cluster(bar_recv, par_recv, 64);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got) got = mbar_wait_cluster(bar_recv, par_recv, 0);
+            got = __all_sync(0xffffffffu, got);
+            if (!got && ready && lane == 0) { wait_failed(g.err, WS_EPI_RECV); *s_fail = 1; }
+            if (got && ready) {
+                // own columns: the KS partials added in rank order, written back in place
+#pragma unroll
+                for (int c = 0; c < OWN; c += 4) {
+                    float tot[4];
+#pragma unroll
+                    for (int k = 0; k < KS; ++k) {
+                        float part[4];
+                        if (k == rank) {
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) part[t] = dsum[own0 - dbeg + c + t];
+                        } else {
+                            const float* rb = recv + (k < rank ? k : k - 1) * kSlotTile * OWN;
+                            const float4 o = *reinterpret_cast<const float4*>(rb + recv_off<OWN>(srow, c));
+                            part[0] = o.x;
+                            part[1] = o.y;
+                            part[2] = o.z;
+                            part[3] = o.w;
+                        }
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) tot[t] = k == 0 ? part[t] : tot[t] + part[t];
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) dsum[own0 - dbeg + c + t] = tot[t];
+                }
+            }
+        }
+        ready = ready && got;
+    }
+    if (KS > 1 && !DRAIN) {
         // send every partner its columns of this warp's TMEM lanes: row (q * 32 + lane)
         // of buffer j of the partner's receive area (j = this CTA's index among the
         // partner's senders), columns half * PER ...
@@ -684,12 +748,12 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
                 // lane = 4 * (slot % 8) + row group: rows r0 + cg .. + 3 of the slot
                 // pass * 8 + lane / 4, read from that slot's drained sums
                 __syncwarp();
-                const float* wsum = drain + (warp - 2) * 32 * (PER + 1);
+                const float* wsum = drain + (warp - 2) * 32 * (DW + 1);
 #pragma unroll
                 for (int pass = 0; pass < 4; ++pass) {
                     const int sl = pass * 8 + (lane >> 2);
                     if (qq[pass] < 0) continue;
-                    const float* src = wsum + sl * (PER + 1) + (c0 - cbeg) + cg;
+                    const float* src = wsum + sl * (DW + 1) + (c0 - dbeg) + cg;
                     const float a4[4] = {src[0], src[1], src[2], src[3]};
                     if (MODE == MODE_CHECK1)
                         check1_4(p, slot0 + q * 32 + sl, qq[pass], ri, r0 + cg, a4, mx[pass][0], mx[pass][1],
@@ -702,14 +766,14 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
             float v[16];
             if (DRAIN) {
 #pragma unroll
-                for (int t = 0; t < 16; ++t) v[t] = dsum[c0 - cbeg + t];
+                for (int t = 0; t < 16; ++t) v[t] = dsum[c0 - dbeg + t];
             } else {
                 float w[16];
                 tmem_ld16x2(tl + c0, tl + BN + c0, v, w);
 #pragma unroll
                 for (int t = 0; t < 16; ++t) v[t] += w[t];
             }
-            if (KS > 1) {
+            if (KS > 1 && !DRAIN) {
                 // partial sums of ranks 0 .. KS-1 added in rank order
                 float tot[16];
 #pragma unroll
@@ -742,9 +806,9 @@ __device__ __forceinline__ bool tile_epilogue(const BatchParams& p, const TcArgs
                 const float* base;
                 int stride, off;
                 if (DRAIN) {
-                    base = drain + (warp - 2) * 32 * (PER + 1);
-                    stride = PER + 1;
-                    off = c0 - cbeg;
+                    base = drain + (warp - 2) * 32 * (DW + 1);
+                    stride = DW + 1;
+                    off = c0 - dbeg;
                 } else {
                     float* xb = xpose + (warp - 2) * 32 * 17;       // [32 slots][16 rows]
 #pragma unroll
@@ -885,8 +949,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
             mbar_init(smem_u32(&bars[STAGES + s]), 1);
         }
         mbar_init(smem_u32(&bars[2 * STAGES]), 1);
-        // one arrival per epilogue warp of every partner
-        mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * HALVES);
+        // one arrival per sending epilogue warp of every partner (refined: every warp;
+        // drained with a K split: the 4 warps that drained this CTA's columns)
+        mbar_init(smem_u32(&bars[2 * STAGES + 1]), (KS > 1 ? KS - 1 : 1) * 4 * (DRAIN ? 1 : HALVES));
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&bars[2 * STAGES + 2 + b]), 1);
             mbar_init(smem_u32(&bars[2 * STAGES + 4 + b]), 4 * HALVES);   // one arrival per epilogue warp
@@ -1757,6 +1822,10 @@ int dispatch_3part(relu_qp_t h, int active_tiles, const CUtensorMap& b64, const 
                    const BatchParams& p, const TcArgs& g, const CUtensorMap* a, int tiles) {
     const long long w64 = (long long)ceil_div(g.rows, 64) * active_tiles;
     const long long w96 = (long long)ceil_div(g.rows, 96) * active_tiles;
+    // few active tiles: the k-blocks of every tile split over a cluster of 4 or 2 CTAs
+    // (at least 2 k-blocks each) while the CTAs still fit one wave
+    if (4 * w64 <= h->num_sms && g.num_kb >= 8) return launch_tc<MODE, 64, 4>(h, a, b64, p, g, tiles, false);
+    if (2 * w64 <= h->num_sms && g.num_kb >= 4) return launch_tc<MODE, 64, 2>(h, a, b64, p, g, tiles, false);
     if (w64 > h->num_sms && w96 <= h->num_sms) return launch_tc<MODE, 96, 1>(h, a, b96, p, g, tiles, false);
     return launch_tc<MODE, 64, 1>(h, a, b64, p, g, tiles, false);
 }
