@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kDecideThreads) batch_decide_kernel(BatchParam
         for (int i = threadIdx.x; i < p.m; i += kDecideThreads) {
             const size_t o = (size_t)qp * p.ldm + i;
             const float rho_i = (float)(p.rhod[nri] * (double)p.rs[i]);
-            p.LAM[o] = p.LSTD[o] - rho_i * (p.AY[o] - p.Z[o]);
+            p.LAM[o] = lam_standard(p.LSTD[o], -rho_i, p.AY[o] - p.Z[o]);
         }
     }
     if (threadIdx.x < RW_WORDS) red[threadIdx.x] = 0u;
@@ -433,7 +433,7 @@ __global__ void batch_fill_kernel(BatchParams p, const int* __restrict__ rho_idx
             } else if (k < p.R) {
                 const int i = k - p.n;
                 const size_t o = (size_t)qp * p.ldm + i;
-                v[t] = 2.f * (p.rho[ri] * p.rs[i]) * p.Z[o] - p.LAM[o];
+                v[t] = next_operand(p.rho[ri] * p.rs[i], p.Z[o], p.LAM[o]);
             }
         }
     }

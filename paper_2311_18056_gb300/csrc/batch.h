@@ -100,11 +100,23 @@ __device__ __forceinline__ void put_check(const BatchParams& p, int slot, int co
 // product t and the carried r = (Ax) - z + lam'/rho_i.  Every FP32 path calls
 // this one function (tiled kernels and the convergence tail), so that a QP's
 // iterates do not depend on which kernel runs its layer.
+//
+// The steps that combine a product with a sum are written with explicit
+// roundings (fmaf, __fmul_rn) rather than left to the compiler's contraction
+// choice, which can differ between kernels: every kernel then rounds them
+// alike and produces the same bits.
+// 2 rho_i z - lam': the operand entry of a row of A x
+__device__ __forceinline__ float next_operand(float rho_i, float z, float lam) { return fmaf(2.f * rho_i, z, -lam); }
+// lam' = rho_i r
+__device__ __forceinline__ float lam_layer(float rho_i, float rr) { return __fmul_rn(rho_i, rr); }
+// lam_std = lam' + rho_i (A x - z)
+__device__ __forceinline__ float lam_standard(float lam, float rho_i, float d) { return fmaf(rho_i, d, lam); }
+
 __device__ __forceinline__ void ax_row_update(float t, float rr, float lo, float up, float rho_i, float& zn,
                                               float& ln, float& s_new) {
     zn = fminf(fmaxf(t + rr, lo), up);
-    ln = rho_i * rr;
-    s_new = 2.f * rho_i * zn - ln;
+    ln = lam_layer(rho_i, rr);
+    s_new = next_operand(rho_i, zn, ln);
 }
 
 __device__ __forceinline__ float ax_row_carry(float ay, float zi, float li, float rho_i) {
@@ -144,7 +156,7 @@ __device__ __forceinline__ void layer_elem(const BatchParams& p, int slot, int q
             rr = p.RR[o];
         } else {
             const float ay = p.AY[o], zi = p.Z[o], li = p.LAM[o];
-            if (f & EPI_REBASE) p.SREF[oR] = 2.f * rho_i * zi - li;
+            if (f & EPI_REBASE) p.SREF[oR] = next_operand(rho_i, zi, li);
             rr = ax_row_carry(ay, zi, li, rho_i);
         }
         float zn, ln;
@@ -233,14 +245,14 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
         for (int k = 0; k < 4; ++k) {
             c.t[k] += acc[k];
             const float rho_i = p.rho[ri] * rs[k];
-            if (f & EPI_REBASE) c.sref[k] = 2.f * rho_i * c.zz[k] - c.lm[k];
-            const float rr = c.ay[k] - c.zz[k] + c.lm[k] / rho_i;
+            if (f & EPI_REBASE) c.sref[k] = next_operand(rho_i, c.zz[k], c.lm[k]);
+            const float rr = ax_row_carry(c.ay[k], c.zz[k], c.lm[k], rho_i);
             const float zn = fminf(fmaxf(c.t[k] + rr, c.lo[k]), c.up[k]);
-            const float ln = rho_i * rr;
+            const float ln = lam_layer(rho_i, rr);
             rn[k] = c.t[k] - zn + rr;
             c.zz[k] = zn;
             c.lm[k] = ln;
-            s_new[k] = 2.f * rho_i * zn - ln;
+            s_new[k] = next_operand(rho_i, zn, ln);
         }
         if (store_state) {
             st4(p.AY + o, c.t);
@@ -312,9 +324,9 @@ __device__ __forceinline__ void chunk4_apply(const BatchParams& p, int slot, int
             c.t[k] += acc[k];
             const float rho_i = p.rho[ri] * rs[k];
             zn[k] = fminf(fmaxf(c.t[k] + c.rr[k], c.lo[k]), c.up[k]);
-            ln[k] = rho_i * c.rr[k];
+            ln[k] = lam_layer(rho_i, c.rr[k]);
             rn[k] = c.t[k] - zn[k] + c.rr[k];
-            s_new[k] = 2.f * rho_i * zn[k] - ln[k];
+            s_new[k] = next_operand(rho_i, zn[k], ln[k]);
         }
         st4(p.RR + o, rn);
         if (last) {
@@ -358,7 +370,7 @@ __device__ __forceinline__ void check1_elem(const BatchParams& p, int slot, int 
         const size_t o = (size_t)qp * p.ldm + i;
         const float zi = p.Z[o];
         const float d = acc - zi;
-        const float ls = p.LAM[o] + p.rho[ri] * p.rs[i] * d;
+        const float ls = lam_standard(p.LAM[o], p.rho[ri] * p.rs[i], d);
         p.AY[o] = acc;
         p.LSTD[o] = ls;
         put_check(p, slot, p.n64 + i, ls);
@@ -389,7 +401,7 @@ __device__ __forceinline__ void check1_4(const BatchParams& p, int slot, int qp,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const float d = a[k] - z[k];
-        ls[k] = lm[k] + p.rho[ri] * rs[k] * d;
+        ls[k] = lam_standard(lm[k], p.rho[ri] * rs[k], d);
         const float f = p.rsz ? p.rsz[i0 + k] : 1.f;
         rp = nmax(rp, fabsf(p.rsz ? d * f : d));
         nax = nmax(nax, fabsf(p.rsz ? a[k] * f : a[k]));

@@ -12,12 +12,17 @@
 // kernels or here.  In the BF16 split backend the QPs that reach the tail
 // continue in FP32 (more accurate than the split products).
 //
-// Work split.  A warp takes one row r of the product at a time for every tail
-// QP: lane l computes the 16-wide k-step partials of the steps l, l + 32, ...
-// (coalesced 64-byte loads of the row of Wt, reused for all QPs; the QPs'
-// operand vectors are staged in shared memory with every 16-float step padded
-// to 20 floats, so that the lanes' 16-byte reads spread over the banks), the
-// partials go to shared memory, and lane j adds QP j's partials in k order.
+// Work split of a layer.  CTA b owns a contiguous block of rows of Wt (cached
+// in shared memory when they fit).  The tail QPs' operand vectors are staged
+// in shared memory with every 16-float step padded to 20 floats, so that
+// lanes reading consecutive steps spread over the banks.  A thread takes one
+// step of kRG rows for every QP (each Wt value loaded feeds all QPs of its bank
+// entry, each operand value kRG rows) and writes the step partials to shared
+// memory; then one thread per (row, QP) adds that output's partials in step
+// order and applies the element-wise part of the layer to state it keeps in
+// registers for the whole chunk.  The residual products of the checks, spread
+// over all warps of the grid, use a warp per row: lane l computes the steps
+// l, l + 32, ... and lane j adds QP j's partials in step order.
 // Every barrier wait has a deadline after which the kernel records
 // RELU_QP_ERR_TIMEOUT and returns.
 #include "batch.h"
@@ -29,9 +34,8 @@ namespace rq {
 
 namespace {
 
-constexpr int kTailThreads = 384;   // 12 warps: one row of the layer each
+constexpr int kTailThreads = 384;   // 12 warps
 constexpr int kTailWarps = kTailThreads / 32;
-constexpr int kTailRPW = 4;         // rows per warp whose state stays in registers during a chunk
 
 struct TailArgs {
     BatchParams p;              // state (QP-indexed rows), bank scalars; Sout / CK32 set per phase
@@ -46,8 +50,10 @@ struct TailArgs {
     const int* qlist;           // [nq] QP ids
     int nq, it0, max_iter, ci;
     int rpc;                    // rows of the layer per CTA (contiguous)
+    int pr;                     // rows of the layer product per pass (the step partials of a pass fit the scratch)
+    int scratch;                // floats of the scratch region (step partials, the checks' round partials)
     int wcache;                 // 1: the CTA's Wt rows of one bank entry are cached in shared memory
-    int regs;                   // 1: every warp owns <= kTailRPW rows (their state kept in registers)
+    int regs;                   // 1: one pass, and every (row, QP) output has its own thread (state in registers)
     long long timeout_ns;
 };
 
@@ -178,6 +184,79 @@ __device__ __forceinline__ void warp_rows(const float* __restrict__ opnd, int op
     }
 }
 
+constexpr int kRG = 4;          // rows of one item of the layer product
+
+// The tail QPs grouped by bank entry: QPs of one group read the same rows of Wt.
+struct TailGroups {
+    unsigned mask[kTailMax];
+    int ri[kTailMax];
+    int n;
+    unsigned live;
+};
+
+// Step partials of the layer product for the CTA's local rows [rl0, rl1) and
+// every live tail QP.  Item (g, c) covers rows rl0 + kRG g .. + kRG - 1 and
+// step c (k = 16 c .. 16 c + 15): for each row i and QP j the FMA chain over k
+// in order, starting at 0 (as fp32_tile), so every Wt value loaded feeds all
+// QPs of its group and every staged operand value feeds kRG rows.  The partial
+// goes to pbuf[(j * (rl1 - rl0) + i) * ps + c] (ps odd: the owners' in-order
+// sums read without bank conflicts).  Wt rows of the cached bank entry come
+// from shared memory (padded step layout), the others from global memory.
+__device__ __forceinline__ void layer_partials(const float* __restrict__ opnd, int ops, float* pbuf, int ps, int rl0,
+                                               int rl1, int nsteps, int row_beg, const TailGroups& gr, int cache_ri,
+                                               const float* wc, int wops, const float* const* W, int ldk) {
+    const int npr = rl1 - rl0;
+    const int ngr = (npr + kRG - 1) / kRG;
+    for (int e = threadIdx.x; e < ngr * nsteps; e += blockDim.x) {
+        const int g = e / nsteps, c = e - g * nsteps;
+        const int rb = rl0 + g * kRG;
+        float part[kRG][kTailMax];
+#pragma unroll
+        for (int i = 0; i < kRG; ++i)
+#pragma unroll
+            for (int j = 0; j < kTailMax; ++j) part[i][j] = 0.f;
+        for (int q = 0; q < gr.n; ++q) {
+            const unsigned mask = gr.mask[q];
+            const bool cached = gr.ri[q] == cache_ri;
+            const float* wp[kRG];
+#pragma unroll
+            for (int i = 0; i < kRG; ++i) {
+                const int rl = rb + i < rl1 ? rb + i : rb;
+                wp[i] = cached ? wc + (size_t)rl * wops + c * kStepPad
+                               : W[gr.ri[q]] + (size_t)(row_beg + rl) * ldk + c * kStep;
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                float4 wv[kRG];
+#pragma unroll
+                for (int i = 0; i < kRG; ++i) {
+                    const float4* w4 = reinterpret_cast<const float4*>(wp[i]) + t;
+                    wv[i] = cached ? *w4 : __ldg(w4);
+                }
+#pragma unroll
+                for (int j = 0; j < kTailMax; ++j) {
+                    if (!((mask >> j) & 1u)) continue;
+                    const float4 xv = *reinterpret_cast<const float4*>(opnd + (size_t)j * ops + c * kStepPad + 4 * t);
+#pragma unroll
+                    for (int i = 0; i < kRG; ++i) {
+                        part[i][j] = fmaf(xv.x, wv[i].x, part[i][j]);
+                        part[i][j] = fmaf(xv.y, wv[i].y, part[i][j]);
+                        part[i][j] = fmaf(xv.z, wv[i].z, part[i][j]);
+                        part[i][j] = fmaf(xv.w, wv[i].w, part[i][j]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kRG; ++i) {
+            if (rb + i >= rl1) break;
+#pragma unroll
+            for (int j = 0; j < kTailMax; ++j)
+                if ((gr.live >> j) & 1u) pbuf[((size_t)j * npr + (rb + i - rl0)) * ps + c] = part[i][j];
+        }
+    }
+}
+
 // Operand of the first layer of a chunk, as batch_fill_kernel: s = [x; 2 rho z - lam'].
 __device__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const int* s_ri) {
     const BatchParams& p = a.p;
@@ -192,7 +271,7 @@ __device__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const 
         } else if (k < p.R) {
             const int i = k - p.n;
             const size_t o = (size_t)qp * p.ldm + i;
-            v = 2.f * (p.rho[ri] * p.rs[i]) * p.Z[o] - p.LAM[o];
+            v = next_operand(p.rho[ri] * p.rs[i], p.Z[o], p.LAM[o]);
         }
         S[(size_t)j * p.ldk + k] = v;
     }
@@ -207,12 +286,18 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
     const int nsteps = (p.ldk > p.ldkc ? p.ldk : p.ldkc) / kStep;
     const int ops = nsteps * kStepPad;                       // staged floats per QP
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* pb = tsm + (size_t)kTailMax * ops + (size_t)warp * kRB * kTailMax * kPbs;
+    // scratch: the layer's step partials, or each warp's round partials in the checks
+    float* pbuf = tsm + (size_t)kTailMax * ops;
+    float* pb = pbuf + (size_t)warp * kRB * kTailMax * kPbs;
     // this CTA's rows of the layer, and (a.wcache) their Wt rows of one bank entry in
     // shared memory, in the padded step layout
     const int row_beg = blockIdx.x * a.rpc, row_end = min(p.R, row_beg + a.rpc);
-    const int wops = (p.ldk / kStep) * kStepPad;             // cached floats per row
-    float* wc = tsm + (size_t)kTailMax * ops + (size_t)(kTailThreads / 32) * kRB * kTailMax * kPbs;
+    const int nr = max(0, row_end - row_beg);
+    const int lsteps = p.ldk / kStep;                        // k steps of the layer product
+    const int ps = lsteps | 1;                               // stride of an output's step partials
+    const int wops = lsteps * kStepPad;                      // cached floats per row
+    float* wc = pbuf + a.scratch;
+    __shared__ TailGroups s_gr;
     int cache_ri = -1;
     const int gwarp = blockIdx.x * (kTailThreads / 32) + warp, nwarps = gridDim.x * (kTailThreads / 32);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
@@ -251,87 +336,95 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                 cache_ri = ri0;
             }
         }
-        // the state of this warp's rows for lane j's QP (bias of its bank entry, and for
-        // rows of A x the carried A x, z, lam', l, u, rho_i) stays in registers for the
-        // chunk: loaded here, written back at the chunk's last layer (the checks, the
-        // decision and the next chunk's fill read it from memory)
-        const bool live_lane = lane < nq && s_live[lane];
-        const int qp_l = live_lane ? a.qlist[lane] : 0, ri_l = live_lane ? s_ri[lane] : 0;
-        float rb[kTailRPW], ray[kTailRPW], rz[kTailRPW], rlam[kTailRPW], rlo[kTailRPW], rup[kTailRPW],
-            rrho[kTailRPW];
-        if (a.regs && live_lane) {
-#pragma unroll
-            for (int w = 0; w < kTailRPW; ++w) {
-                const int r = row_beg + warp + kTailWarps * w;
-                rb[w] = ray[w] = rz[w] = rlam[w] = rlo[w] = rup[w] = rrho[w] = 0.f;
-                if (r >= row_end) continue;
-                rb[w] = p.BIAS[((size_t)ri_l * p.cap + qp_l) * p.ldR + r];
-                if (r >= p.n) {
-                    const int i = r - p.n;
-                    const size_t o = (size_t)qp_l * p.ldm + i;
-                    ray[w] = p.AY[o];
-                    rz[w] = p.Z[o];
-                    rlam[w] = p.LAM[o];
-                    rlo[w] = p.L[o];
-                    rup[w] = p.U[o];
-                    rrho[w] = p.rho[ri_l] * p.rs[i];
+        // the QPs grouped by bank entry for the layer product
+        if (threadIdx.x == 0) {
+            TailGroups g{};
+            for (int j = 0; j < nq; ++j) {
+                if (!s_live[j]) continue;
+                g.live |= 1u << j;
+                int q = 0;
+                while (q < g.n && g.ri[q] != s_ri[j]) ++q;
+                if (q == g.n) {
+                    g.ri[q] = s_ri[j];
+                    g.mask[q] = 0u;
+                    ++g.n;
                 }
+                g.mask[q] |= 1u << j;
+            }
+            s_gr = g;
+        }
+        __syncthreads();
+        const TailGroups gr = s_gr;
+        // a.regs: thread o owns output (row row_beg + o % nr, QP o / nr); its state (bias of
+        // the QP's bank entry, and for rows of A x the carried A x, z, lam', l, u, rho_i)
+        // stays in registers for the chunk: loaded here, written back at the chunk's last
+        // layer (the checks, the decision and the next chunk's fill read it from memory)
+        const int oj = nr > 0 ? (int)threadIdx.x / nr : kTailMax, orl = nr > 0 ? (int)threadIdx.x % nr : 0;
+        const bool own = a.regs && oj < nq && s_live[oj];
+        const int o_qp = own ? a.qlist[oj] : 0, o_ri = own ? s_ri[oj] : 0, o_r = row_beg + orl;
+        float rb = 0.f, ray = 0.f, rz = 0.f, rlam = 0.f, rlo = 0.f, rup = 0.f, rrho = 0.f;
+        if (own) {
+            rb = p.BIAS[((size_t)o_ri * p.cap + o_qp) * p.ldR + o_r];
+            if (o_r >= p.n) {
+                const size_t o = (size_t)o_qp * p.ldm + (o_r - p.n);
+                ray = p.AY[o];
+                rz = p.Z[o];
+                rlam = p.LAM[o];
+                rlo = p.L[o];
+                rup = p.U[o];
+                rrho = p.rho[o_ri] * p.rs[o_r - p.n];
             }
         }
-        auto wrow = [&](int j, int r) {
-            return s_ri[j] == cache_ri ? WRowRef{wc + (size_t)(r - row_beg) * wops, kStepPad}
-                                       : WRowRef{a.W[s_ri[j]] + (size_t)r * p.ldk, kStep};
-        };
         for (int jl = 0; jl < len; ++jl) {
             const float* Sc = a.S + (size_t)cur * kTailMax * p.ldk;
             p.Sout = a.S + (size_t)(cur ^ 1) * kTailMax * p.ldk;
             p.CK32 = a.CKB;
             p.CK = nullptr;
             p.flags = jl == len - 1 ? (EPI_LAST | (check ? EPI_CHECK : 0u)) : 0u;
+            const bool last = jl == len - 1;
             stage_rows(tsm, ops, Sc, p.ldk, 0, p.ldk, nq, s_live);
             __syncthreads();
-            if (a.regs) {
-                const bool last = jl == len - 1;
-#pragma unroll
-                for (int w = 0; w < kTailRPW; ++w) {
-                    const int r = row_beg + warp + kTailWarps * w;
-                    if (r >= row_end) break;
-                    float acc[kRB];
-                    warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r, row_end, wrow, acc);
-                    if (!live_lane) continue;
-                    // the FP32 layer of layer_elem on register state
-                    const float t = acc[0] + rb[w];
+            for (int rl0 = 0; rl0 < nr; rl0 += a.pr) {
+                const int rl1 = min(nr, rl0 + a.pr), npr = rl1 - rl0;
+                if (rl0 > 0) __syncthreads();   // the previous pass's sums have read pbuf
+                layer_partials(tsm, ops, pbuf, ps, rl0, rl1, lsteps, row_beg, gr, cache_ri, wc, wops, a.W, p.ldk);
+                __syncthreads();
+                // every output's partials added in step order (as fp32_tile), then the layer's
+                // element-wise part
+                for (int o = threadIdx.x; o < kTailMax * npr; o += blockDim.x) {
+                    const int j = o / npr, r = row_beg + rl0 + (o - j * npr);
+                    if (!((gr.live >> j) & 1u)) continue;
+                    const float* q = pbuf + (size_t)o * ps;
+                    float acc = 0.f;
+                    for (int c = 0; c < lsteps; ++c) acc += q[c];
+                    if (!a.regs) {
+                        layer_elem(p, j, a.qlist[j], s_ri[j], r, acc);
+                        continue;
+                    }
+                    // the FP32 layer of layer_elem on register state (o == threadIdx.x here)
+                    const float t = acc + rb;
                     float s_new;
                     if (r < p.n) {
                         s_new = t;
                         if (last) {
-                            p.Y[(size_t)qp_l * p.ldn + r] = t;
-                            if (check) put_check(p, lane, r, t);
+                            p.Y[(size_t)o_qp * p.ldn + r] = t;
+                            if (check) put_check(p, j, r, t);
                         }
                     } else {
                         float zn, ln;
-                        const float rr = ax_row_carry(ray[w], rz[w], rlam[w], rrho[w]);
-                        ax_row_update(t, rr, rlo[w], rup[w], rrho[w], zn, ln, s_new);
-                        ray[w] = t;
-                        rz[w] = zn;
-                        rlam[w] = ln;
+                        const float rr = ax_row_carry(ray, rz, rlam, rrho);
+                        ax_row_update(t, rr, rlo, rup, rrho, zn, ln, s_new);
+                        ray = t;
+                        rz = zn;
+                        rlam = ln;
                         if (last) {
-                            const size_t o = (size_t)qp_l * p.ldm + (r - p.n);
-                            p.AY[o] = t;
-                            p.Z[o] = zn;
-                            p.LAM[o] = ln;
+                            const size_t oo = (size_t)o_qp * p.ldm + (r - p.n);
+                            p.AY[oo] = t;
+                            p.Z[oo] = zn;
+                            p.LAM[oo] = ln;
                         }
                     }
-                    if (!last) p.Sout[(size_t)lane * p.ldk + r] = s_new;
-                }
-            } else {
-                for (int r0 = row_beg + warp * kRB; r0 < row_end; r0 += kTailWarps * kRB) {
-                    float acc[kRB];
-                    warp_rows(tsm, ops, pb, nq, s_live, 0, p.ldk / kStep, r0, row_end, wrow, acc);
-                    if (live_lane)
-#pragma unroll
-                        for (int i = 0; i < kRB; ++i)
-                            if (r0 + i < row_end) layer_elem(p, lane, qp_l, ri_l, r0 + i, acc[i]);
+                    if (!last) p.Sout[(size_t)j * p.ldk + r] = s_new;
                 }
             }
             cur ^= 1;
@@ -444,7 +537,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                 } else if (s_act[j] == 2 && e < p.m) {
                     const size_t oo = (size_t)qp * p.ldm + e;
                     const float rho_i = (float)(p.rhod[s_ri[j]] * (double)p.rs[e]);
-                    p.LAM[oo] = p.LSTD[oo] - rho_i * (p.AY[oo] - p.Z[oo]);
+                    p.LAM[oo] = lam_standard(p.LSTD[oo], -rho_i, p.AY[oo] - p.Z[oo]);
                 }
             }
             if (!s_any) return;
@@ -470,11 +563,18 @@ __global__ void tail_list_kernel(int B, const int* __restrict__ status, int* lis
     }
 }
 
-// staged operands [kTailMax][steps][kStepPad] + per-warp round partials [8][kRB][kTailMax][kPbs]
-// (+ the cached Wt rows [rows][ldk steps][kStepPad])
-size_t tail_smem(const BatchWork& w, int cached_rows) {
+// floats of the scratch region: the step partials of `pass_rows` rows of the layer
+// product [kTailMax][pass_rows][ps], or the checks' per-warp round partials
+size_t tail_scratch(const BatchWork& w, int pass_rows) {
+    const size_t ps = (size_t)((w.ldk / kStep) | 1);
+    return std::max((size_t)kTailWarps * kRB * kTailMax * kPbs, (size_t)pass_rows * kTailMax * ps);
+}
+
+// staged operands [kTailMax][steps][kStepPad] + scratch (+ the cached Wt rows
+// [rows][ldk steps][kStepPad])
+size_t tail_smem(const BatchWork& w, int pass_rows, int cached_rows) {
     const size_t steps = (size_t)std::max(w.ldk, w.ldkc) / kStep;
-    return ((size_t)kTailMax * steps * kStepPad + (size_t)(kTailThreads / 32) * kRB * kTailMax * kPbs +
+    return ((size_t)kTailMax * steps * kStepPad + tail_scratch(w, pass_rows) +
             (size_t)cached_rows * (w.ldk / kStep) * kStepPad) *
            sizeof(float);
 }
@@ -492,22 +592,30 @@ int batch_tail_alloc(relu_qp_t h) {
     RQ_CUDA(h, cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
     w.tail_grid = 0;
     // one CTA per SM and (while the SMs suffice) one row of the layer per warp; the CTA's
-    // rows of Wt cached in shared memory when they fit (every CTA co-resident: grid barrier)
-    constexpr int kWarps = kTailThreads / 32;
-    const int grid = std::min(h->num_sms, ceil_div(h->R, kWarps));
+    // rows of Wt cached in shared memory when they fit (every CTA co-resident: grid
+    // barrier), and the step partials of all its rows in one pass when they fit
+    const int grid = std::min(h->num_sms, ceil_div(h->R, kTailWarps));
     const int rpc = ceil_div(h->R, grid);
     for (int cache = 1; cache >= 0; --cache) {
-        const size_t smem = tail_smem(w, cache ? rpc : 0);
-        if (smem + 1024 > (size_t)smem_max) continue;
-        RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads, smem));
-        if (per_sm < 1) continue;
-        w.tail_grid = grid;
-        w.tail_rpc = rpc;
-        w.tail_cache = cache;
-        w.tail_smem = smem;
-        return RELU_QP_OK;
+        for (int pr = rpc;; pr = std::max(kRG, pr / 2)) {
+            const size_t smem = tail_smem(w, pr, cache ? rpc : 0);
+            if (smem + 1024 <= (size_t)smem_max) {
+                RQ_CUDA(h, cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)smem));
+                int per_sm = 0;
+                RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_tail_kernel, kTailThreads,
+                                                                         smem));
+                if (per_sm >= 1) {
+                    w.tail_grid = grid;
+                    w.tail_rpc = rpc;
+                    w.tail_pr = pr;
+                    w.tail_cache = cache;
+                    w.tail_smem = smem;
+                    return RELU_QP_OK;
+                }
+            }
+            if (pr <= kRG) break;
+        }
     }
     return RELU_QP_OK;   // problem too large for the staged operands: no tail kernel
 }
@@ -535,8 +643,10 @@ int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, i
     a.max_iter = max_iter;
     a.ci = h->opts.check_interval;
     a.rpc = w.tail_rpc;
+    a.pr = w.tail_pr;
+    a.scratch = (int)tail_scratch(w, w.tail_pr);
     a.wcache = w.tail_cache;
-    a.regs = w.tail_rpc <= kTailWarps * kTailRPW ? 1 : 0;
+    a.regs = w.tail_pr >= w.tail_rpc && w.tail_rpc * kTailMax <= kTailThreads ? 1 : 0;
     a.timeout_ns = 2000000000LL;
     void* args[] = {&a};
     RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)batch_tail_kernel, dim3(w.tail_grid), dim3(kTailThreads), args,

@@ -125,6 +125,7 @@ struct BatchWork {
     int* TLIST = nullptr;
     int tail_grid = 0;                     // CTAs of its cooperative launch (0: unavailable)
     int tail_rpc = 0, tail_cache = 0;      // rows per CTA; 1 = those rows of Wt cached in shared memory
+    int tail_pr = 0;                       // rows of the layer product per pass of the tail kernel
     size_t tail_smem = 0;                  // its dynamic shared memory
     unsigned* chunk_sync = nullptr;        // per slot tile: layer counters of the persistent chunk kernel
     int* cnt_host = nullptr;               // pinned host copy of the counters read back after a check

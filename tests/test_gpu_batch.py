@@ -261,3 +261,61 @@ def test_one_tile_resident_weight_kernel(rq, B):
     assert np.all(conv["status"] == rq.SOLVED)
     check_converged(rq, pq, Q, L, U, conv, range(0, B, 9))
     print(f"B={B}: resident-weight chunk launches {used}, iterate error {worst:.2e}")
+
+
+@pytest.mark.parametrize("case", ["mpc_n800", "random_n2000"])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
+def test_tail_kernel_iterates(rq, prec, case):
+    """Fixed-rho layers through the convergence-tail kernel.  Five QPs, a check
+    every 25 layers with an eps no iterate reaches and adaptive rho off: after
+    the first check at most 8 QPs are left, so layers 26..100 run in the tail
+    kernel.  The same five QPs inside a batch of nine (more than 8 stay active,
+    so the tail never starts) run all 100 layers in the tiled kernels.  FP32:
+    the tail repeats the tiled kernels' arithmetic (products in the same
+    summation order, the element-wise steps with explicit roundings), so the
+    two give the same bits.  Both match the oracle's fixed-rho iterates: 1e-5
+    FP32 and 1e-4 BF16 split on the MPC problem; on the random QP the equality
+    rows (rho scaled by 1e3) amplify rounding over 100 layers, and the bound
+    there is 2e-4.
+    n = m = 800 runs the tail's one-pass form (all step partials of a CTA's rows
+    at once, every output's state in registers); the random QP with n = 2000
+    and m = 1000 (3000 rows, 20 per CTA) adds up the step partials in two
+    passes of 10 rows, and its Wt rows do not fit shared memory."""
+    from workloads import random_qp
+    B, B_tiled = 5, 9
+    if case == "mpc_n800":
+        pq, X0, Q, L, U = mpc_batch("batched", B_tiled)
+        P, A = pq.P, pq.A
+        tol = TOL_ITER[prec]
+    else:
+        P, q, A, l, u = random_qp.random_dense_qp(0, 2000)
+        rng = np.random.default_rng(11)
+        Q = q[None, :] + rng.standard_normal((B_tiled, q.size))
+        L = np.repeat(l[None, :], B_tiled, axis=0)
+        U = np.repeat(u[None, :], B_tiled, axis=0)
+        tol = 2e-4
+    n, m = P.shape[0], A.shape[0]
+    outs = []
+    for nb in (B, B_tiled):
+        s = rq.ReluQP(P, A, L[0], U[0], q=Q[0], sigma=SIGMA, rho_bank=BANK, check_interval=25,
+                      adaptive_rho=False, rho0=BANK[0], max_batch=nb, precision=prec)
+        s.update_batch(Q[:nb], L[:nb], U[:nb])
+        outs.append(s.solve_batch(eps_abs=1e-12, eps_rel=0.0, max_iter=100))
+        s.close()
+    tail, tiled = outs
+    for out in outs:
+        assert np.all(out["iters"] == 100) and np.all(out["status"] == rq.MAX_ITER)
+    if prec == 0:
+        for k in ("x", "z", "lam"):
+            assert np.array_equal(tail[k], tiled[k][:B]), k
+    worst = {"tail": 0.0, "tiled": 0.0}
+    for b in (0, B - 1):
+        v = O.layer_iterates(P, Q[b], A, L[b], U[b], SIGMA, BANK[0], 100)[-1]
+        x, z, lam_l = v[:n], v[n:n + m], v[n + m:]
+        lam = O.std_multiplier(A, x, z, lam_l, O.rho_vector(L[b], U[b], BANK[0]))
+        ref = np.concatenate([x, z, lam])
+        for name, out in (("tail", tail), ("tiled", tiled)):
+            got = np.concatenate([out["x"][b], out["z"][b], out["lam"][b]]).astype(np.float64)
+            worst[name] = max(worst[name], rel(got, ref))
+    print(f"{case} prec={prec}: error vs oracle {worst}")
+    assert worst["tail"] <= tol and worst["tiled"] <= tol, worst
