@@ -45,7 +45,7 @@ struct TailArgs {
     float* S;                   // operand double buffer [2][kTailMax][ldk]
     float* CKB;                 // check operand [kTailMax][ldkc]
     unsigned* red;              // [3][kTailMax][RW_WORDS] reduction words, rotated per check
-    unsigned* bar;              // grid barrier [count, generation]
+    unsigned* bar;              // grid barrier: arrival count of the launch (+ pad word)
     int* err;                   // error word
     const int* qlist;           // [nq] QP ids
     int nq, it0, max_iter, ci;
@@ -58,7 +58,7 @@ struct TailArgs {
 };
 
 // Grid-wide barrier over all CTAs of the cooperative launch (grid_sync.h).
-__device__ __forceinline__ bool tail_barrier(const TailArgs& a, int* s_ok) {
+__device__ __forceinline__ bool tail_barrier(const TailArgs& a, GridSyncState* s_ok) {
     return grid_sync(a.bar, a.err, a.timeout_ns, s_ok);
 }
 
@@ -279,7 +279,9 @@ __device__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const 
 
 __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a) {
     extern __shared__ __align__(16) float tsm[];
-    __shared__ int s_ok, s_live[kTailMax], s_ri[kTailMax], s_act[kTailMax], s_nri[kTailMax], s_any;
+    __shared__ GridSyncState s_ok;
+    __shared__ int s_live[kTailMax], s_ri[kTailMax], s_act[kTailMax], s_nri[kTailMax], s_any;
+    grid_sync_init(&s_ok);
     __shared__ unsigned s_red[kTailMax][RW_WORDS];
     BatchParams p = a.p;
     const int nq = a.nq;

@@ -66,7 +66,7 @@ struct SingleWork {
     float* xin = nullptr;       // warm-start x (FP32)
     float* lin = nullptr;       // warm-start lam (FP32)
     unsigned* red = nullptr;    // 3 slots x 8 reduction words
-    unsigned* bar = nullptr;    // grid barrier [count, generation]
+    unsigned* bar = nullptr;    // grid barrier: arrival count of the launch (+ pad word)
     int* out_i = nullptr;       // status, iters, rho_index, switches, err
     float* out_f = nullptr;     // r_prim, r_dual
     int grid = 0;               // CTAs of the cooperative launch (autotuned)
@@ -83,7 +83,7 @@ struct SingleWork64 {
     double *c = nullptr, *sref = nullptr;   // refined form: anchor layer product and its operand
     float* d32 = nullptr;                   // refined form: FP32 increment of the next layer (ldw)
     unsigned long long* red = nullptr;   // 3 slots x 8 reduction words (bits of non-negative doubles)
-    unsigned* bar = nullptr;             // grid barrier [count, generation]
+    unsigned* bar = nullptr;             // grid barrier: arrival count of the launch (+ pad word)
     int* out_i = nullptr;                // status, iters, rho_index, switches, err
     double* out_f = nullptr;             // r_prim, r_dual
     int grid = 0;

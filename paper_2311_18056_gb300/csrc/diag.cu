@@ -26,17 +26,16 @@ namespace {
 // `expected` arrivals: expected = grid passes; expected = grid + 1 makes every
 // CTA wait for an arrival that never comes, until the deadline.
 __global__ void diag_grid_kernel(unsigned* bar, int* err, unsigned expected, long long timeout_ns) {
-    __shared__ int s_ok;
+    __shared__ GridSyncState s_ok;
+    grid_sync_init(&s_ok);
     grid_sync_n(bar, err, timeout_ns, &s_ok, expected);
 }
 
 // Host policy of barrier_arrive_wait: C++ atomics on the same words.
 struct HostOps {
-    unsigned load_relaxed(const unsigned* p) { return __atomic_load_n(p, __ATOMIC_RELAXED); }
-    unsigned fetch_add_acq_rel(unsigned* p, unsigned v) { return __atomic_fetch_add(p, v, __ATOMIC_ACQ_REL); }
-    void store_relaxed(unsigned* p, unsigned v) { __atomic_store_n(p, v, __ATOMIC_RELAXED); }
-    void store_release(unsigned* p, unsigned v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+    void add_release(unsigned* p, unsigned v) { __atomic_fetch_add(p, v, __ATOMIC_RELEASE); }
     unsigned load_acquire(const unsigned* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+    int load_error(const int* err) { return __atomic_load_n(err, __ATOMIC_RELAXED); }
     long long now_ns() {
         return std::chrono::duration_cast<std::chrono::nanoseconds>(
                    std::chrono::steady_clock::now().time_since_epoch())
@@ -44,7 +43,6 @@ struct HostOps {
     }
     void relax() { std::this_thread::yield(); }
     void set_error(int* err, int code) { __atomic_store_n(err, code, __ATOMIC_SEQ_CST); }
-    int load_error(const int* err) { return __atomic_load_n(err, __ATOMIC_SEQ_CST); }
 };
 
 }  // namespace
@@ -65,7 +63,7 @@ int relu_qp_diag_device_wait(int kind, long long timeout_ns, int* status, double
         cudaGetLastError();
         return RELU_QP_ERR_CUDA;
     }
-    int* words = nullptr;   // [0] error, [1] site, [2] counter, [3] pad, [4..5] barrier
+    int* words = nullptr;   // [0] error, [1] site, [2] counter, [3] pad, [4] barrier arrivals, [5] pad
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = RELU_QP_OK;
     if (cudaMalloc(&words, 8 * sizeof(int)) != cudaSuccess) {
@@ -125,8 +123,9 @@ int relu_qp_diag_host_barrier(int threads, int extra, int rounds, long long time
     for (int t = 0; t < threads; ++t)
         pool.emplace_back([&]() {
             rq::HostOps o;
+            unsigned epoch = 0;
             for (int r = 0; r < rounds; ++r) {
-                if (!rq::barrier_arrive_wait(o, bar, &err, expected, timeout_ns)) {
+                if (!rq::barrier_arrive_wait(o, bar, &err, expected, epoch, timeout_ns)) {
                     n_timeout.fetch_add(1);
                     return;
                 }

@@ -56,7 +56,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Grid-wide barrier over all CTAs of the cooperative launch (grid_sync.h).
-__device__ __forceinline__ bool grid_barrier(const SP& p, int* s_ok) {
+__device__ __forceinline__ bool grid_barrier(const SP& p, GridSyncState* s_ok) {
     return grid_sync(p.bar, p.out_i + OUT_ERR, p.timeout_ns, s_ok);
 }
 
@@ -122,7 +122,8 @@ __device__ __forceinline__ float red_get(const unsigned* slot, int word) {
 
 __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
     extern __shared__ __align__(16) float smem[];
-    __shared__ int s_ok;
+    __shared__ GridSyncState s_ok;
+    grid_sync_init(&s_ok);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n, m = p.m, R = p.R;
     const int row0 = blockIdx.x * p.rows_per_cta;

@@ -70,7 +70,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Grid-wide barrier over all CTAs of the cooperative launch (grid_sync.h).
-__device__ __forceinline__ bool grid_barrier(const SP64& p, int* s_ok) {
+__device__ __forceinline__ bool grid_barrier(const SP64& p, GridSyncState* s_ok) {
     return grid_sync(p.bar, p.out_i + OUT_ERR, p.timeout_ns, s_ok);
 }
 
@@ -129,7 +129,8 @@ __device__ __forceinline__ double red_get(const unsigned long long* slot, int wo
 template <bool REFINED>
 __global__ void __launch_bounds__(kThreads, 1) single64_kernel(SP64 p) {
     extern __shared__ __align__(16) double sv[];   // R doubles (refined layers: ldw floats of the increment)
-    __shared__ int s_ok;
+    __shared__ GridSyncState s_ok;
+    grid_sync_init(&s_ok);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n, m = p.m, R = p.R;
     const int row0 = blockIdx.x * p.rows_per_cta;
