@@ -398,7 +398,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                     if (!((gr.live >> j) & 1u)) continue;
                     const float* q = pbuf + (size_t)o * ps;
                     float acc = 0.f;
-                    for (int c = 0; c < lsteps; ++c) acc += q[c];
+                    int c = 0;
+                    for (; c + 20 <= lsteps; c += 20) {
+                        // loads first, then the additions in step order
+                        float v[20];
+#pragma unroll
+                        for (int u = 0; u < 20; ++u) v[u] = q[c + u];
+#pragma unroll
+                        for (int u = 0; u < 20; ++u) acc += v[u];
+                    }
+                    for (; c < lsteps; ++c) acc += q[c];
                     if (!a.regs) {
                         layer_elem(p, j, a.qlist[j], s_ri[j], r, acc);
                         continue;
