@@ -13,16 +13,20 @@
 // continue in FP32 (more accurate than the split products).
 //
 // Work split of a layer.  CTA b owns a contiguous block of rows of Wt (cached
-// in shared memory when they fit).  The tail QPs' operand vectors are staged
-// in shared memory with every 16-float step padded to 20 floats, so that
-// lanes reading consecutive steps spread over the banks.  A thread takes one
-// step of kRG rows for every QP (each Wt value loaded feeds all QPs of its bank
-// entry, each operand value kRG rows) and writes the step partials to shared
-// memory; then one thread per (row, QP) adds that output's partials in step
-// order and applies the element-wise part of the layer to state it keeps in
-// registers for the whole chunk.  The residual products of the checks, spread
-// over all warps of the grid, use a warp per row: lane l computes the steps
-// l, l + 32, ... and lane j adds QP j's partials in step order.
+// in shared memory when they fit).  At the start of a chunk the live tail QPs
+// are listed in compact slots, grouped by bank entry, and every layer stages
+// only their operand vectors in shared memory, with every 16-float step padded
+// to 20 floats so that lanes reading consecutive steps spread over the banks.
+// A thread takes one step of kRG rows for all QPs of a group (code specialised
+// on the group's size: each Wt value loaded feeds every QP of the group, each
+// operand value kRG rows) and writes the step partials to shared memory; then
+// one thread per (row, QP) adds that output's partials in step order and
+// applies the element-wise part of the layer to state it keeps in registers
+// for the whole chunk.  Nothing the kernel indexes at run time lives in local
+// memory, which would miss in the small L1 left beside the staged data.  The
+// residual products of the checks, spread over all warps of the grid, use a
+// warp per row: lane l computes the steps l, l + 32, ... and lane j adds QP j's
+// partials in step order.
 // Every barrier wait has a deadline after which the kernel records
 // RELU_QP_ERR_TIMEOUT and returns.
 #include "batch.h"
@@ -38,7 +42,7 @@ constexpr int kTailThreads = 384;   // 12 warps
 constexpr int kTailWarps = kTailThreads / 32;
 
 struct TailArgs {
-    BatchParams p;              // state (QP-indexed rows), bank scalars; Sout / CK32 set per phase
+    BatchParams p;              // state (QP-indexed rows), bank scalars, CK32 = CKB (Sout, flags unused)
     DecideArgs d;
     const float* W[RQ_MAX_RHO];  // FP32 Wt of every bank entry, rows of ldk floats
     const float* Wc;            // FP32 check matrix [[P, A^T], [A, 0]], rows of ldkc floats
@@ -186,64 +190,74 @@ __device__ __forceinline__ void warp_rows(const float* __restrict__ opnd, int op
 
 constexpr int kRG = 4;          // rows of one item of the layer product
 
-// The tail QPs grouped by bank entry: QPs of one group read the same rows of Wt.
-struct TailGroups {
-    unsigned mask[kTailMax];
+// The live tail QPs of a chunk, compacted and grouped by bank entry: compact
+// slot k holds tail slot j[k]; group g (QPs reading the same rows of Wt) is
+// compact slots [g0[g], g0[g + 1]) with bank entry ri[g].
+struct TailList {
+    int nl;
+    int j[kTailMax];
+    int ng;
+    int g0[kTailMax + 1];
     int ri[kTailMax];
-    int n;
-    unsigned live;
 };
 
+// Copy the operand rows of the live tail QPs (floats [0, cols), a multiple of
+// 16, of row j[k] of `src`, row stride ld) into compact slots k of the padded
+// shared layout [k][step][kStepPad] (ops floats per slot).  As stage_rows.
+__device__ __forceinline__ void stage_list(float* sm, int ops, const float* src, int ld, int cols, const TailList& L) {
+    const int c4 = cols >> 2;
+    for (int e = threadIdx.x; e < L.nl * c4; e += blockDim.x) {
+        const int k = e / c4, q = e - k * c4;
+        const uint32_t d = static_cast<uint32_t>(
+            __cvta_generic_to_shared(sm + (size_t)k * ops + (q >> 2) * kStepPad + (q & 3) * 4));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src + (size_t)L.j[k] * ld + 4 * q)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
 // Step partials of the layer product for the CTA's local rows [rl0, rl1) and
-// every live tail QP.  Item (g, c) covers rows rl0 + kRG g .. + kRG - 1 and
-// step c (k = 16 c .. 16 c + 15): for each row i and QP j the FMA chain over k
-// in order, starting at 0 (as fp32_tile), so every Wt value loaded feeds all
-// QPs of its group and every staged operand value feeds kRG rows.  The partial
-// goes to pbuf[(j * (rl1 - rl0) + i) * ps + c] (ps odd: the owners' in-order
-// sums read without bank conflicts).  Wt rows of the cached bank entry come
-// from shared memory (padded step layout), the others from global memory.
-__device__ __forceinline__ void layer_partials(const float* __restrict__ opnd, int ops, float* pbuf, int ps, int rl0,
-                                               int rl1, int nsteps, int row_beg, const TailGroups& gr, int cache_ri,
-                                               const float* wc, int wops, const float* const* W, int ldk) {
+// the NL compact slots s0 .. s0 + NL - 1 of one group.  Item (g, c) covers rows
+// rl0 + kRG g .. + kRG - 1 and step c (k = 16 c .. 16 c + 15): for each row i
+// and slot the FMA chain over k in order, starting at 0 (as fp32_tile), so
+// every Wt value loaded feeds the NL QPs and every staged operand value kRG
+// rows; NL is a template parameter, so the item's code has no per-QP tests.
+// The partial goes to pbuf[((s0 + k) * (rl1 - rl0) + i) * ps + c] (ps odd: the
+// owners' in-order sums read without bank conflicts).  Row rl of Wt starts at
+// w0 + rl * wr and step c of it at + c * ws: the cached rows in shared memory
+// (padded step layout) or the bank entry's rows in global memory, read with
+// generic loads.
+template <int NL>
+__device__ __forceinline__ void group_partials(const float* __restrict__ opnd, int ops, float* pbuf, int ps, int rl0,
+                                               int rl1, int nsteps, int s0, const float* w0, size_t wr, int ws) {
     const int npr = rl1 - rl0;
     const int ngr = (npr + kRG - 1) / kRG;
     for (int e = threadIdx.x; e < ngr * nsteps; e += blockDim.x) {
         const int g = e / nsteps, c = e - g * nsteps;
         const int rb = rl0 + g * kRG;
-        float part[kRG][kTailMax];
+        float part[kRG][NL];
 #pragma unroll
         for (int i = 0; i < kRG; ++i)
 #pragma unroll
-            for (int j = 0; j < kTailMax; ++j) part[i][j] = 0.f;
-        for (int q = 0; q < gr.n; ++q) {
-            const unsigned mask = gr.mask[q];
-            const bool cached = gr.ri[q] == cache_ri;
-            const float* wp[kRG];
+            for (int k = 0; k < NL; ++k) part[i][k] = 0.f;
+        const float* wp[kRG];
 #pragma unroll
-            for (int i = 0; i < kRG; ++i) {
-                const int rl = rb + i < rl1 ? rb + i : rb;
-                wp[i] = cached ? wc + (size_t)rl * wops + c * kStepPad
-                               : W[gr.ri[q]] + (size_t)(row_beg + rl) * ldk + c * kStep;
-            }
+        for (int i = 0; i < kRG; ++i) wp[i] = w0 + (size_t)(rb + i < rl1 ? rb + i : rb) * wr + (size_t)c * ws;
+        const float* xs = opnd + (size_t)s0 * ops + c * kStepPad;
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                float4 wv[kRG];
+        for (int t = 0; t < 4; ++t) {
+            float4 wv[kRG];
+#pragma unroll
+            for (int i = 0; i < kRG; ++i) wv[i] = *(reinterpret_cast<const float4*>(wp[i]) + t);
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const float4 xv = *reinterpret_cast<const float4*>(xs + (size_t)k * ops + 4 * t);
 #pragma unroll
                 for (int i = 0; i < kRG; ++i) {
-                    const float4* w4 = reinterpret_cast<const float4*>(wp[i]) + t;
-                    wv[i] = cached ? *w4 : __ldg(w4);
-                }
-#pragma unroll
-                for (int j = 0; j < kTailMax; ++j) {
-                    if (!((mask >> j) & 1u)) continue;
-                    const float4 xv = *reinterpret_cast<const float4*>(opnd + (size_t)j * ops + c * kStepPad + 4 * t);
-#pragma unroll
-                    for (int i = 0; i < kRG; ++i) {
-                        part[i][j] = fmaf(xv.x, wv[i].x, part[i][j]);
-                        part[i][j] = fmaf(xv.y, wv[i].y, part[i][j]);
-                        part[i][j] = fmaf(xv.z, wv[i].z, part[i][j]);
-                        part[i][j] = fmaf(xv.w, wv[i].w, part[i][j]);
-                    }
+                    part[i][k] = fmaf(xv.x, wv[i].x, part[i][k]);
+                    part[i][k] = fmaf(xv.y, wv[i].y, part[i][k]);
+                    part[i][k] = fmaf(xv.z, wv[i].z, part[i][k]);
+                    part[i][k] = fmaf(xv.w, wv[i].w, part[i][k]);
                 }
             }
         }
@@ -251,14 +265,36 @@ __device__ __forceinline__ void layer_partials(const float* __restrict__ opnd, i
         for (int i = 0; i < kRG; ++i) {
             if (rb + i >= rl1) break;
 #pragma unroll
-            for (int j = 0; j < kTailMax; ++j)
-                if ((gr.live >> j) & 1u) pbuf[((size_t)j * npr + (rb + i - rl0)) * ps + c] = part[i][j];
+            for (int k = 0; k < NL; ++k) pbuf[((size_t)(s0 + k) * npr + (rb + i - rl0)) * ps + c] = part[i][k];
+        }
+    }
+}
+
+// group_partials for every group of L.
+__device__ __forceinline__ void layer_partials(const float* __restrict__ opnd, int ops, float* pbuf, int ps, int rl0,
+                                               int rl1, int nsteps, int row_beg, const TailList& L, int cache_ri,
+                                               const float* wc, int wops, const float* const* s_W, int ldk) {
+    for (int g = 0; g < L.ng; ++g) {
+        const int s0 = L.g0[g], n = L.g0[g + 1] - s0, ri = L.ri[g];
+        const bool cached = ri == cache_ri;
+        const float* w0 = cached ? wc : s_W[ri] + (size_t)row_beg * ldk;
+        const size_t wr = cached ? (size_t)wops : (size_t)ldk;
+        const int ws = cached ? kStepPad : kStep;
+        switch (n) {
+            case 1: group_partials<1>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            case 2: group_partials<2>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            case 3: group_partials<3>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            case 4: group_partials<4>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            case 5: group_partials<5>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            case 6: group_partials<6>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            case 7: group_partials<7>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
+            default: group_partials<8>(opnd, ops, pbuf, ps, rl0, rl1, nsteps, s0, w0, wr, ws); break;
         }
     }
 }
 
 // Operand of the first layer of a chunk, as batch_fill_kernel: s = [x; 2 rho z - lam'].
-__device__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const int* s_ri) {
+__device__ __forceinline__ void tail_fill(const TailArgs& a, float* S, const int* s_live, const int* s_ri) {
     const BatchParams& p = a.p;
     const int total = a.nq * p.ldk;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -283,7 +319,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
     __shared__ int s_live[kTailMax], s_ri[kTailMax], s_act[kTailMax], s_nri[kTailMax], s_any;
     grid_sync_init(&s_ok);
     __shared__ unsigned s_red[kTailMax][RW_WORDS];
-    BatchParams p = a.p;
+    // the launch's parameters are read in place: per-layer values (the operand the layer
+    // writes, the epilogue flags) are kept in scalars
+    const BatchParams& p = a.p;
     const int nq = a.nq;
     const int nsteps = (p.ldk > p.ldkc ? p.ldk : p.ldkc) / kStep;
     const int ops = nsteps * kStepPad;                       // staged floats per QP
@@ -299,7 +337,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
     const int ps = lsteps | 1;                               // stride of an output's step partials
     const int wops = lsteps * kStepPad;                      // cached floats per row
     float* wc = pbuf + a.scratch;
-    __shared__ TailGroups s_gr;
+    __shared__ TailList s_L;
+    __shared__ const float* s_W[RQ_MAX_RHO];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int r = 0; r < RQ_MAX_RHO; ++r) s_W[r] = a.W[r];
+    }
     int cache_ri = -1;
     const int gwarp = blockIdx.x * (kTailThreads / 32) + warp, nwarps = gridDim.x * (kTailThreads / 32);
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
@@ -330,7 +373,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                     const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(
                         wc + (size_t)rr * wops + (q >> 2) * kStepPad + (q & 3) * 4));
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
-                                 "l"(a.W[ri0] + (size_t)(row_beg + rr) * p.ldk + 4 * q)
+                                 "l"(s_W[ri0] + (size_t)(row_beg + rr) * p.ldk + 4 * q)
                                  : "memory");
                 }
                 asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
@@ -338,31 +381,33 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                 cache_ri = ri0;
             }
         }
-        // the QPs grouped by bank entry for the layer product
+        // the live QPs, compacted and grouped by bank entry, for the layer product
         if (threadIdx.x == 0) {
-            TailGroups g{};
+            TailList L{};
             for (int j = 0; j < nq; ++j) {
                 if (!s_live[j]) continue;
-                g.live |= 1u << j;
-                int q = 0;
-                while (q < g.n && g.ri[q] != s_ri[j]) ++q;
-                if (q == g.n) {
-                    g.ri[q] = s_ri[j];
-                    g.mask[q] = 0u;
-                    ++g.n;
-                }
-                g.mask[q] |= 1u << j;
+                int g = 0;
+                while (g < L.ng && L.ri[g] != s_ri[j]) ++g;
+                if (g == L.ng) L.ri[L.ng++] = s_ri[j];
             }
-            s_gr = g;
+            for (int g = 0; g < L.ng; ++g) {
+                L.g0[g] = L.nl;
+                for (int j = 0; j < nq; ++j)
+                    if (s_live[j] && s_ri[j] == L.ri[g]) L.j[L.nl++] = j;
+            }
+            L.g0[L.ng] = L.nl;
+            s_L = L;
         }
         __syncthreads();
-        const TailGroups gr = s_gr;
-        // a.regs: thread o owns output (row row_beg + o % nr, QP o / nr); its state (bias of
-        // the QP's bank entry, and for rows of A x the carried A x, z, lam', l, u, rho_i)
-        // stays in registers for the chunk: loaded here, written back at the chunk's last
-        // layer (the checks, the decision and the next chunk's fill read it from memory)
-        const int oj = nr > 0 ? (int)threadIdx.x / nr : kTailMax, orl = nr > 0 ? (int)threadIdx.x % nr : 0;
-        const bool own = a.regs && oj < nq && s_live[oj];
+        const TailList& L = s_L;
+        const int nl = L.nl;
+        // a.regs: thread o owns output (row row_beg + o % nr, compact slot o / nr); its state
+        // (bias of the QP's bank entry, and for rows of A x the carried A x, z, lam', l, u,
+        // rho_i) stays in registers for the chunk: loaded here, written back at the chunk's
+        // last layer (the checks, the decision and the next chunk's fill read it from memory)
+        const int ok = nr > 0 ? (int)threadIdx.x / nr : kTailMax, orl = nr > 0 ? (int)threadIdx.x % nr : 0;
+        const bool own = a.regs && ok < nl;
+        const int oj = own ? L.j[ok] : 0;
         const int o_qp = own ? a.qlist[oj] : 0, o_ri = own ? s_ri[oj] : 0, o_r = row_beg + orl;
         float rb = 0.f, ray = 0.f, rz = 0.f, rlam = 0.f, rlo = 0.f, rup = 0.f, rrho = 0.f;
         if (own) {
@@ -379,23 +424,19 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
         }
         for (int jl = 0; jl < len; ++jl) {
             const float* Sc = a.S + (size_t)cur * kTailMax * p.ldk;
-            p.Sout = a.S + (size_t)(cur ^ 1) * kTailMax * p.ldk;
-            p.CK32 = a.CKB;
-            p.CK = nullptr;
-            p.flags = jl == len - 1 ? (EPI_LAST | (check ? EPI_CHECK : 0u)) : 0u;
+            float* Sout = a.S + (size_t)(cur ^ 1) * kTailMax * p.ldk;
             const bool last = jl == len - 1;
-            stage_rows(tsm, ops, Sc, p.ldk, 0, p.ldk, nq, s_live);
+            stage_list(tsm, ops, Sc, p.ldk, p.ldk, L);
             __syncthreads();
             for (int rl0 = 0; rl0 < nr; rl0 += a.pr) {
                 const int rl1 = min(nr, rl0 + a.pr), npr = rl1 - rl0;
                 if (rl0 > 0) __syncthreads();   // the previous pass's sums have read pbuf
-                layer_partials(tsm, ops, pbuf, ps, rl0, rl1, lsteps, row_beg, gr, cache_ri, wc, wops, a.W, p.ldk);
+                layer_partials(tsm, ops, pbuf, ps, rl0, rl1, lsteps, row_beg, L, cache_ri, wc, wops, s_W, p.ldk);
                 __syncthreads();
                 // every output's partials added in step order (as fp32_tile), then the layer's
                 // element-wise part
-                for (int o = threadIdx.x; o < kTailMax * npr; o += blockDim.x) {
-                    const int j = o / npr, r = row_beg + rl0 + (o - j * npr);
-                    if (!((gr.live >> j) & 1u)) continue;
+                for (int o = threadIdx.x; o < nl * npr; o += blockDim.x) {
+                    const int k = o / npr, r = row_beg + rl0 + (o - k * npr), j = L.j[k];
                     const float* q = pbuf + (size_t)o * ps;
                     float acc = 0.f;
                     int c = 0;
@@ -409,7 +450,10 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                     }
                     for (; c < lsteps; ++c) acc += q[c];
                     if (!a.regs) {
-                        layer_elem(p, j, a.qlist[j], s_ri[j], r, acc);
+                        BatchParams q = p;
+                        q.Sout = Sout;
+                        q.flags = last ? (EPI_LAST | (check ? EPI_CHECK : 0u)) : 0u;
+                        layer_elem(q, j, a.qlist[j], s_ri[j], r, acc);
                         continue;
                     }
                     // the FP32 layer of layer_elem on register state (o == threadIdx.x here)
@@ -435,7 +479,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                             p.LAM[oo] = ln;
                         }
                     }
-                    if (!last) p.Sout[(size_t)j * p.ldk + r] = s_new;
+                    if (!last) Sout[(size_t)j * p.ldk + r] = s_new;
                 }
             }
             cur ^= 1;
@@ -448,8 +492,6 @@ __global__ void __launch_bounds__(kTailThreads, 1) batch_tail_kernel(TailArgs a)
                 for (int e = threadIdx.x; e < kTailMax * RW_WORDS; e += blockDim.x)
                     a.red[(size_t)((checks + 1) % 3) * kTailMax * RW_WORDS + e] = 0u;
             ++checks;
-            p.CK32 = a.CKB;
-            p.CK = nullptr;
             // phase 1: [P; A] x over the x columns of the check operand
             for (int e = threadIdx.x; e < kTailMax * RW_WORDS; e += blockDim.x) (&s_red[0][0])[e] = 0u;
             stage_rows(tsm, ops, a.CKB, p.ldkc, 0, p.n64, nq, s_live);
@@ -640,6 +682,8 @@ int batch_tail(relu_qp_t h, const BatchParams& p, const DecideArgs& d, int nq, i
     RQ_CUDA(h, cudaMemsetAsync(w.TBAR, 0, sizeof(unsigned) * 4, h->stream));
     TailArgs a{};
     a.p = p;
+    a.p.CK32 = w.TCK;
+    a.p.CK = nullptr;
     a.d = d;
     for (int r = 0; r < h->nr; ++r) a.W[r] = h->be[r].Wt;
     a.Wc = w.Wc32;
