@@ -435,6 +435,28 @@ int relu_qp_dims(relu_qp_t h, int* n, int* m, int* n_rho);
 long long relu_qp_device_bytes(relu_qp_t h);
 
 /*
+ * ---- launch shape of the single-QP FP32 solve --------------------------------
+ * relu_qp_setup times candidate launch shapes of the solve kernel behind
+ * relu_qp_solve (the online stage of Algorithm 1, Sec. III-B) and keeps the
+ * fastest: a cooperative grid of `ctas` CTAs with a grid barrier between
+ * layers, or one thread-block cluster of `ctas` CTAs (cluster = ctas) that keep
+ * the layer's operand in distributed shared memory and synchronise through
+ * cluster-scope mbarriers.  Each row's dot product and update is the same
+ * arithmetic in every shape, so the results do not depend on the choice; these
+ * calls exist for tests and tuning.
+ *
+ * relu_qp_single_config: the shape in use: *ctas, *cluster (0 = grid form),
+ *   *cached_rows (rows of the layer each CTA keeps in shared memory); any
+ *   pointer may be NULL.  Errors: INVALID (NULL handle, or no setup yet).
+ * relu_qp_single_set_config: use ctas CTAs (1 <= ctas <= n + m) as a grid
+ *   (cluster = 0) or as one cluster (cluster = ctas, one of 2, 4, 8, 16).
+ *   Errors: INVALID (handle, no setup, arguments), UNSUPPORTED (the shape
+ *   cannot be resident on this GPU); the previous shape stays on error.
+ */
+int relu_qp_single_config(relu_qp_t h, int* ctas, int* cluster, int* cached_rows);
+int relu_qp_single_set_config(relu_qp_t h, int ctas, int cluster);
+
+/*
  * ---- deadline diagnostics ---------------------------------------------------
  * No counterpart in the paper.  Every device-side wait of the library (the
  * grid barrier of the cooperative kernels, and the mbarrier and layer-counter

@@ -91,6 +91,9 @@ _SIGNATURES = {
                                              ctypes.POINTER(ctypes.c_longlong)]),
     "relu_qp_server_bytes_in_use": (ctypes.c_longlong, [_c_void_p]),
     "relu_qp_device_bytes": (ctypes.c_longlong, [_c_void_p]),
+    "relu_qp_single_config": (_c_int, [_c_void_p, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int),
+                                      ctypes.POINTER(_c_int)]),
+    "relu_qp_single_set_config": (_c_int, [_c_void_p, _c_int, _c_int]),
     "relu_qp_diag_device_wait": (_c_int, [_c_int, ctypes.c_longlong, ctypes.POINTER(_c_int),
                                           ctypes.POINTER(_c_double)]),
     "relu_qp_diag_host_barrier": (_c_int, [_c_int, _c_int, _c_int, ctypes.c_longlong, ctypes.POINTER(_c_int),
@@ -222,6 +225,16 @@ class ReluQP:
     def device_bytes(self):
         """Device memory the handle keeps (what device_budget caps)."""
         return int(lib().relu_qp_device_bytes(self._h))
+
+    def single_config(self):
+        """Launch shape of the single-QP solve: (ctas, cluster, cached_rows); cluster 0 = grid form."""
+        c, k, r = _c_int(0), _c_int(0), _c_int(0)
+        self._check(lib().relu_qp_single_config(self._h, ctypes.byref(c), ctypes.byref(k), ctypes.byref(r)))
+        return c.value, k.value, r.value
+
+    def set_single_config(self, ctas, cluster=0):
+        """Use `ctas` CTAs as a grid (cluster 0) or as one cluster (cluster = ctas in 2, 4, 8, 16)."""
+        self._check(lib().relu_qp_single_set_config(self._h, int(ctas), int(cluster)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -523,6 +523,16 @@ int relu_qp_dims(relu_qp_t h, int* n, int* m, int* n_rho) {
 
 long long relu_qp_device_bytes(relu_qp_t h) { return h ? (long long)h->dev_bytes : -1; }
 
+int relu_qp_single_config(relu_qp_t h, int* ctas, int* cluster, int* cached_rows) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    return rq::single_get_config(h, ctas, cluster, cached_rows);
+}
+
+int relu_qp_single_set_config(relu_qp_t h, int ctas, int cluster) {
+    if (!h) return rq::fail(nullptr, RELU_QP_ERR_INVALID, "handle is NULL");
+    return rq::single_set_config(h, ctas, cluster);
+}
+
 void relu_qp_destroy(relu_qp_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);

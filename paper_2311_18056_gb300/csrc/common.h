@@ -69,7 +69,8 @@ struct SingleWork {
     unsigned* bar = nullptr;    // grid barrier: arrival count of the launch (+ pad word)
     int* out_i = nullptr;       // status, iters, rho_index, switches, err
     float* out_f = nullptr;     // r_prim, r_dual
-    int grid = 0;               // CTAs of the cooperative launch (autotuned)
+    int grid = 0;               // CTAs of the launch (autotuned)
+    int cluster = 0;            // > 1: the launch is one cluster of `grid` CTAs (else a cooperative grid)
     int cached_rows = 0;        // rows of W each CTA keeps in shared memory
     int rows_per_cta = 0;
 };
@@ -214,6 +215,8 @@ int compute_bias(relu_qp_t h);
 int single_solve(relu_qp_t h, const float* x_warm_dev, const float* lam_warm_dev, int rho_index,
                  double eps_abs, double eps_rel, int max_iter, relu_qp_info* info);
 int single_prepare(relu_qp_t h);
+int single_get_config(relu_qp_t h, int* ctas, int* cluster, int* cached_rows);
+int single_set_config(relu_qp_t h, int ctas, int cluster);
 // Same solve with its scratch in a fixed device array (single_solve.cu).
 int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm, int rho_index, double eps_abs,
                          double eps_rel, int max_iter, float* x_out, float* z_out, float* lam_out,

@@ -60,6 +60,94 @@ __device__ __forceinline__ bool grid_barrier(const SP& p, GridSyncState* s_ok) {
     return grid_sync(p.bar, p.out_i + OUT_ERR, p.timeout_ns, s_ok);
 }
 
+// --- one thread-block cluster instead of a cooperative grid ---
+__device__ __forceinline__ uint32_t cl_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_smem(const void* ptr) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+// shared::cluster address of the shared::cta address `addr` in CTA `rank`
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cl_st(uint32_t cluster_addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cluster_addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cl_mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n fence.mbarrier_init.release.cluster;" ::"r"(bar),
+                 "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void cl_arrive(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool cl_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// hardware barrier of every thread of the cluster (no deadline: used only where every
+// CTA is known to arrive, at the start and at the end of the kernel)
+__device__ __forceinline__ void cl_sync_hw() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Synchronisation between layers and phases.  Grid form: the grid barrier.
+// Cluster form (the launch is one cluster of C CTAs): every CTA has an
+// mbarrier expecting C arrivals per phase; thread 0 arrives (release at cluster
+// scope) on all C of them (lane q of warp 0 on CTA q's) and thread 0 waits
+// (acquire) on its own, with a deadline and
+// leaving early once another CTA has set the error word.  Each CTA arrives once
+// per barrier on every mbarrier, so no CTA passes barrier k before every CTA
+// has arrived at it, and a CTA's own mbarrier is never more than one phase
+// ahead of it (the parity wait cannot miss a phase).
+struct SyncCtx {
+    GridSyncState* gs;
+    uint32_t cbar;       // the CTA's cluster mbarrier (shared::cta address)
+    uint32_t phase;      // barriers passed (cluster form)
+    int C;               // CTAs of the cluster (cluster form)
+};
+
+template <bool CL>
+__device__ __forceinline__ bool sync_all(const SP& p, SyncCtx& sc) {
+    if (!CL) return grid_barrier(p, sc.gs);
+    __syncthreads();
+    // lane q of warp 0 arrives on CTA q's mbarrier (the C releases overlap)
+    if (threadIdx.x < (unsigned)sc.C) cl_arrive(cl_mapa(sc.cbar, threadIdx.x));
+    if (threadIdx.x == 0) {
+        int* err = p.out_i + OUT_ERR;
+        int ok = 1;
+        const long long t0 = grid_sync_timer();
+        while (!cl_try(sc.cbar, sc.phase & 1u)) {
+            int e;
+            asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
+            if (e != 0) {
+                ok = 0;
+                break;
+            }
+            if (grid_sync_timer() - t0 > p.timeout_ns) {
+                atomicExch(err, RELU_QP_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        sc.gs->ok = ok;
+    }
+    ++sc.phase;
+    __syncthreads();
+    return sc.gs->ok != 0;
+}
+
 // Dot product of a padded row with a padded vector in shared memory; the
 // result is valid in every lane.  Rows and vectors are 16-byte aligned and
 // zero padded to a multiple of 4 floats.
@@ -97,6 +185,65 @@ __device__ __forceinline__ float row_dot_global(const float* __restrict__ w, con
     return warp_sum((a0 + a1) + (a2 + a3));
 }
 
+// Dot products of NR padded rows (w[j], in shared or global memory) with one
+// padded vector in shared memory, in one pass over k: every row keeps the
+// four accumulators and the reduction of row_dot, so each result has row_dot's
+// bits, while the rows' loads and shuffle reductions overlap.  Results are
+// valid in every lane.
+template <int NR, bool LDG>
+__device__ __forceinline__ void rows_dot(const float* const (&w)[NR], const float* __restrict__ s, int ld, int lane,
+                                         float (&out)[NR]) {
+    const float4* s4 = reinterpret_cast<const float4*>(s);
+    const int n4 = ld >> 2;
+    float a[NR][4];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) a[j][0] = a[j][1] = a[j][2] = a[j][3] = 0.f;
+    for (int k = lane; k < n4; k += 32) {
+        const float4 b = s4[k];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const float4* wj = reinterpret_cast<const float4*>(w[j]) + k;
+            const float4 x = LDG ? __ldg(wj) : *wj;
+            a[j][0] = fmaf(x.x, b.x, a[j][0]);
+            a[j][1] = fmaf(x.y, b.y, a[j][1]);
+            a[j][2] = fmaf(x.z, b.z, a[j][2]);
+            a[j][3] = fmaf(x.w, b.w, a[j][3]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) out[j] = warp_sum((a[j][0] + a[j][1]) + (a[j][2] + a[j][3]));
+}
+
+constexpr int kRowsILP = 4;   // rows of a warp whose dot products run together
+
+// rows_dot for the first cnt (1 .. kRowsILP) pointers of w.  LDG: every row is in
+// global memory (read-only loads); else the rows are in shared memory or mixed.
+template <bool LDG>
+__device__ __forceinline__ void group_dots(int cnt, const float* const (&w)[kRowsILP], const float* s, int ld,
+                                           int lane, float (&acc)[kRowsILP]) {
+    if (cnt == 1) {
+        const float* w1[1] = {w[0]};
+        float o[1];
+        rows_dot<1, LDG>(w1, s, ld, lane, o);
+        acc[0] = o[0];
+    } else if (cnt == 2) {
+        const float* w2[2] = {w[0], w[1]};
+        float o[2];
+        rows_dot<2, LDG>(w2, s, ld, lane, o);
+        acc[0] = o[0];
+        acc[1] = o[1];
+    } else if (cnt == 3) {
+        const float* w3[3] = {w[0], w[1], w[2]};
+        float o[3];
+        rows_dot<3, LDG>(w3, s, ld, lane, o);
+        acc[0] = o[0];
+        acc[1] = o[1];
+        acc[2] = o[2];
+    } else {
+        rows_dot<4, LDG>(w, s, ld, lane, acc);
+    }
+}
+
 // Copy `count` floats (padded length `ld`, a multiple of 4) written by other
 // CTAs into shared memory, bypassing L1 so that no stale line is read.
 __device__ __forceinline__ void load_shared_cg(float* dst, const float* src, int ld) {
@@ -120,58 +267,142 @@ __device__ __forceinline__ float red_get(const unsigned* slot, int word) {
     return __uint_as_float(__ldcg(slot + word));
 }
 
-__global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
-    extern __shared__ __align__(16) float smem[];
-    __shared__ GridSyncState s_ok;
-    grid_sync_init(&s_ok);
+// The solve.  Grid form (CL = false): a cooperative grid; the operand s of a
+// layer goes through global memory (written by the rows' owners, staged into
+// shared memory after the grid barrier).  Cluster form (CL = true): the launch
+// is one cluster; every CTA keeps both operand buffers in shared memory and the
+// owner of a row writes its new entry into every CTA's copy (distributed shared
+// memory) before the cluster barrier, so a layer never touches L2 for s.
+template <bool CL>
+__device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n, m = p.m, R = p.R;
     const int row0 = blockIdx.x * p.rows_per_cta;
     const int row1 = min(row0 + p.rows_per_cta, R);
     const int ncache = max(0, min(p.cached_rows, row1 - row0));
     float* wcache = smem;
-    float* sv = smem + (size_t)p.cached_rows * p.ldw;     // ldw floats
+    float* sv = smem + (size_t)p.cached_rows * p.ldw;     // ldw floats (cluster form: 2 x ldw, both operands)
+    float* svk = CL ? sv + 2 * (size_t)p.ldw : sv;        // the checks' staged vector (ldw floats)
+    // the state of the CTA's rows, kept in shared memory for the whole solve (the
+    // global copies are still written, for the checks and the outputs): bias of the
+    // bank entry in use, and for rows of A x the carried A x, z, lam', rho_i, l, u
+    const int rpc = p.rows_per_cta;
+    float* st_bias = sv + (CL ? 3 : 1) * (size_t)p.ldw;
+    float* st_ay = st_bias + rpc;
+    float* st_z = st_ay + rpc;
+    float* st_lam = st_z + rpc;
+    float* st_rho = st_lam + rpc;
+    float* st_l = st_rho + rpc;
+    float* st_u = st_l + rpc;
     const int r2_0 = blockIdx.x * p.rows2_per_cta;
     const int r2_1 = min(r2_0 + p.rows2_per_cta, n);
 
     int ri = p.rho_index0;
     int switches = 0, checks = 0, cur = 0;
     if (ncache > 0) load_w_cache(p, wcache, ri, row0, ncache);
+    for (int r = row0 + threadIdx.x; r < row1; r += blockDim.x) {
+        const int lr = r - row0;
+        st_bias[lr] = __ldg(p.bias[ri] + r);
+        if (r >= n) {
+            const int i = r - n;
+            st_ay[lr] = __ldcg(p.Ay + i);
+            st_z[lr] = __ldcg(p.z + i);
+            st_lam[lr] = __ldcg(p.lam + i);
+            st_rho[lr] = (float)(p.rho[ri] * (double)__ldg(p.rs + i));
+            st_l[lr] = __ldg(p.l + i);
+            st_u[lr] = __ldg(p.u + i);
+        }
+    }
+    if (CL) {
+        // operand buffer 0 is s0; buffer 1 only needs its padding zeroed: its rows are
+        // written by the partners' first layer, which may already be running (nobody
+        // writes buffer 0 before every CTA has passed the first barrier)
+        load_shared_cg(sv, p.s0, p.ldw);
+        for (int k = R + threadIdx.x; k < p.ldw; k += blockDim.x) sv[p.ldw + k] = 0.f;
+    }
     __syncthreads();
 
     for (int it = 1; it <= p.max_iter; ++it) {
         // ---------------- one layer: s[cur] -> s[cur^1] ----------------
         const float* scur = cur ? p.s1 : p.s0;
         float* snext = cur ? p.s0 : p.s1;
-        load_shared_cg(sv, scur, p.ldw);
-        __syncthreads();
+        const float* svc = CL ? sv + (size_t)cur * p.ldw : sv;
+        const uint32_t svn = CL ? cl_smem(sv + (size_t)(cur ^ 1) * p.ldw) : 0u;
+        if (!CL) {
+            load_shared_cg(sv, scur, p.ldw);
+            __syncthreads();
+        }
         const float* Wg = p.Wt[ri];
-        const float* bias = p.bias[ri];
-        const double rho = p.rho[ri];
-        for (int r = row0 + warp; r < row1; r += kWarps) {
-            const int lr = r - row0;
-            const float acc = (lr < ncache) ? row_dot(wcache + (size_t)lr * p.ldw, sv, p.ldw, lane)
-                                            : row_dot_global(Wg + (size_t)r * p.ldw, sv, p.ldw, lane);
-            if (lane == 0) {
-                const float t = acc + __ldg(bias + r);
+        // the global copies of the rows' state are read only by the checks and the
+        // outputs: written on the layers before a check and on the last one
+        const bool keep = (p.check_interval > 0 && it % p.check_interval == 0) || it == p.max_iter;
+        // a warp's rows rb, rb + kWarps, ... in groups of up to kRowsILP: their dot
+        // products together, then lane j updates row j of the group
+        for (int rb = row0 + warp; rb < row1; rb += kRowsILP * kWarps) {
+            const int cnt = min(kRowsILP, (row1 - rb + kWarps - 1) / kWarps);
+            // the cached rows are the first ncache of the CTA: a group is all cached, all in
+            // global memory, or (once per CTA) mixed
+            const int lr_first = rb - row0, lr_last = rb + (cnt - 1) * kWarps - row0;
+            float acc[kRowsILP] = {0.f, 0.f, 0.f, 0.f};
+            if (lr_last < ncache) {
+                const float* w[kRowsILP];
+#pragma unroll
+                for (int j = 0; j < kRowsILP; ++j) w[j] = wcache + (size_t)(lr_first + (j < cnt ? j : 0) * kWarps) * p.ldw;
+                group_dots<false>(cnt, w, svc, p.ldw, lane, acc);
+            } else if (lr_first >= ncache) {
+                const float* w[kRowsILP];
+#pragma unroll
+                for (int j = 0; j < kRowsILP; ++j) w[j] = Wg + (size_t)(rb + (j < cnt ? j : 0) * kWarps) * p.ldw;
+                group_dots<true>(cnt, w, svc, p.ldw, lane, acc);
+            } else {
+                const float* w[kRowsILP];
+#pragma unroll
+                for (int j = 0; j < kRowsILP; ++j) {
+                    const int r = rb + (j < cnt ? j : 0) * kWarps, lr = r - row0;
+                    w[j] = lr < ncache ? wcache + (size_t)lr * p.ldw : Wg + (size_t)r * p.ldw;
+                }
+                group_dots<false>(cnt, w, svc, p.ldw, lane, acc);
+            }
+            float snew = 0.f;
+            if (lane < cnt) {
+                float a = acc[0];
+#pragma unroll
+                for (int j = 1; j < kRowsILP; ++j)
+                    if (lane == j) a = acc[j];
+                const int r = rb + lane * kWarps, lr = r - row0;
+                const float t = a + st_bias[lr];
                 if (r < n) {
-                    p.y[r] = t;
-                    snext[r] = t;
+                    if (keep) p.y[r] = t;
+                    snew = t;
                 } else {
                     const int i = r - n;
-                    const float rho_i = (float)(rho * (double)__ldg(p.rs + i));
-                    const float rr = p.Ay[i] - p.z[i] + p.lam[i] / rho_i;
-                    const float zn = fminf(fmaxf(t + rr, __ldg(p.l + i)), __ldg(p.u + i));
+                    const float rho_i = st_rho[lr];
+                    const float rr = st_ay[lr] - st_z[lr] + st_lam[lr] / rho_i;
+                    const float zn = fminf(fmaxf(t + rr, st_l[lr]), st_u[lr]);
                     const float ln = rho_i * rr;
-                    p.Ay[i] = t;
-                    p.z[i] = zn;
-                    p.lam[i] = ln;
-                    snext[r] = 2.0f * rho_i * zn - ln;
+                    st_ay[lr] = t;
+                    st_z[lr] = zn;
+                    st_lam[lr] = ln;
+                    if (keep) {
+                        p.Ay[i] = t;
+                        p.z[i] = zn;
+                        p.lam[i] = ln;
+                    }
+                    snew = 2.0f * rho_i * zn - ln;
+                }
+                if (!CL) snext[r] = snew;
+            }
+            if (CL) {
+                // lane q writes each row's entry into CTA q's next operand
+                for (int j = 0; j < cnt; ++j) {
+                    const float v = __shfl_sync(0xffffffffu, snew, j);
+                    const uint32_t addr = svn + 4u * (uint32_t)(rb + j * kWarps);
+                    for (int q = lane; q < sc.C; q += 32) cl_st(cl_mapa(addr, (uint32_t)q), v);
                 }
             }
         }
         cur ^= 1;
-        if (!grid_barrier(p, &s_ok)) return;
+        if (!sync_all<CL>(p, sc)) return;
 
         const bool is_check = (p.check_interval > 0) && (it % p.check_interval == 0);
         const bool last = (it == p.max_iter);
@@ -182,18 +413,18 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
         if (blockIdx.x == 0 && threadIdx.x < RED_WORDS)
             p.red[((checks + 1) % 3) * RED_WORDS + threadIdx.x] = 0u;
         ++checks;
-        load_shared_cg(sv, p.y, p.ldp);
+        load_shared_cg(svk, p.y, p.ldp);
         __syncthreads();
         for (int r = row0 + warp; r < row1; r += kWarps) {
             if (r < n) {
-                const float v = row_dot_global(p.P + (size_t)r * p.ldp, sv, p.ldp, lane);
+                const float v = row_dot_global(p.P + (size_t)r * p.ldp, svk, p.ldp, lane);
                 if (lane == 0) {
                     p.Py[r] = v;
                     red_max(slot, RED_PX, p.rsx ? v * p.rsx[r] : v);
                 }
             } else {
                 const int i = r - n;
-                const float v = row_dot_global(p.A + (size_t)i * p.lda, sv, p.lda, lane);
+                const float v = row_dot_global(p.A + (size_t)i * p.lda, svk, p.lda, lane);
                 if (lane == 0) {
                     const float zi = p.z[i];
                     const float rho_i = (float)(p.rho[ri] * (double)__ldg(p.rs + i));
@@ -206,18 +437,18 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
                 }
             }
         }
-        if (!grid_barrier(p, &s_ok)) return;
-        if (m > 0) load_shared_cg(sv, p.lstd, p.ldt);
+        if (!sync_all<CL>(p, sc)) return;
+        if (m > 0) load_shared_cg(svk, p.lstd, p.ldt);
         __syncthreads();
         for (int j = r2_0 + warp; j < r2_1; j += kWarps) {
-            const float v = (m > 0) ? row_dot_global(p.At + (size_t)j * p.ldt, sv, p.ldt, lane) : 0.f;
+            const float v = (m > 0) ? row_dot_global(p.At + (size_t)j * p.ldt, svk, p.ldt, lane) : 0.f;
             if (lane == 0) {
                 const float f = p.rsx ? p.rsx[j] : 1.f;
                 red_max(slot, RED_RD, (__ldcg(p.Py + j) + __ldg(p.q + j) + v) * f);
                 red_max(slot, RED_ATL, v * f);
             }
         }
-        if (!grid_barrier(p, &s_ok)) return;
+        if (!sync_all<CL>(p, sc)) return;
 
         // ---------------- decision (identical in every CTA) ----------------
         const double rp = red_get(slot, RED_RP), rd = red_get(slot, RED_RD);
@@ -240,7 +471,11 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
             return;
         }
         // refresh the carried Ax with the directly computed one
-        for (int r = max(row0, n) + threadIdx.x; r < row1; r += blockDim.x) p.Ay[r - n] = p.Axf[r - n];
+        for (int r = max(row0, n) + threadIdx.x; r < row1; r += blockDim.x) {
+            const float v = p.Axf[r - n];
+            p.Ay[r - n] = v;
+            st_ay[r - row0] = v;
+        }
         if (!p.adaptive || !is_check) continue;
         // Eq. rho_update (inf-norms, 1e-4 floors), nearest bank entry in log distance
         const double num = rp * fmax(fmax(nPx, nAtl), fmax(p.qnorm, 1e-4));
@@ -266,12 +501,43 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
             const float zi = p.z[i];
             const float lnew = p.lstd[i] - rho_i * (p.Axf[i] - zi);
             p.lam[i] = lnew;
-            scur2[r] = 2.0f * rho_i * zi - lnew;
+            st_lam[r - row0] = lnew;
+            st_rho[r - row0] = rho_i;
+            const float sn = 2.0f * rho_i * zi - lnew;
+            if (CL) {
+                const uint32_t a = cl_smem(sv + (size_t)cur * p.ldw + r);
+                for (int q = 0; q < sc.C; ++q) cl_st(cl_mapa(a, (uint32_t)q), sn);
+            } else {
+                scur2[r] = sn;
+            }
         }
         ri = nri;
         ++switches;
         if (ncache > 0) load_w_cache(p, wcache, ri, row0, ncache);
-        if (!grid_barrier(p, &s_ok)) return;
+        for (int r = row0 + threadIdx.x; r < row1; r += blockDim.x) st_bias[r - row0] = __ldg(p.bias[ri] + r);
+        if (!sync_all<CL>(p, sc)) return;
+    }
+}
+
+template <bool CL>
+__global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ GridSyncState s_ok;
+    __shared__ __align__(8) unsigned long long s_cbar;
+    grid_sync_init(&s_ok);
+    SyncCtx sc{&s_ok, 0u, 0u, 1};
+    if (CL) {
+        sc.C = (int)cl_size();
+        sc.cbar = cl_smem(&s_cbar);
+        if (threadIdx.x == 0) cl_mbar_init(sc.cbar, (uint32_t)sc.C);
+        cl_sync_hw();   // every mbarrier initialised before any remote arrival
+    }
+    solve_body<CL>(p, smem, sc);
+    if (CL) {
+        // no CTA leaves while a partner may still write its shared memory (every
+        // wait before this point has a deadline, so every CTA gets here)
+        __syncthreads();
+        cl_sync_hw();
     }
 }
 
@@ -352,29 +618,93 @@ int fill_params(relu_qp_t h, SP& p, int grid) {
     return RELU_QP_OK;
 }
 
-size_t smem_bytes(int cached_rows, int ldw) { return ((size_t)cached_rows + 1) * ldw * sizeof(float); }
+// cached rows of W + the staged operand (cluster form: both operands and the checks' vector)
+// + the state of the CTA's rows (7 floats per row)
+size_t smem_bytes(int cached_rows, int ldw, bool cl, int rows_per_cta) {
+    return (((size_t)cached_rows + (cl ? 3 : 1)) * ldw + 7 * (size_t)rows_per_cta) * sizeof(float);
+}
 
 // Largest dynamic shared memory the solve kernel may request: the opt-in
-// per-block limit minus the kernel's static shared memory.
+// per-block limit minus the kernel's static shared memory (of either form).
 int max_shared(relu_qp_t h) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    int stat = 0;
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, single_solve_kernel) == cudaSuccess) v -= (int)fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, single_solve_kernel<false>) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+    if (cudaFuncGetAttributes(&fa, single_solve_kernel<true>) == cudaSuccess && (int)fa.sharedSizeBytes > stat)
+        stat = (int)fa.sharedSizeBytes;
     cudaGetLastError();
-    return v - 256;
+    return v - stat - 256;
 }
 
 // Shared-memory rows a CTA of a `grid`-CTA launch can cache.
-int cached_rows_for(relu_qp_t h, int grid) {
+int cached_rows_for(relu_qp_t h, int grid, bool cl) {
     const int rows = ceil_div(h->R, grid);
-    const size_t budget = (size_t)max_shared(h);
-    long cap = (long)(budget / ((size_t)h->ldw * sizeof(float))) - 1;
+    const long budget = (long)max_shared(h) - 7L * rows * (long)sizeof(float);
+    long cap = budget / (long)((size_t)h->ldw * sizeof(float)) - (cl ? 3 : 1);
     if (cap < 0) cap = 0;
     return rows < cap ? rows : (int)cap;
 }
 
-int launch(relu_qp_t h, int grid, int cached, int rho_index, double eps_abs, double eps_rel,
+// Launch the solve kernel: a cooperative grid of `grid` CTAs, or (cluster > 1)
+// one cluster of `grid` CTAs.
+int launch_kernel(relu_qp_t h, SP& p, int grid, int cluster, int cached) {
+    const size_t smem = smem_bytes(cached, h->ldw, cluster > 1, ceil_div(h->R, grid));
+    if (cluster > 1) {
+        auto k = single_solve_kernel<true>;
+        RQ_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (cluster > 8) RQ_CUDA(h, cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = h->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        RQ_CUDA(h, cudaLaunchKernelEx(&cfg, k, p));
+        return RELU_QP_OK;
+    }
+    RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+    void* args[] = {&p};
+    RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)single_solve_kernel<false>, dim3(grid), dim3(kThreads), args,
+                                           smem, h->stream));
+    return RELU_QP_OK;
+}
+
+// Whether one cluster of `c` CTAs with this shared memory can be resident.
+bool cluster_fits(relu_qp_t h, int c, int cached) {
+    auto k = single_solve_kernel<true>;
+    const size_t smem = smem_bytes(cached, h->ldw, true, ceil_div(h->R, c));
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (c > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(c);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+    cudaGetLastError();
+    return e == cudaSuccess && n >= 1;
+}
+
+int launch(relu_qp_t h, int grid, int cluster, int cached, int rho_index, double eps_abs, double eps_rel,
            int max_iter, int check_interval, int adaptive) {
     SP p{};
     fill_params(h, p, grid);
@@ -392,13 +722,7 @@ int launch(relu_qp_t h, int grid, int cached, int rho_index, double eps_abs, dou
     RQ_CUDA(h, cudaMemsetAsync(w.red, 0, sizeof(unsigned) * 3 * RED_WORDS, h->stream));
     RQ_CUDA(h, cudaMemsetAsync(w.bar, 0, sizeof(unsigned) * 2, h->stream));
     RQ_CUDA(h, cudaMemsetAsync(w.out_i, 0, sizeof(int) * OUT_WORDS, h->stream));
-    const size_t smem = smem_bytes(cached, h->ldw);
-    RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-    void* args[] = {&p};
-    RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)single_solve_kernel, dim3(grid), dim3(kThreads),
-                                           args, smem, h->stream));
-    return RELU_QP_OK;
+    return launch_kernel(h, p, grid, cluster, cached);
 }
 
 int init_state(relu_qp_t h, const float* x, const float* lam, int rho_index) {
@@ -427,42 +751,88 @@ int compute_bias(relu_qp_t h) {
 // layers (no checks) for each candidate that fits co-resident on the GPU.
 int single_prepare(relu_qp_t h) {
     int per_sm = 0;
-    const int smem_max = max_shared(h);
-    RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    smem_max));
-    std::vector<int> cands;
-    for (int g = 1; g <= 4 * h->num_sms; g *= 2) cands.push_back(g);
-    cands.push_back(h->num_sms);
-    int best_g = 1, best_c = cached_rows_for(h, 1);
+    // candidates: (CTAs, cluster); cluster > 1 = one cluster of that many CTAs
+    std::vector<std::pair<int, int>> cands;
+    for (int g = 1; g <= 4 * h->num_sms; g *= 2) cands.push_back({g, 0});
+    cands.push_back({h->num_sms, 0});
+    for (int c = 2; c <= 16; c *= 2) cands.push_back({c, c});
+    int best_g = 1, best_cl = 0, best_c = cached_rows_for(h, 1, false);
     float best_t = 1e30f;
-    for (int g : cands) {
+    for (const auto& gc : cands) {
+        const int g = gc.first, cl = gc.second;
         if (g > h->R) continue;
-        const int cached = cached_rows_for(h, g);
-        RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, single_solve_kernel, kThreads,
-                                                                 smem_bytes(cached, h->ldw)));
-        if (per_sm < 1 || g > per_sm * h->num_sms) continue;
+        const int cached = cached_rows_for(h, g, cl > 1);
+        if (cl > 1) {
+            if (!cluster_fits(h, cl, cached)) continue;
+        } else {
+            // the occupancy query needs the kernel's shared-memory limit at least this large
+            // (each launch below sets it to its own size)
+            const size_t smem = smem_bytes(cached, h->ldw, false, ceil_div(h->R, g));
+            RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+            RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, single_solve_kernel<false>, kThreads,
+                                                                     smem));
+            if (per_sm < 1 || g > per_sm * h->num_sms) continue;
+        }
         h->sw.grid = g;
+        h->sw.cluster = cl;
         RQ_TRY(init_state(h, nullptr, nullptr, 0));
-        RQ_TRY(launch(h, g, cached, 0, 0.0, 0.0, 10, 0, 0));   // warm-up
+        RQ_TRY(launch(h, g, cl, cached, 0, 0.0, 0.0, 10, 0, 0));   // warm-up
         RQ_TRY(init_state(h, nullptr, nullptr, 0));
         RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-        RQ_TRY(launch(h, g, cached, 0, 0.0, 0.0, 50, 0, 0));
+        RQ_TRY(launch(h, g, cl, cached, 0, 0.0, 0.0, 50, 0, 0));
         RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
         RQ_CUDA(h, cudaStreamSynchronize(h->stream));
         int err = 0;
         RQ_CUDA(h, cudaMemcpy(&err, h->sw.out_i + OUT_ERR, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) return fail(h, RELU_QP_ERR_TIMEOUT, "grid barrier deadline passed while tuning");
+        if (err) return fail(h, RELU_QP_ERR_TIMEOUT, "a barrier deadline passed while tuning the solve");
         float ms = 0.f;
         RQ_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
         if (ms < best_t) {
             best_t = ms;
             best_g = g;
+            best_cl = cl;
             best_c = cached;
         }
     }
     h->sw.grid = best_g;
+    h->sw.cluster = best_cl;
     h->sw.cached_rows = best_c;
     h->sw.rows_per_cta = ceil_div(h->R, best_g);
+    return RELU_QP_OK;
+}
+
+int single_get_config(relu_qp_t h, int* ctas, int* cluster, int* cached_rows) {
+    if (h->sw.grid <= 0) return fail(h, RELU_QP_ERR_INVALID, "the single-QP solve is not set up");
+    if (ctas) *ctas = h->sw.grid;
+    if (cluster) *cluster = h->sw.cluster > 1 ? h->sw.cluster : 0;
+    if (cached_rows) *cached_rows = h->sw.cached_rows;
+    return RELU_QP_OK;
+}
+
+int single_set_config(relu_qp_t h, int ctas, int cluster) {
+    if (h->sw.grid <= 0) return fail(h, RELU_QP_ERR_INVALID, "the single-QP solve is not set up");
+    if (ctas < 1 || ctas > h->R || cluster < 0 || (cluster > 1 && cluster != ctas) ||
+        (cluster > 1 && cluster != 2 && cluster != 4 && cluster != 8 && cluster != 16))
+        return fail(h, RELU_QP_ERR_INVALID, "ctas in [1, n + m]; cluster 0 or cluster = ctas in {2, 4, 8, 16}");
+    const bool cl = cluster > 1;
+    const int cached = cached_rows_for(h, ctas, cl);
+    if (cl) {
+        if (!cluster_fits(h, ctas, cached))
+            return fail(h, RELU_QP_ERR_UNSUPPORTED, "a cluster of this size cannot be resident");
+    } else {
+        int per_sm = 0;
+        RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem_bytes(cached, h->ldw, false, ceil_div(h->R, ctas))));
+        RQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, single_solve_kernel<false>, kThreads,
+                                                                 smem_bytes(cached, h->ldw, false, ceil_div(h->R, ctas))));
+        if (per_sm < 1 || ctas > per_sm * h->num_sms)
+            return fail(h, RELU_QP_ERR_UNSUPPORTED, "that many CTAs cannot be co-resident");
+    }
+    h->sw.grid = ctas;
+    h->sw.cluster = cl ? cluster : 0;
+    h->sw.cached_rows = cached;
+    h->sw.rows_per_cta = ceil_div(h->R, ctas);
     return RELU_QP_OK;
 }
 
@@ -471,8 +841,8 @@ int single_solve(relu_qp_t h, const float* x_warm, const float* lam_warm, int rh
     SingleWork& w = h->sw;
     RQ_TRY(init_state(h, x_warm, lam_warm, rho_index));
     RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-    RQ_TRY(launch(h, w.grid, w.cached_rows, rho_index, eps_abs, eps_rel, max_iter, h->opts.check_interval,
-                  h->opts.adaptive_rho));
+    RQ_TRY(launch(h, w.grid, w.cluster, w.cached_rows, rho_index, eps_abs, eps_rel, max_iter,
+                  h->opts.check_interval, h->opts.adaptive_rho));
     h->launches += 2;
     RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
     int oi[OUT_WORDS];
@@ -480,7 +850,7 @@ int single_solve(relu_qp_t h, const float* x_warm, const float* lam_warm, int rh
     RQ_CUDA(h, cudaMemcpyAsync(oi, w.out_i, sizeof(oi), cudaMemcpyDeviceToHost, h->stream));
     RQ_CUDA(h, cudaMemcpyAsync(of, w.out_f, sizeof(of), cudaMemcpyDeviceToHost, h->stream));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (oi[OUT_ERR]) return fail(h, RELU_QP_ERR_TIMEOUT, "grid barrier deadline passed in relu_qp_solve");
+    if (oi[OUT_ERR]) return fail(h, RELU_QP_ERR_TIMEOUT, "a barrier deadline passed in relu_qp_solve");
     if (info) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -630,12 +1000,8 @@ int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm
     init_state_kernel<<<blocks, 256, 0, h->stream>>>(n, m, ldp, ldw, h->A32, x_warm, lam_warm, h->rs32,
                                                       h->be[rho_index].rho, y, z, lam, Ay, s0, s1);
     RQ_CUDA(h, cudaGetLastError());
-    const size_t smem = smem_bytes(p.cached_rows, ldw);
-    RQ_CUDA(h, cudaFuncSetAttribute(single_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     RQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-    void* args[] = {&p};
-    RQ_CUDA(h, cudaLaunchCooperativeKernel((const void*)single_solve_kernel, dim3(h->sw.grid), dim3(kThreads),
-                                           args, smem, h->stream));
+    RQ_TRY(launch_kernel(h, p, h->sw.grid, h->sw.cluster, p.cached_rows));
     RQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
     RQ_CUDA(h, cudaMemcpyAsync(x_out, y, sizeof(float) * n, cudaMemcpyDeviceToDevice, h->stream));
     if (z_out && m > 0) RQ_CUDA(h, cudaMemcpyAsync(z_out, z, sizeof(float) * m, cudaMemcpyDeviceToDevice, h->stream));
@@ -646,7 +1012,7 @@ int single_solve_noalloc(relu_qp_t h, const float* x_warm, const float* lam_warm
     RQ_CUDA(h, cudaMemcpyAsync(oi, out_i, sizeof(oi), cudaMemcpyDeviceToHost, h->stream));
     RQ_CUDA(h, cudaMemcpyAsync(of, out_f, sizeof(of), cudaMemcpyDeviceToHost, h->stream));
     RQ_CUDA(h, cudaStreamSynchronize(h->stream));
-    if (oi[OUT_ERR]) return fail(h, RELU_QP_ERR_TIMEOUT, "grid barrier deadline passed in relu_qp_solve_noalloc");
+    if (oi[OUT_ERR]) return fail(h, RELU_QP_ERR_TIMEOUT, "a barrier deadline passed in relu_qp_solve_noalloc");
     if (info) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, h->ev0, h->ev1);

@@ -212,6 +212,54 @@ def test_converged_ragged_and_degenerate(rq, dims):
     s.close()
 
 
+@pytest.mark.parametrize("name", ["sweep4", "sweep8", "sweep16"])
+def test_launch_shapes_give_the_same_bits(rq, name):
+    """The single-QP solve as a cooperative grid (1, 4 and one CTA per SM) and
+    as one thread-block cluster (2, 4, 8 and 16 CTAs that keep the layer's
+    operand in distributed shared memory and meet at cluster-scope mbarriers):
+    each row's dot product and update is the same arithmetic in every shape, so
+    every shape returns the same bits (x, z, lam, iterations, bank index) on two
+    warm-started converged solves, and the result matches the oracle.
+    n = m = 160, 320, 640 (closed-loop random MPC at nu = 4, 8, 16)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    pq, X0, _ = mpc.workload(name, 2)
+    q, l, u = pq.instance(X0[0])
+    s = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+    tuned = s.single_config()
+    ref, shapes_run = None, []
+    for ctas, cluster in [(1, 0), (4, 0), (sms, 0), (2, 2), (4, 4), (8, 8), (16, 16)]:
+        try:
+            s.set_single_config(ctas, cluster)
+        except rq.ReluQPError as e:
+            assert e.code == -6, e          # UNSUPPORTED: the shape cannot be resident
+            continue
+        assert s.single_config()[:2] == (ctas, cluster)
+        outs = []
+        x_w, lam_w, ri = None, None, -1
+        for x0 in X0:
+            qq, ll, uu = pq.instance(x0)
+            s.update(qq, ll, uu)
+            o = s.solve(x_warm=x_w, lam_warm=lam_w, rho_index=ri, eps_abs=1e-3)
+            assert o["status"] == rq.SOLVED
+            x_w, lam_w, ri = o["x"], o["lam"], o["rho_index"]
+            outs.append(o)
+        if ref is None:
+            ref = outs
+            qq, ll, uu = pq.instance(X0[-1])
+            orc = O.solve(pq.P, qq, pq.A, ll, uu, sigma=SIGMA, rho_bank=BANK, eps_abs=1e-3, max_iter=4000)
+            assert np.max(np.abs(outs[-1]["x"] - orc.x)) <= 1e-3
+        else:
+            for a, b in zip(outs, ref):
+                assert (a["iters"], a["rho_index"]) == (b["iters"], b["rho_index"]), (ctas, cluster)
+                for k in ("x", "z", "lam"):
+                    assert np.array_equal(a[k], b[k]), (ctas, cluster, k)
+        shapes_run.append((ctas, cluster))
+    s.close()
+    assert any(c > 0 for _, c in shapes_run), shapes_run
+    print(f"{name}: tuned shape {tuned}; shapes run {shapes_run}")
+
+
 def test_warm_start_at_optimum_stops_at_first_check(rq):
     pq, X0, _ = mpc.workload("sweep4", 1)
     q, l, u = pq.instance(X0[0])

@@ -71,6 +71,29 @@ def test_noalloc_matches_solve_twice(rq, name):
     s.close()
 
 
+def test_noalloc_in_cluster_shape(rq):
+    """The allocation-free solve launches the same shape as relu_qp_solve; as
+    one cluster of 8 CTAs (operand in distributed shared memory) it returns the
+    ordinary solve's bits."""
+    pq, X0, _ = mpc.workload("sweep4", 2)
+    q, l, u = pq.instance(X0[0])
+    s = rq.ReluQP(pq.P, pq.A, l, u, q=q, sigma=SIGMA, rho_bank=BANK)
+    try:
+        s.set_single_config(8, 8)
+    except rq.ReluQPError as e:
+        s.close()
+        pytest.skip(f"a cluster of 8 CTAs is not resident here: {e}")
+    for x0 in X0:
+        q, l, u = pq.instance(x0)
+        s.update(q, l, u)
+        ref = s.solve(eps_abs=1e-3)
+        got = noalloc(rq, s)
+        assert got["status"] == ref["status"] == rq.SOLVED and got["iters"] == ref["iters"]
+        for k in ("x", "z", "lam"):
+            assert np.array_equal(got[k], ref[k]), k
+    s.close()
+
+
 def test_noalloc_warm_start_and_fixed_layers(rq):
     pq, X0, _ = mpc.workload("sweep4", 1)
     q, l, u = pq.instance(X0[0])
