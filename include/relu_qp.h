@@ -469,11 +469,14 @@ int relu_qp_single_set_config(relu_qp_t h, int ctas, int cluster);
  *   whose grid barrier expects one arrival more than there are CTAs (every
  *   CTA waits until timeout_ns); kind 1: the same barrier with the right
  *   arrival count (passes; the control case); kind 2: an mbarrier wait that
- *   nothing completes; kind 3: a layer-counter wait that nothing increments.
- *   timeout_ns in [1e3, 1e9].  *status receives the kernel's error word
- *   (RELU_QP_ERR_TIMEOUT, or 0 when the wait completed), *ms (may be NULL)
- *   the device time of the launch.  Returns INVALID, OOM, CUDA, UNSUPPORTED
- *   (no cooperative launch) or OK.
+ *   nothing completes; kind 3: a layer-counter wait that nothing increments;
+ *   kind 4: a cluster of 2 CTAs whose cluster barrier (the one the
+ *   single-QP solve uses in its cluster form) expects one arrival more than
+ *   there are CTAs; kind 5: the same barrier with the right count, three
+ *   rounds (passes).  timeout_ns in [1e3, 1e9].  *status receives the
+ *   kernel's error word (RELU_QP_ERR_TIMEOUT, or 0 when the wait completed),
+ *   *ms (may be NULL) the device time of the launch.  Returns INVALID, OOM,
+ *   CUDA, UNSUPPORTED (no cooperative or cluster launch) or OK.
  * relu_qp_diag_host_barrier -- the grid barrier's arrival and wait logic (the
  *   template the kernels use) run by `threads` host threads for `rounds`
  *   barriers, with an arrival count of threads + extra: extra = 0 passes

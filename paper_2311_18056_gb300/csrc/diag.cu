@@ -31,6 +31,22 @@ __global__ void diag_grid_kernel(unsigned* bar, int* err, unsigned expected, lon
     grid_sync_n(bar, err, timeout_ns, &s_ok, expected);
 }
 
+// One cluster of CTAs that meet `rounds` times at the cluster barrier, whose
+// mbarriers expect `extra` arrivals more than there are CTAs (extra = 1: every
+// CTA waits until the deadline); every CTA then reaches the final hardware
+// cluster barrier (no CTA exits while a partner may still arrive on its
+// mbarrier).
+__global__ void diag_cluster_kernel(int* err, unsigned extra, int rounds, long long timeout_ns) {
+    __shared__ GridSyncState s_ok;
+    __shared__ __align__(8) unsigned long long s_bar;
+    ClusterBarrier cb{0u, 0u, 1};
+    cluster_barrier_init(cb, &s_bar, extra);
+    for (int k = 0; k < rounds; ++k)
+        if (!cluster_barrier(cb, err, timeout_ns, &s_ok)) break;
+    __syncthreads();
+    cl_sync_hw();
+}
+
 // Host policy of barrier_arrive_wait: C++ atomics on the same words.
 struct HostOps {
     void add_release(unsigned* p, unsigned v) { __atomic_fetch_add(p, v, __ATOMIC_RELEASE); }
@@ -52,14 +68,15 @@ struct HostOps {
 extern "C" {
 
 int relu_qp_diag_device_wait(int kind, long long timeout_ns, int* status, double* ms) {
-    if (kind < 0 || kind > 3 || timeout_ns < 1000 || timeout_ns > 1000000000LL || !status)
+    if (kind < 0 || kind > 5 || timeout_ns < 1000 || timeout_ns > 1000000000LL || !status)
         return RELU_QP_ERR_INVALID;
     *status = 0;
     if (ms) *ms = 0.0;
-    int dev = 0, sms = 0, coop = 0;
+    int dev = 0, sms = 0, coop = 0, clus = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&clus, cudaDevAttrClusterLaunch, dev) != cudaSuccess) {
         cudaGetLastError();
         return RELU_QP_ERR_CUDA;
     }
@@ -89,8 +106,29 @@ int relu_qp_diag_device_wait(int kind, long long timeout_ns, int* status, double
                 cudaSuccess)
                 rc = RELU_QP_ERR_CUDA;
         }
-    } else {
+    } else if (kind <= 3) {
         rc = rq::tc_diag_wait(kind - 2, words, timeout_ns, 0);
+    } else if (!clus) {
+        rc = RELU_QP_ERR_UNSUPPORTED;
+    } else {
+        // a cluster of 2 CTAs: kind 4 one arrival short, kind 5 three complete rounds
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(64);
+        cfg.stream = 0;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int* err = words;
+        const unsigned extra = kind == 4 ? 1u : 0u;
+        const int rounds = kind == 4 ? 1 : 3;
+        const long long ns = timeout_ns;
+        if (cudaLaunchKernelEx(&cfg, rq::diag_cluster_kernel, err, extra, rounds, ns) != cudaSuccess)
+            rc = RELU_QP_ERR_CUDA;
     }
     cudaEventRecord(e1, 0);
     if (cudaEventSynchronize(e1) != cudaSuccess) rc = RELU_QP_ERR_CUDA;

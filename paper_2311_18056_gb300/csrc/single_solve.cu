@@ -60,92 +60,12 @@ __device__ __forceinline__ bool grid_barrier(const SP& p, GridSyncState* s_ok) {
     return grid_sync(p.bar, p.out_i + OUT_ERR, p.timeout_ns, s_ok);
 }
 
-// --- one thread-block cluster instead of a cooperative grid ---
-__device__ __forceinline__ uint32_t cl_size() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cl_smem(const void* ptr) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
-}
-// shared::cluster address of the shared::cta address `addr` in CTA `rank`
-__device__ __forceinline__ uint32_t cl_mapa(uint32_t addr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void cl_st(uint32_t cluster_addr, float v) {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cluster_addr), "f"(v) : "memory");
-}
-__device__ __forceinline__ void cl_mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n fence.mbarrier_init.release.cluster;" ::"r"(bar),
-                 "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void cl_arrive(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
-}
-__device__ __forceinline__ bool cl_try(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// hardware barrier of every thread of the cluster (no deadline: used only where every
-// CTA is known to arrive, at the start and at the end of the kernel)
-__device__ __forceinline__ void cl_sync_hw() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// Synchronisation between layers and phases.  Grid form: the grid barrier.
-// Cluster form (the launch is one cluster of C CTAs): every CTA has an
-// mbarrier expecting C arrivals per phase; thread 0 arrives (release at cluster
-// scope) on all C of them (lane q of warp 0 on CTA q's) and thread 0 waits
-// (acquire) on its own, with a deadline and
-// leaving early once another CTA has set the error word.  Each CTA arrives once
-// per barrier on every mbarrier, so no CTA passes barrier k before every CTA
-// has arrived at it, and a CTA's own mbarrier is never more than one phase
-// ahead of it (the parity wait cannot miss a phase).
-struct SyncCtx {
-    GridSyncState* gs;
-    uint32_t cbar;       // the CTA's cluster mbarrier (shared::cta address)
-    uint32_t phase;      // barriers passed (cluster form)
-    int C;               // CTAs of the cluster (cluster form)
-};
-
+// Synchronisation between layers and phases: the grid barrier (grid form) or
+// the one-cluster barrier (cluster form, grid_sync.h).
 template <bool CL>
-__device__ __forceinline__ bool sync_all(const SP& p, SyncCtx& sc) {
-    if (!CL) return grid_barrier(p, sc.gs);
-    __syncthreads();
-    // lane q of warp 0 arrives on CTA q's mbarrier (the C releases overlap)
-    if (threadIdx.x < (unsigned)sc.C) cl_arrive(cl_mapa(sc.cbar, threadIdx.x));
-    if (threadIdx.x == 0) {
-        int* err = p.out_i + OUT_ERR;
-        int ok = 1;
-        const long long t0 = grid_sync_timer();
-        while (!cl_try(sc.cbar, sc.phase & 1u)) {
-            int e;
-            asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(e) : "l"(err) : "memory");
-            if (e != 0) {
-                ok = 0;
-                break;
-            }
-            if (grid_sync_timer() - t0 > p.timeout_ns) {
-                atomicExch(err, RELU_QP_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        sc.gs->ok = ok;
-    }
-    ++sc.phase;
-    __syncthreads();
-    return sc.gs->ok != 0;
+__device__ __forceinline__ bool sync_all(const SP& p, ClusterBarrier& cb, GridSyncState* gs) {
+    if (!CL) return grid_barrier(p, gs);
+    return cluster_barrier(cb, p.out_i + OUT_ERR, p.timeout_ns, gs);
 }
 
 // Dot product of a padded row with a padded vector in shared memory; the
@@ -274,7 +194,7 @@ __device__ __forceinline__ float red_get(const unsigned* slot, int word) {
 // owner of a row writes its new entry into every CTA's copy (distributed shared
 // memory) before the cluster barrier, so a layer never touches L2 for s.
 template <bool CL>
-__device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc) {
+__device__ __forceinline__ void solve_body(const SP& p, float* smem, ClusterBarrier& cb, GridSyncState* gs) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = p.n, m = p.m, R = p.R;
     const int row0 = blockIdx.x * p.rows_per_cta;
@@ -397,12 +317,12 @@ __device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc
                 for (int j = 0; j < cnt; ++j) {
                     const float v = __shfl_sync(0xffffffffu, snew, j);
                     const uint32_t addr = svn + 4u * (uint32_t)(rb + j * kWarps);
-                    for (int q = lane; q < sc.C; q += 32) cl_st(cl_mapa(addr, (uint32_t)q), v);
+                    for (int q = lane; q < cb.C; q += 32) cl_st(cl_mapa(addr, (uint32_t)q), v);
                 }
             }
         }
         cur ^= 1;
-        if (!sync_all<CL>(p, sc)) return;
+        if (!sync_all<CL>(p, cb, gs)) return;
 
         const bool is_check = (p.check_interval > 0) && (it % p.check_interval == 0);
         const bool last = (it == p.max_iter);
@@ -437,7 +357,7 @@ __device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc
                 }
             }
         }
-        if (!sync_all<CL>(p, sc)) return;
+        if (!sync_all<CL>(p, cb, gs)) return;
         if (m > 0) load_shared_cg(svk, p.lstd, p.ldt);
         __syncthreads();
         for (int j = r2_0 + warp; j < r2_1; j += kWarps) {
@@ -448,7 +368,7 @@ __device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc
                 red_max(slot, RED_ATL, v * f);
             }
         }
-        if (!sync_all<CL>(p, sc)) return;
+        if (!sync_all<CL>(p, cb, gs)) return;
 
         // ---------------- decision (identical in every CTA) ----------------
         const double rp = red_get(slot, RED_RP), rd = red_get(slot, RED_RD);
@@ -506,7 +426,7 @@ __device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc
             const float sn = 2.0f * rho_i * zi - lnew;
             if (CL) {
                 const uint32_t a = cl_smem(sv + (size_t)cur * p.ldw + r);
-                for (int q = 0; q < sc.C; ++q) cl_st(cl_mapa(a, (uint32_t)q), sn);
+                for (int q = 0; q < cb.C; ++q) cl_st(cl_mapa(a, (uint32_t)q), sn);
             } else {
                 scur2[r] = sn;
             }
@@ -515,7 +435,7 @@ __device__ __forceinline__ void solve_body(const SP& p, float* smem, SyncCtx& sc
         ++switches;
         if (ncache > 0) load_w_cache(p, wcache, ri, row0, ncache);
         for (int r = row0 + threadIdx.x; r < row1; r += blockDim.x) st_bias[r - row0] = __ldg(p.bias[ri] + r);
-        if (!sync_all<CL>(p, sc)) return;
+        if (!sync_all<CL>(p, cb, gs)) return;
     }
 }
 
@@ -525,14 +445,9 @@ __global__ void __launch_bounds__(kThreads, 1) single_solve_kernel(SP p) {
     __shared__ GridSyncState s_ok;
     __shared__ __align__(8) unsigned long long s_cbar;
     grid_sync_init(&s_ok);
-    SyncCtx sc{&s_ok, 0u, 0u, 1};
-    if (CL) {
-        sc.C = (int)cl_size();
-        sc.cbar = cl_smem(&s_cbar);
-        if (threadIdx.x == 0) cl_mbar_init(sc.cbar, (uint32_t)sc.C);
-        cl_sync_hw();   // every mbarrier initialised before any remote arrival
-    }
-    solve_body<CL>(p, smem, sc);
+    ClusterBarrier cb{0u, 0u, 1};
+    if (CL) cluster_barrier_init(cb, &s_cbar, 0u);   // C arrivals per phase
+    solve_body<CL>(p, smem, cb, &s_ok);
     if (CL) {
         // no CTA leaves while a partner may still write its shared memory (every
         // wait before this point has a deadline, so every CTA gets here)

@@ -52,7 +52,8 @@ def solve_small(rq):
     return out, ref
 
 
-@pytest.mark.parametrize("kind,what", [(0, "grid barrier"), (2, "mbarrier"), (3, "layer counter")])
+@pytest.mark.parametrize("kind,what", [(0, "grid barrier"), (2, "mbarrier"), (3, "layer counter"),
+                                       (4, "cluster barrier")])
 def test_device_wait_gives_up_at_its_deadline(rq, kind, what):
     rc, status, ms = device_wait(rq, kind, 1_000_000)          # 1 ms deadline
     assert rc == 0, what
@@ -63,8 +64,9 @@ def test_device_wait_gives_up_at_its_deadline(rq, kind, what):
     assert np.max(np.abs(out["x"] - ref.x)) <= 1e-3
 
 
-def test_grid_barrier_with_every_arrival_passes(rq):
-    rc, status, ms = device_wait(rq, 1, 1_000_000)
+@pytest.mark.parametrize("kind", [1, 5], ids=["grid barrier", "cluster barrier"])
+def test_barrier_with_every_arrival_passes(rq, kind):
+    rc, status, ms = device_wait(rq, kind, 1_000_000)
     assert rc == 0 and status == 0 and ms < 100.0
 
 
