@@ -149,3 +149,18 @@ def test_grid_barrier_logic_on_host_threads(libpath):
     assert 1.5 <= ms.value < 2000.0
     # arguments are checked
     assert L.relu_qp_diag_host_barrier(0, 0, 1, 2_000_000, ctypes.byref(n_to), None) == -1
+
+
+def test_single_launch_shape_calls_check_their_handle(libpath):
+    """relu_qp_single_config / relu_qp_single_set_config refuse a NULL handle
+    with INVALID (no GPU needed), and the device-wait diagnostics refuse kinds
+    outside 0..5 before touching the device."""
+    import paper_2311_18056_gb300 as rq
+    L = rq.lib()
+    c, k, r = ctypes.c_int(-7), ctypes.c_int(-7), ctypes.c_int(-7)
+    assert L.relu_qp_single_config(None, ctypes.byref(c), ctypes.byref(k), ctypes.byref(r)) == -1
+    assert (c.value, k.value, r.value) == (-7, -7, -7)
+    assert L.relu_qp_single_set_config(None, 8, 8) == -1
+    st, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+    assert L.relu_qp_diag_device_wait(6, 1_000_000, ctypes.byref(st), ctypes.byref(ms)) == -1
+    assert L.relu_qp_diag_device_wait(-1, 1_000_000, ctypes.byref(st), ctypes.byref(ms)) == -1
