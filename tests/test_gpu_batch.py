@@ -263,9 +263,10 @@ def test_one_tile_resident_weight_kernel(rq, B):
     print(f"B={B}: resident-weight chunk launches {used}, iterate error {worst:.2e}")
 
 
+@pytest.mark.parametrize("B", [2, 5])
 @pytest.mark.parametrize("case", ["mpc_n800", "random_n2000"])
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
-def test_tail_kernel_iterates(rq, prec, case):
+def test_tail_kernel_iterates(rq, prec, case, B):
     """Fixed-rho layers through the convergence-tail kernel.  Five QPs, a check
     every 25 layers with an eps no iterate reaches and adaptive rho off: after
     the first check at most 8 QPs are left, so layers 26..100 run in the tail
@@ -280,9 +281,10 @@ def test_tail_kernel_iterates(rq, prec, case):
     n = m = 800 runs the tail's one-pass form (all step partials of a CTA's rows
     at once, every output's state in registers); the random QP with n = 2000
     and m = 1000 (3000 rows, 20 per CTA) adds up the step partials in two
-    passes of 10 rows, and its Wt rows do not fit shared memory."""
+    passes of 10 rows, and its Wt rows do not fit shared memory.  Two and five
+    QPs: the step partials specialised on groups of 2 and 5 QPs."""
     from workloads import random_qp
-    B, B_tiled = 5, 9
+    B_tiled = 9
     if case == "mpc_n800":
         pq, X0, Q, L, U = mpc_batch("batched", B_tiled)
         P, A = pq.P, pq.A
@@ -317,5 +319,5 @@ def test_tail_kernel_iterates(rq, prec, case):
         for name, out in (("tail", tail), ("tiled", tiled)):
             got = np.concatenate([out["x"][b], out["z"][b], out["lam"][b]]).astype(np.float64)
             worst[name] = max(worst[name], rel(got, ref))
-    print(f"{case} prec={prec}: error vs oracle {worst}")
+    print(f"{case} prec={prec} B={B}: error vs oracle {worst}")
     assert worst["tail"] <= tol and worst["tiled"] <= tol, worst
