@@ -11,10 +11,14 @@
 //
 // Work split: the R = n + m rows of Wt are cut into contiguous slices, one
 // per CTA; each CTA keeps as many of its rows as fit in shared memory (the
-// rest stream from L2), and each warp produces one row at a time (coalesced
-// 128-bit loads, shuffle reduction).  A grid barrier separates layers; every
-// barrier wait has a deadline after which the kernel records
-// RELU_QP_ERR_TIMEOUT and returns.
+// rest stream from L2) and its rows' state for the whole solve, and each warp
+// computes up to 4 of its rows at once (coalesced 128-bit loads, one shuffle
+// reduction per row).  Two launch forms, chosen by timing at setup: a
+// cooperative grid, whose CTAs exchange the layer's operand through global
+// memory and meet at the grid barrier, or one thread-block cluster, whose CTAs
+// write each new operand entry into every CTA's shared copy and meet at a
+// cluster barrier.  Every barrier wait has a deadline after which the kernel
+// records RELU_QP_ERR_TIMEOUT and returns.
 #include "common.h"
 #include "grid_sync.h"
 
