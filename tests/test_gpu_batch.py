@@ -136,6 +136,42 @@ def test_converged_batched_workload_sampled(rq, prec):
     check_converged(rq, pq, Q, L, U, out, [0, 1, 333, 512, 800, 1023])
 
 
+def test_converged_batched_workload_4096_sampled(rq):
+    """The largest bench configuration (n = m = 800, B = 4096, BF16 split, the
+    launch configuration bench.py times): every QP solved with FP64-recomputed
+    residuals <= eps; 4 sampled QPs within 1e-3 of the oracle."""
+    B = 4096
+    pq, X0, Q, L, U = mpc_batch("batched", B)
+    s = rq.ReluQP(pq.P, pq.A, L[0], U[0], q=Q[0], sigma=SIGMA, rho_bank=BANK, max_batch=B,
+                  precision=rq.PREC_BF16X3)
+    s.update_batch(Q, L, U)
+    out = s.solve_batch(eps_abs=1e-3)
+    s.close()
+    assert np.all(out["status"] == rq.SOLVED)
+    X = out["x"].astype(np.float64)
+    Z = out["z"].astype(np.float64)
+    LM = out["lam"].astype(np.float64)
+    rp = np.max(np.abs(X @ pq.A.T - Z), axis=1)
+    rd = np.max(np.abs(X @ pq.P + Q + LM @ pq.A), axis=1)
+    assert np.max(rp) <= RES_SLACK * 1e-3 and np.max(rd) <= RES_SLACK * 1e-3, (np.max(rp), np.max(rd))
+    check_converged(rq, pq, Q, L, U, out, [0, 1777, 2048, 4095])
+
+
+def test_batch_sizes_are_validated(rq):
+    """An empty batch and a batch over the handle's capacity are refused with
+    INVALID before any GPU work; the handle then still solves."""
+    pq, X0, Q, L, U = mpc_batch("family0", 8)
+    s = rq.ReluQP(pq.P, pq.A, L[0], U[0], q=Q[0], sigma=SIGMA, rho_bank=BANK, max_batch=8)
+    for bad in (0, 9):
+        with pytest.raises(rq.ReluQPError) as e:
+            s.solve_batch(B=bad, eps_abs=1e-3)
+        assert e.value.kind == "INVALID", bad
+    s.update_batch(Q, L, U)
+    out = s.solve_batch(eps_abs=1e-3)
+    s.close()
+    assert np.all(out["status"] == rq.SOLVED)
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp32", "bf16x3"])
 def test_converged_humanoid_sampled(rq, prec):
     pq, X0, Q, L, U = mpc_batch("humanoid", 256)
